@@ -1,0 +1,199 @@
+/*
+ * lexgpu.h -- C ABI of the GB300 certified-split lexer.
+ *
+ * Longest-match (maximal munch), table-driven DFA lexing of one large byte
+ * buffer on one GPU, split at certified split symbols and rejoined by ordered
+ * concatenation, after "Certified Split Points for Parallel Lexing: Exact and
+ * Modulo Discarded Tokens".  Paper references below are to its sections,
+ * definitions and theorems.
+ *
+ * Conventions
+ *   - Every function returns LX_OK (0) or a negative LX_E_* code.  A lexing
+ *     error in the input is NOT a status error: it is reported through
+ *     *consumed (Section 3: con(w)); the input is completely tokenizable iff
+ *     *consumed == n.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device.  The caller owns every buffer it
+ *     passes; the library never frees or retains them past the call.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = the legacy
+ *     default stream).  Work is stream-ordered.
+ *   - Objects (lx_tokenset, lx_ctx) are owned by the library and released
+ *     with the matching *_free call.  A token set is immutable after
+ *     compilation and may be shared by several contexts and threads; a
+ *     context must not be used by two host threads at once.
+ */
+#ifndef LEXGPU_H
+#define LEXGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LX_OK 0
+#define LX_E_INVAL (-1)    /* malformed argument or automaton                  */
+#define LX_E_NOMEM (-2)    /* host or device allocation failed                 */
+#define LX_E_CAPACITY (-3) /* output capacity too small; *n_tokens = required  */
+#define LX_E_CUDA (-4)     /* a CUDA runtime call failed                       */
+#define LX_E_TIMEOUT (-5)  /* a bounded device-side wait ran out               */
+#define LX_E_MODE (-6)     /* mode not allowed (e.g. full stream, modulo cuts) */
+#define LX_E_TOOBIG (-7)   /* automaton too large for the shared-memory tables */
+
+#define LX_NONE 0xFFFFFFFFu /* undefined transition in lx_dfa.next             */
+#define LX_NO_KIND 0xFFFFu  /* non-accepting state in lx_dfa.accept_kind       */
+
+/*
+ * A compiled token set, A = (Q, Sigma, delta, q0, tau) of Section 3, in the
+ * class-compressed physical form `state = table[row(byte) + state]` of
+ * Section 1.  All arrays are host memory, read during lx_compile_tokenset
+ * only (copied).
+ *   n_states     |Q| >= 1
+ *   n_classes    number of byte classes, 1..256
+ *   q0           initial state, < n_states
+ *   n_kinds      number of token kinds, 1..32767
+ *   byte_class   [256]: class of each byte value, < n_classes
+ *   next         [n_classes * n_states]: next[c * n_states + q] = delta(q, b)
+ *                for any byte b of class c, or LX_NONE when undefined
+ *   accept_kind  [n_states]: tau(q), or LX_NO_KIND (tau is partial; any
+ *                same-length tie is already resolved, Section 3)
+ */
+typedef struct lx_dfa {
+    uint32_t n_states;
+    uint32_t n_classes;
+    uint32_t q0;
+    uint32_t n_kinds;
+    const uint8_t *byte_class;
+    const uint32_t *next;
+    const uint16_t *accept_kind;
+} lx_dfa;
+
+typedef struct lx_tokenset lx_tokenset;
+typedef struct lx_ctx lx_ctx;
+
+/* Output modes of lx_lex. */
+enum {
+    LX_FULL_EXACT = 0,      /* tok(w) in full, cuts at exact certificates (Theorem 1)          */
+    LX_FILTERED_EXACT = 1,  /* pi_I(tok(w)), cuts at exact certificates (Theorem 1, Section 5) */
+    LX_FILTERED_MODULO = 2  /* pi_I(tok(w)), cuts at certificates modulo I (Theorem 3)         */
+};
+
+/*
+ * lx_compile_tokenset -- validate the automaton and derive both certificates
+ * (Sections 4 and 6; Section 6.1 for the modulo condition) in time linear in
+ * the table: predecessor index, co-accessibility, reachability, re-entrancy
+ * (Definition 1), the exact map (Definition 2) and the map modulo the
+ * discarded set I (Definition 3), each restricted to useful bytes
+ * (Corollary 2, Proposition 2).  I is fixed here, not per call (Section 6.1).
+ *   dfa          host, read only during the call
+ *   discarded    host array of n_discarded kind ids (< dfa->n_kinds), may be
+ *                NULL when n_discarded == 0; duplicates allowed
+ *   out          receives a new token set; release with lx_tokenset_free
+ * Pure host code: needs no GPU.  Device tables are uploaded lazily by the
+ * first lx_lex on each device.
+ * Errors: LX_E_INVAL (bad sizes, out-of-range entries), LX_E_NOMEM.
+ */
+int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded, uint32_t n_discarded,
+                        lx_tokenset **out);
+
+/*
+ * lx_certificates -- the useful certified bytes (Corollary 2) and the useful
+ * bytes certified modulo I (Proposition 2).  Bit (b & 31) of word (b >> 5) is
+ * byte b.  Either output pointer may be NULL.  Host only.
+ */
+int lx_certificates(const lx_tokenset *ts, uint32_t exact_useful[8], uint32_t modulo_useful[8]);
+
+/* lx_tokenset_info -- sizes of the compiled set: n_states, live states (|Q+|),
+ * re-entrancy of q0 (Definition 1) as 0/1, and the shared-memory table form
+ * chosen for `mode` (0 = byte-indexed, 1 = class-indexed) with its row count.
+ * Any output pointer may be NULL. */
+int lx_tokenset_info(const lx_tokenset *ts, int mode, uint32_t *n_states, uint32_t *n_live,
+                     int *reentrant, int *table_form, uint32_t *table_rows);
+
+/*
+ * lx_tokenset_table -- the packed shared-memory walk table built for `mode`
+ * (for inspection and host-side tests).  Copies min(cap, size) bytes of the
+ * blob to `out` (host, may be NULL) and fills meta[10] (host, may be NULL):
+ *   { blob bytes, table_form, n_rows, ncols, row_bytes, table_bytes,
+ *     p_start, p_flag, p_slow, kind_off | cmap_off << 16 } and meta[10] =
+ *   cert_off when the array holds 11 entries (pass meta_len).
+ * Row pointers in the blob are offsets from the start of the blob.
+ */
+int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
+                      uint32_t meta_len);
+
+/* Release a token set (NULL is a no-op).  Frees its device tables. */
+void lx_tokenset_free(lx_tokenset *ts);
+
+/*
+ * lx_ctx_create -- a lexing context bound to the current CUDA device.  It owns
+ * the scratch memory of lx_lex (per-tile look-back status words, a tile
+ * counter and a result record), grown on demand with cudaMalloc.
+ * Errors: LX_E_CUDA (no device), LX_E_NOMEM.
+ */
+int lx_ctx_create(lx_ctx **out);
+
+/* Release a context (NULL is a no-op).  Synchronizes its device first. */
+void lx_ctx_free(lx_ctx *ctx);
+
+/* Bound, in milliseconds, of every device-side wait of later calls (the
+ * look-back spin and the shared-memory load barrier).  Default 20000.
+ * A wait that runs out makes the call return LX_E_TIMEOUT. */
+int lx_ctx_set_timeout_ms(lx_ctx *ctx, uint32_t ms);
+
+/* Kernel timing: when enabled, lx_lex records a CUDA event pair on its stream
+ * around the tile-kernel launch; lx_ctx_last_kernel_ms returns the elapsed
+ * time of the most recent launch (milliseconds, host out).  Off by default. */
+int lx_ctx_enable_timing(lx_ctx *ctx, int on);
+int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
+
+/*
+ * lx_lex -- lex n bytes at d_in (device) on the context's device.
+ *
+ * The input is cut before occurrences of the certified bytes that `mode`
+ * selects (Definition 2 or Definition 3), every chunk is scanned from q0 by
+ * the longest-match loop of Section 3, and the chunk streams are concatenated
+ * in order (Section 6).  By Theorem 1 (exact cuts) the result equals the
+ * serial tok(w); by Theorem 3 (modulo cuts) it equals pi_I(tok(w)).
+ *
+ *   d_in       device, n bytes, read only.  16-byte alignment enables the
+ *              bulk-copy (TMA) staging path; other alignments are accepted.
+ *   mode       LX_FULL_EXACT, LX_FILTERED_EXACT or LX_FILTERED_MODULO.
+ *   d_kinds    device, capacity entries: token kind of each emitted token.
+ *   d_lens     device, capacity entries: its length in bytes.
+ *   capacity   entries available in d_kinds / d_lens.
+ *   n_tokens   host out: tokens emitted (or required, on LX_E_CAPACITY).
+ *   consumed   host out: con(w), the offset after the last emitted token;
+ *              < n iff the scan halts on malformed input.  The tokens
+ *              returned are then exactly those before the failure
+ *              (Corollary 1; for modulo cuts, the reading in the design doc).
+ *   stream     cudaStream_t.  The call synchronizes this stream once, to
+ *              read back the 32-byte result record.
+ * Errors: LX_E_INVAL, LX_E_MODE (LX_FULL_EXACT needs exact cuts: modulo
+ * cuts only preserve pi_I, Theorem 3), LX_E_CAPACITY (entries beyond
+ * capacity are not written), LX_E_TOOBIG, LX_E_CUDA, LX_E_TIMEOUT, LX_E_NOMEM.
+ */
+int lx_lex(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+           uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
+           uint64_t *consumed, void *stream);
+
+/*
+ * lx_lex_host -- lx_lex on HOST buffers: copies h_in to the device, lexes it
+ * and copies the tokens back into h_kinds / h_lens (host, capacity entries),
+ * all on `stream`, using device buffers owned by the context.  Same results
+ * and errors as lx_lex.  Host buffers should be pinned for full copy speed.
+ */
+int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_t n, int mode,
+                uint16_t *h_kinds, uint32_t *h_lens, uint64_t capacity, uint64_t *n_tokens,
+                uint64_t *consumed, void *stream);
+
+/* Message for a status code (static string). */
+const char *lx_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LEXGPU_H */

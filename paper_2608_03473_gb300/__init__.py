@@ -1,0 +1,261 @@
+"""GB300-native certified-split lexer -- Python binding of ``include/lexgpu.h``.
+
+Argument marshalling only: every step of the lexing path runs in
+``liblexgpu.so`` (CUDA kernels for sm_103a).  PyTorch supplies device memory
+and streams.  The functions keep the C names:
+
+    ts  = lx_compile_tokenset(dfa, discarded)        # host-only analysis
+    ex, mo = lx_certificates(ts)                       # 256-bit masks as bytes
+    ctx = lx_ctx_create()
+    rc, n_tokens, consumed = lx_lex(ctx, ts, d_in, mode, d_kinds, d_lens)
+
+``dfa`` is any object with ``n_states, q0, n_kinds`` and numpy arrays
+``byte_class[256]``, ``next[n_classes, n_states]`` (-1 = undefined) and
+``accept[n_states]`` (-1 = not accepting).
+
+If the shared library is missing the import still succeeds, but every call
+raises ``RuntimeError``: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblexgpu.so")
+
+LX_OK = 0
+LX_E_INVAL = -1
+LX_E_NOMEM = -2
+LX_E_CAPACITY = -3
+LX_E_CUDA = -4
+LX_E_TIMEOUT = -5
+LX_E_MODE = -6
+LX_E_TOOBIG = -7
+LX_NONE = 0xFFFFFFFF
+LX_NO_KIND = 0xFFFF
+
+LX_FULL_EXACT = 0
+LX_FILTERED_EXACT = 1
+LX_FILTERED_MODULO = 2
+
+# every function declared in include/lexgpu.h
+EXPORTED = (
+    "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_free",
+    "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
+    "lx_lex", "lx_lex_host",
+    "lx_strerror",
+)
+
+
+class LexError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {lx_strerror(code)} ({code})" if what else f"{lx_strerror(code)} ({code})")
+
+
+class _Dfa(ctypes.Structure):
+    _fields_ = [
+        ("n_states", ctypes.c_uint32), ("n_classes", ctypes.c_uint32), ("q0", ctypes.c_uint32),
+        ("n_kinds", ctypes.c_uint32), ("byte_class", ctypes.c_void_p), ("next", ctypes.c_void_p),
+        ("accept_kind", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: Optional[str] = None):
+    """Load liblexgpu.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        sig = {
+            "lx_compile_tokenset": (i32, [vp, vp, u32, vp]),
+            "lx_certificates": (i32, [vp, vp, vp]),
+            "lx_tokenset_info": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+            "lx_tokenset_table": (i32, [vp, i32, vp, u32, vp, u32]),
+            "lx_tokenset_free": (None, [vp]),
+            "lx_ctx_create": (i32, [vp]),
+            "lx_ctx_free": (None, [vp]),
+            "lx_ctx_set_timeout_ms": (i32, [vp, u32]),
+            "lx_ctx_enable_timing": (i32, [vp, i32]),
+            "lx_ctx_last_kernel_ms": (i32, [vp, vp]),
+            "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
+            "lx_lex_host": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
+            "lx_strerror": (ctypes.c_char_p, [i32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def lx_strerror(code: int) -> str:
+    try:
+        return load_library().lx_strerror(int(code)).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+class Tokenset:
+    """Owning handle of an ``lx_tokenset``."""
+
+    def __init__(self, handle: int, n_kinds: int):
+        self.handle = handle
+        self.n_kinds = n_kinds
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.lx_tokenset_free(self.handle)
+            self.handle = None
+
+
+class Ctx:
+    """Owning handle of an ``lx_ctx``."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.lx_ctx_free(self.handle)
+            self.handle = None
+
+
+def lx_compile_tokenset(dfa, discarded: Sequence[int] = ()) -> Tokenset:
+    lib = load_library()
+    nxt = np.ascontiguousarray(dfa.next, dtype=np.int64)
+    n_classes, n_states = nxt.shape
+    nxt32 = np.where(nxt < 0, LX_NONE, nxt).astype(np.uint32)
+    acc = np.ascontiguousarray(dfa.accept, dtype=np.int64)
+    acc16 = np.where(acc < 0, LX_NO_KIND, acc).astype(np.uint16)
+    cls = np.ascontiguousarray(dfa.byte_class, dtype=np.uint8)
+    n_kinds = int(getattr(dfa, "n_kinds", 0) or (int(acc.max()) + 1))
+    d = _Dfa(n_states, n_classes, int(dfa.q0), n_kinds, cls.ctypes.data, nxt32.ctypes.data, acc16.ctypes.data)
+    disc = np.ascontiguousarray(list(discarded), dtype=np.uint16)
+    out = ctypes.c_void_p()
+    rc = lib.lx_compile_tokenset(ctypes.byref(d), disc.ctypes.data if disc.size else None, int(disc.size),
+                                 ctypes.byref(out))
+    if rc != LX_OK:
+        raise LexError(rc, "lx_compile_tokenset")
+    return Tokenset(out.value, n_kinds)
+
+
+def _mask_to_bytes(words) -> np.ndarray:
+    w = np.array(words, dtype=np.uint32)
+    return np.array([(w[b >> 5] >> (b & 31)) & 1 for b in range(256)], dtype=bool)
+
+
+def lx_certificates(ts: Tokenset) -> Tuple[np.ndarray, np.ndarray]:
+    """Useful exact and modulo-I certificate masks, as bool[256]."""
+    lib = load_library()
+    ex = (ctypes.c_uint32 * 8)()
+    mo = (ctypes.c_uint32 * 8)()
+    rc = lib.lx_certificates(ts.handle, ex, mo)
+    if rc != LX_OK:
+        raise LexError(rc, "lx_certificates")
+    return _mask_to_bytes(list(ex)), _mask_to_bytes(list(mo))
+
+
+def lx_tokenset_info(ts: Tokenset, mode: int = LX_FULL_EXACT) -> dict:
+    lib = load_library()
+    ns, nl, tr = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    re_, tf = ctypes.c_int(), ctypes.c_int()
+    rc = lib.lx_tokenset_info(ts.handle, int(mode), ctypes.byref(ns), ctypes.byref(nl), ctypes.byref(re_),
+                              ctypes.byref(tf), ctypes.byref(tr))
+    return {"status": rc, "n_states": ns.value, "n_live": nl.value, "reentrant": bool(re_.value),
+            "table_form": tf.value, "table_rows": tr.value}
+
+
+def lx_tokenset_table(ts: Tokenset, mode: int) -> Tuple[int, np.ndarray, dict]:
+    """(status, blob bytes, layout) of the packed walk table for ``mode``."""
+    lib = load_library()
+    meta = (ctypes.c_uint32 * 11)()
+    rc = lib.lx_tokenset_table(ts.handle, int(mode), None, 0, meta, 11)
+    blob = np.zeros(max(meta[0], 1), dtype=np.uint8)
+    lib.lx_tokenset_table(ts.handle, int(mode), blob.ctypes.data, int(meta[0]), None, 0)
+    keys = ("blob_bytes", "form", "n_rows", "ncols", "row_bytes", "table_bytes", "p_start", "p_flag", "p_slow")
+    info = {k: int(meta[i]) for i, k in enumerate(keys)}
+    info["kind_off"] = int(meta[9]) & 0xFFFF
+    info["cmap_off"] = int(meta[9]) >> 16
+    info["cert_off"] = int(meta[10])
+    return rc, blob[:meta[0]], info
+
+
+def lx_ctx_create() -> Ctx:
+    lib = load_library()
+    out = ctypes.c_void_p()
+    rc = lib.lx_ctx_create(ctypes.byref(out))
+    if rc != LX_OK:
+        raise LexError(rc, "lx_ctx_create")
+    return Ctx(out.value)
+
+
+def lx_ctx_set_timeout_ms(ctx: Ctx, ms: int) -> int:
+    return load_library().lx_ctx_set_timeout_ms(ctx.handle, int(ms))
+
+
+def lx_ctx_enable_timing(ctx: Ctx, on: bool = True) -> int:
+    return load_library().lx_ctx_enable_timing(ctx.handle, 1 if on else 0)
+
+
+def lx_ctx_last_kernel_ms(ctx: Ctx) -> float:
+    ms = ctypes.c_float()
+    rc = load_library().lx_ctx_last_kernel_ms(ctx.handle, ctypes.byref(ms))
+    if rc != LX_OK:
+        raise LexError(rc, "lx_ctx_last_kernel_ms")
+    return ms.value
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def lx_lex(ctx: Ctx, ts: Tokenset, d_in, mode: int, d_kinds, d_lens, n: Optional[int] = None,
+           capacity: Optional[int] = None, stream=None) -> Tuple[int, int, int]:
+    """Lex the device tensor ``d_in`` (uint8).  Returns (status, n_tokens, consumed)."""
+    lib = load_library()
+    n = d_in.numel() if n is None else int(n)
+    cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
+    nt, con = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib.lx_lex(ctx.handle, ts.handle, d_in.data_ptr(), n, int(mode), d_kinds.data_ptr(), d_lens.data_ptr(),
+                    cap, ctypes.byref(nt), ctypes.byref(con), _stream_handle(stream))
+    return rc, nt.value, con.value
+
+
+def lx_lex_host(ctx: Ctx, ts: Tokenset, h_in, mode: int, h_kinds, h_lens, n: Optional[int] = None,
+                capacity: Optional[int] = None, stream=None) -> Tuple[int, int, int]:
+    """Lex a host buffer (numpy array or CPU tensor, ideally pinned)."""
+    lib = load_library()
+
+    def ptr(x):
+        return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+
+    def size(x):
+        return x.numel() if hasattr(x, "numel") else x.size
+
+    n = size(h_in) if n is None else int(n)
+    cap = min(size(h_kinds), size(h_lens)) if capacity is None else int(capacity)
+    nt, con = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib.lx_lex_host(ctx.handle, ts.handle, ptr(h_in), n, int(mode), ptr(h_kinds), ptr(h_lens), cap,
+                         ctypes.byref(nt), ctypes.byref(con), _stream_handle(stream))
+    return rc, nt.value, con.value

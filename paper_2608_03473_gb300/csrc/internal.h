@@ -1,0 +1,82 @@
+// internal.h -- definitions shared by the host token-set compiler
+// (tokenset.cpp) and the device path (lex.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "lexgpu.h"
+
+namespace lx {
+
+// ---------------------------------------------------------------------------
+// Shared-memory walk tables.
+//
+// The scanner of Section 3 runs as a Moore machine over "rows".  Row R[q] is
+// automaton state q while a token is in progress; START is q0 at a token
+// start (nothing consumed yet); E[q'] is a copy of R[q'] entered when the
+// previous token ended just before the current byte and the new token moved
+// q0 -> q' on it; SLOW means "the fast loop cannot decide" (backtrack to the
+// last accepting position, or fail).  Rows are ordered
+//     R[0..S-1], START, E[...], SLOW
+// so "a token ended here" is one comparison of the row pointer with P_flag and
+// "take the slow path" one comparison with P_slow.  A table entry is the
+// 16-bit shared-memory address of the target row (relative offsets here; the
+// kernel adds the table's shared base when it stages the blob).
+//
+// Certified bytes are folded in: from any row but START, a byte in the cut
+// set of the mode ends the token in progress (Definition 2 / 3 guarantee the
+// serial scan has no accepting position past it), so every occurrence of a
+// certified byte is a chunk boundary.
+//
+// Two physical forms:
+//   byte-indexed:  256 u16 columns per row (512 B), row r's entry for byte b
+//                  at column b ^ 2*sigma(r); P(r) = 512 r + 4 sigma(r), so the
+//                  next address is P ^ (b << 1) -- one LOP3, and the XOR
+//                  spreads equal bytes of different rows over banks.
+//   class-indexed: n_classes + 1 u16 columns per row; P(r) = 2 (C+1) r; the
+//                  next address is P + 2 class(b); column C holds the row's
+//                  kind word.
+// ---------------------------------------------------------------------------
+enum TableForm : int { FORM_BYTE = 0, FORM_CLASS = 1 };
+
+constexpr uint32_t KIND_NONE = 0x7FFFu;   // kind word: bits 0..14 kind, bit 15 kept
+constexpr uint32_t KIND_KEEP = 0x8000u;
+constexpr uint32_t MAX_TABLE_BYTES = 60u * 1024u;
+constexpr uint32_t MAX_BYTE_FORM_BYTES = 40u * 1024u;
+
+struct HostTable {
+    int status = LX_OK;          // LX_OK, or LX_E_TOOBIG for this mode
+    int form = FORM_BYTE;
+    uint32_t n_rows = 0;
+    uint32_t ncols = 0;          // 256 (byte form) or C + 1 (class form)
+    uint32_t row_bytes = 0;
+    uint32_t table_bytes = 0;    // bytes of row entries
+    uint32_t p_start = 0, p_flag = 0, p_slow = 0;   // relative row pointers
+    uint32_t kind_off = 0;       // byte form: u16 kind word per row
+    uint32_t cmap_off = 0;       // class form: u8 class per byte
+    uint32_t cert_off = 0;       // u8 per byte: 1 = cut byte in this mode
+    std::vector<uint8_t> blob;   // everything above, 16-byte padded
+};
+
+struct DeviceTables {
+    int device = -1;
+    void *d_blob[3] = {nullptr, nullptr, nullptr};
+};
+
+}  // namespace lx
+
+struct lx_tokenset {
+    uint32_t n_states = 0, n_classes = 0, q0 = 0, n_kinds = 0;
+    std::vector<uint8_t> byte_class;
+    std::vector<uint32_t> next;       // [c * S + q]
+    std::vector<uint16_t> accept;     // [q]
+    std::vector<uint8_t> discard;     // [kind]
+    std::vector<uint8_t> live;        // [q], Q+
+    bool reentrant = false;
+    uint32_t exact[8] = {0}, modulo[8] = {0};
+    lx::HostTable tab[3];
+    std::mutex mu;
+    std::vector<lx::DeviceTables> dev;
+};

@@ -1,0 +1,331 @@
+// tokenset.cpp -- lx_compile_tokenset: the linear certificate derivation of
+// Sections 4.1, 6 and 6.1, and the packing of the shared-memory walk tables.
+// Pure host code.
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace {
+
+using lx::HostTable;
+
+// Predecessor index over the stored (class-compressed) table: one entry per
+// defined (state, class) edge, grouped by target (Section 6.1 builds it once
+// per class row and reuses it for both closures).
+struct PredIndex {
+    std::vector<uint32_t> start;   // [S + 1]
+    std::vector<uint32_t> src;     // sources, grouped by target
+};
+
+PredIndex build_pred(const lx_tokenset &t)
+{
+    const uint32_t S = t.n_states, C = t.n_classes;
+    PredIndex pi;
+    pi.start.assign(S + 1, 0);
+    for (uint32_t c = 0; c < C; c++)
+        for (uint32_t q = 0; q < S; q++) {
+            uint32_t d = t.next[(size_t)c * S + q];
+            if (d != LX_NONE) pi.start[d + 1]++;
+        }
+    for (uint32_t q = 0; q < S; q++) pi.start[q + 1] += pi.start[q];
+    pi.src.resize(pi.start[S]);
+    std::vector<uint32_t> fill(pi.start.begin(), pi.start.end() - 1);
+    for (uint32_t c = 0; c < C; c++)
+        for (uint32_t q = 0; q < S; q++) {
+            uint32_t d = t.next[(size_t)c * S + q];
+            if (d != LX_NONE) pi.src[fill[d]++] = q;
+        }
+    return pi;
+}
+
+// Reverse closure from `seed` states along edges accepted by `edge_ok`.
+template <class EdgeOk>
+std::vector<uint8_t> reverse_closure(const PredIndex &pi, std::vector<uint32_t> work,
+                                     uint32_t S, EdgeOk edge_ok)
+{
+    std::vector<uint8_t> mark(S, 0);
+    for (uint32_t q : work) mark[q] = 1;
+    while (!work.empty()) {
+        uint32_t t = work.back();
+        work.pop_back();
+        for (uint32_t k = pi.start[t]; k < pi.start[t + 1]; k++) {
+            uint32_t p = pi.src[k];
+            if (!mark[p] && edge_ok(p, t)) {
+                mark[p] = 1;
+                work.push_back(p);
+            }
+        }
+    }
+    return mark;
+}
+
+void derive_certificates(lx_tokenset &t)
+{
+    const uint32_t S = t.n_states, C = t.n_classes, q0 = t.q0;
+    auto nx = [&](uint32_t c, uint32_t q) { return t.next[(size_t)c * S + q]; };
+    PredIndex pi = build_pred(t);
+
+    // co-accessibility: accepting states seed a worklist over predecessors
+    std::vector<uint32_t> seeds;
+    for (uint32_t q = 0; q < S; q++)
+        if (t.accept[q] != LX_NO_KIND) seeds.push_back(q);
+    std::vector<uint8_t> coacc = reverse_closure(pi, seeds, S, [](uint32_t, uint32_t) { return true; });
+
+    // reachability: forward sweep from q0
+    std::vector<uint8_t> reach(S, 0);
+    std::vector<uint32_t> stack{q0};
+    reach[q0] = 1;
+    while (!stack.empty()) {
+        uint32_t q = stack.back();
+        stack.pop_back();
+        for (uint32_t c = 0; c < C; c++) {
+            uint32_t d = nx(c, q);
+            if (d != LX_NONE && !reach[d]) {
+                reach[d] = 1;
+                stack.push_back(d);
+            }
+        }
+    }
+    t.live.assign(S, 0);
+    for (uint32_t q = 0; q < S; q++) t.live[q] = reach[q] && coacc[q];
+    const std::vector<uint8_t> &live = t.live;
+    auto live_edge = [&](uint32_t c, uint32_t q) -> uint32_t {   // delta+(q, c)
+        if (!live[q]) return LX_NONE;
+        uint32_t d = nx(c, q);
+        return (d != LX_NONE && live[d]) ? d : LX_NONE;
+    };
+
+    // re-entrancy: any live transition into q0 (the equivalent test below
+    // Definition 1)
+    t.reentrant = false;
+    for (uint32_t c = 0; c < C && !t.reentrant; c++)
+        for (uint32_t q = 0; q < S; q++)
+            if (live_edge(c, q) == q0) { t.reentrant = true; break; }
+
+    // T(q) subset of I  <=>  q not reached by the reverse closure seeded with
+    // live accepting states whose kind is kept (Section 6.1)
+    std::vector<uint32_t> kept;
+    for (uint32_t q = 0; q < S; q++)
+        if (live[q] && t.accept[q] != LX_NO_KIND && !t.discard[t.accept[q]]) kept.push_back(q);
+    std::vector<uint8_t> keeps = reverse_closure(pi, kept, S, [&](uint32_t p, uint32_t d) {
+        return live[p] && live[d];
+    });
+
+    std::memset(t.exact, 0, sizeof t.exact);
+    std::memset(t.modulo, 0, sizeof t.modulo);
+    if (!live[q0]) return;   // accepts nothing: no useful symbol
+    std::vector<uint8_t> ex_c(C), mo_c(C);
+    for (uint32_t c = 0; c < C; c++) {
+        uint32_t d0 = live_edge(c, q0);
+        bool ex = true, mo = true;
+        for (uint32_t q = 0; q < S && (ex || mo); q++) {
+            uint32_t d = live_edge(c, q);
+            if (d == LX_NONE) continue;
+            bool A = (q == q0) && !t.reentrant;
+            if (!A) ex = false;
+            bool Cq = t.accept[q] != LX_NO_KIND && d0 != LX_NONE && d0 == d && !keeps[q];
+            if (!(A || Cq)) mo = false;
+        }
+        ex_c[c] = ex && d0 != LX_NONE;    // useful (Corollary 2)
+        mo_c[c] = mo && d0 != LX_NONE;    // useful (Proposition 2)
+    }
+    for (uint32_t b = 0; b < 256; b++) {
+        uint32_t c = t.byte_class[b];
+        if (ex_c[c]) t.exact[b >> 5] |= 1u << (b & 31);
+        if (mo_c[c]) t.modulo[b >> 5] |= 1u << (b & 31);
+    }
+}
+
+inline bool bit(const uint32_t m[8], uint32_t b) { return (m[b >> 5] >> (b & 31)) & 1u; }
+
+// Walk rows (see internal.h).  target(row, class) -> row.
+void build_table(const lx_tokenset &t, int mode, HostTable &ht)
+{
+    const uint32_t S = t.n_states, C = t.n_classes, q0 = t.q0;
+    auto nx = [&](uint32_t c, uint32_t q) { return t.next[(size_t)c * S + q]; };
+    const uint32_t *cutmask = (mode == LX_FILTERED_MODULO) ? t.modulo : t.exact;
+    std::vector<uint8_t> cut_c(C, 0);
+    for (uint32_t b = 0; b < 256; b++)
+        if (bit(cutmask, b)) cut_c[t.byte_class[b]] = 1;
+
+    // E rows: one per distinct delta(q0, c)
+    std::vector<uint32_t> e_row(S, LX_NONE);
+    std::vector<uint32_t> e_state;
+    for (uint32_t c = 0; c < C; c++) {
+        uint32_t d = nx(c, q0);
+        if (d != LX_NONE && e_row[d] == LX_NONE) {
+            e_row[d] = S + 1 + (uint32_t)e_state.size();
+            e_state.push_back(d);
+        }
+    }
+    const uint32_t START = S, SLOW = S + 1 + (uint32_t)e_state.size();
+    const uint32_t R = SLOW + 1;
+
+    std::vector<uint32_t> tgt((size_t)R * C);
+    auto state_row = [&](uint32_t row, uint32_t s) {
+        for (uint32_t c = 0; c < C; c++) {
+            uint32_t d0 = nx(c, q0), d = nx(c, s);
+            bool acc = t.accept[s] != LX_NO_KIND;
+            uint32_t r;
+            if (cut_c[c]) r = acc ? e_row[d0] : SLOW;
+            else if (d != LX_NONE) r = d;
+            else if (acc && d0 != LX_NONE) r = e_row[d0];
+            else r = SLOW;
+            tgt[(size_t)row * C + c] = r;
+        }
+    };
+    for (uint32_t s = 0; s < S; s++) state_row(s, s);
+    for (uint32_t c = 0; c < C; c++) {
+        uint32_t d0 = nx(c, q0);
+        tgt[(size_t)START * C + c] = d0 != LX_NONE ? d0 : SLOW;
+        tgt[(size_t)SLOW * C + c] = SLOW;
+    }
+    for (uint32_t k = 0; k < e_state.size(); k++) state_row(S + 1 + k, e_state[k]);
+
+    std::vector<uint16_t> kind(R, (uint16_t)lx::KIND_NONE);
+    auto kind_word = [&](uint32_t s) -> uint16_t {
+        uint16_t a = t.accept[s];
+        if (a == LX_NO_KIND) return (uint16_t)lx::KIND_NONE;
+        bool keep = (mode == LX_FULL_EXACT) || !t.discard[a];
+        return (uint16_t)(a | (keep ? lx::KIND_KEEP : 0));
+    };
+    for (uint32_t s = 0; s < S; s++) kind[s] = kind_word(s);
+    for (uint32_t k = 0; k < e_state.size(); k++) kind[S + 1 + k] = kind_word(e_state[k]);
+
+    ht = HostTable();
+    ht.n_rows = R;
+    bool byte_form = (uint64_t)R * 512 <= lx::MAX_BYTE_FORM_BYTES;
+    std::vector<uint32_t> P(R);
+    if (byte_form) {
+        ht.form = lx::FORM_BYTE;
+        ht.ncols = 256;
+        ht.row_bytes = 512;
+        for (uint32_t r = 0; r < R; r++) P[r] = 512 * r + 4 * (r & 31);
+        ht.p_flag = 512 * (S + 1);
+        ht.p_slow = 512 * SLOW;
+    } else {
+        ht.form = lx::FORM_CLASS;
+        ht.ncols = C + 1;
+        ht.row_bytes = 2 * (C + 1);
+        for (uint32_t r = 0; r < R; r++) P[r] = ht.row_bytes * r;
+        ht.p_flag = P[S + 1];
+        ht.p_slow = P[SLOW];
+    }
+    ht.p_start = P[START];
+    ht.table_bytes = R * ht.row_bytes;
+    if (ht.table_bytes > lx::MAX_TABLE_BYTES) {
+        ht.status = LX_E_TOOBIG;
+        return;
+    }
+    uint32_t off = ht.table_bytes;
+    if (byte_form) {
+        ht.kind_off = off;
+        off += 2 * R;
+    }
+    off = (off + 15) & ~15u;
+    ht.cmap_off = off;
+    off += 256;
+    ht.cert_off = off;
+    off += 256;
+    off = (off + 15) & ~15u;
+    ht.blob.assign(off, 0);
+    uint16_t *ent = reinterpret_cast<uint16_t *>(ht.blob.data());
+    for (uint32_t r = 0; r < R; r++) {
+        if (byte_form) {
+            uint32_t sig2 = 2 * (r & 31);
+            for (uint32_t b = 0; b < 256; b++)
+                ent[(size_t)r * 256 + (b ^ sig2)] = (uint16_t)P[tgt[(size_t)r * C + t.byte_class[b]]];
+        } else {
+            for (uint32_t c = 0; c < C; c++)
+                ent[(size_t)r * (C + 1) + c] = (uint16_t)P[tgt[(size_t)r * C + c]];
+            ent[(size_t)r * (C + 1) + C] = kind[r];
+        }
+    }
+    if (byte_form) {
+        uint16_t *kw = reinterpret_cast<uint16_t *>(ht.blob.data() + ht.kind_off);
+        for (uint32_t r = 0; r < R; r++) kw[r] = kind[r];
+    }
+    for (uint32_t b = 0; b < 256; b++) {
+        ht.blob[ht.cmap_off + b] = t.byte_class[b];
+        ht.blob[ht.cert_off + b] = bit(cutmask, b) ? 1 : 0;
+    }
+}
+
+}  // namespace
+
+extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
+                                   uint32_t n_discarded, lx_tokenset **out)
+{
+    if (!dfa || !out) return LX_E_INVAL;
+    *out = nullptr;
+    const uint32_t S = dfa->n_states, C = dfa->n_classes;
+    if (S == 0 || S > (1u << 20) || C == 0 || C > 256 || dfa->q0 >= S || dfa->n_kinds == 0 ||
+        dfa->n_kinds > 32767 || !dfa->byte_class || !dfa->next || !dfa->accept_kind)
+        return LX_E_INVAL;
+    if (n_discarded && !discarded) return LX_E_INVAL;
+    for (uint32_t b = 0; b < 256; b++)
+        if (dfa->byte_class[b] >= C) return LX_E_INVAL;
+    for (size_t k = 0; k < (size_t)S * C; k++)
+        if (dfa->next[k] != LX_NONE && dfa->next[k] >= S) return LX_E_INVAL;
+    for (uint32_t q = 0; q < S; q++)
+        if (dfa->accept_kind[q] != LX_NO_KIND && dfa->accept_kind[q] >= dfa->n_kinds) return LX_E_INVAL;
+    for (uint32_t k = 0; k < n_discarded; k++)
+        if (discarded[k] >= dfa->n_kinds) return LX_E_INVAL;
+
+    lx_tokenset *t = new (std::nothrow) lx_tokenset();
+    if (!t) return LX_E_NOMEM;
+    try {
+        t->n_states = S;
+        t->n_classes = C;
+        t->q0 = dfa->q0;
+        t->n_kinds = dfa->n_kinds;
+        t->byte_class.assign(dfa->byte_class, dfa->byte_class + 256);
+        t->next.assign(dfa->next, dfa->next + (size_t)S * C);
+        t->accept.assign(dfa->accept_kind, dfa->accept_kind + S);
+        t->discard.assign(dfa->n_kinds, 0);
+        for (uint32_t k = 0; k < n_discarded; k++) t->discard[discarded[k]] = 1;
+        derive_certificates(*t);
+        for (int m = 0; m < 3; m++) build_table(*t, m, t->tab[m]);
+    } catch (const std::bad_alloc &) {
+        delete t;
+        return LX_E_NOMEM;
+    }
+    *out = t;
+    return LX_OK;
+}
+
+extern "C" int lx_certificates(const lx_tokenset *ts, uint32_t exact_useful[8], uint32_t modulo_useful[8])
+{
+    if (!ts) return LX_E_INVAL;
+    if (exact_useful) std::memcpy(exact_useful, ts->exact, sizeof ts->exact);
+    if (modulo_useful) std::memcpy(modulo_useful, ts->modulo, sizeof ts->modulo);
+    return LX_OK;
+}
+
+extern "C" int lx_tokenset_info(const lx_tokenset *ts, int mode, uint32_t *n_states, uint32_t *n_live,
+                                int *reentrant, int *table_form, uint32_t *table_rows)
+{
+    if (!ts || mode < 0 || mode > 2) return LX_E_INVAL;
+    if (n_states) *n_states = ts->n_states;
+    if (n_live) *n_live = (uint32_t)std::count(ts->live.begin(), ts->live.end(), (uint8_t)1);
+    if (reentrant) *reentrant = ts->reentrant ? 1 : 0;
+    if (table_form) *table_form = ts->tab[mode].form;
+    if (table_rows) *table_rows = ts->tab[mode].n_rows;
+    return ts->tab[mode].status;
+}
+
+extern "C" int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
+                                 uint32_t meta_len)
+{
+    if (!ts || mode < 0 || mode > 2) return LX_E_INVAL;
+    const HostTable &h = ts->tab[mode];
+    if (out && cap) std::memcpy(out, h.blob.data(), std::min<size_t>(cap, h.blob.size()));
+    const uint32_t m[11] = {(uint32_t)h.blob.size(), (uint32_t)h.form, h.n_rows, h.ncols, h.row_bytes,
+                            h.table_bytes, h.p_start, h.p_flag, h.p_slow, h.kind_off | (h.cmap_off << 16),
+                            h.cert_off};
+    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 11));
+    return h.status;
+}
