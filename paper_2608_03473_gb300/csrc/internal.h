@@ -18,10 +18,10 @@ namespace lx {
 // start (nothing consumed yet); E[q'] is a copy of R[q'] entered when the
 // previous token ended just before the current byte and the new token moved
 // q0 -> q' on it; SLOW means "the fast loop cannot decide" (backtrack to the
-// last accepting position, or fail).  Rows are ordered
-//     R[0..S-1], START, E[...], SLOW
-// so "a token ended here" is one comparison of the row pointer with P_flag and
-// "take the slow path" one comparison with P_slow.  A table entry is the
+// last accepting position, or fail) and absorbs every byte.  Rows are ordered
+//     SLOW, R[0..S-1], START, E[...]
+// so "a token ended here" is one comparison of the row pointer with P_flag
+// and "take the slow path" one equality with P_slow.  A table entry is the
 // 16-bit shared-memory address of the target row (relative offsets here; the
 // kernel adds the table's shared base when it stages the blob).
 //

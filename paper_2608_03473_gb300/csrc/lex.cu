@@ -34,13 +34,15 @@
 namespace lx {
 
 constexpr int NT = 256;                 // threads per CTA
+constexpr int NW = NT / 32;
 constexpr int SEG = 68;                 // bytes per thread target (17 words: odd stride)
 constexpr int TILE = NT * SEG;          // 17408 input bytes per tile
-constexpr int HALO = 1024;              // extra staged bytes for walks that run past the tile
+constexpr int HALO = 1024;              // extra staged bytes for ranges that run past the tile
 constexpr int BUF = TILE + HALO;        // 18432, a multiple of 16
-constexpr int KSLOT = 20;               // shared token slots per thread
-constexpr int STAGE_CAP = 4096;         // tokens per tile that take the coalesced path
+constexpr int KS = 40;                  // token-end records per thread
+constexpr int STAGE_CAP = 4096;         // kept tokens per tile that take the deferred coalesced path
 constexpr uint64_t NOPOS = ~0ull;
+constexpr uint32_t NONE32 = 0xFFFFFFFFu;
 
 constexpr unsigned ERR_TIMEOUT = 1u;
 constexpr unsigned ERR_SMEM = 2u;
@@ -76,20 +78,20 @@ struct Params {
 };
 
 // ---- shared-memory layout (bytes from the dynamic shared base) ----
+// [walk tables][input tile + halo, one TMA buffer][per-lane record columns]
+// [stage: the previous tile's kept tokens, waiting for its output offset][misc]
 struct Layout {
-    uint32_t blob, buf0, buf1, slots, stage, misc, total;
+    uint32_t buf, slots, stage, misc, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) & ~(a - 1); }
 
 __host__ __device__ inline Layout make_layout(uint32_t blob_bytes)
 {
-    Layout L;
-    L.blob = 0;                                   // + up to 511 bytes to 512-align the table
-    L.buf0 = align_up(512 + blob_bytes, 128);
-    L.buf1 = L.buf0 + BUF;
-    L.slots = L.buf1 + BUF;
-    L.stage = L.slots + KSLOT * NT * 4;
+    Layout L;                                    // blob first: + up to 511 bytes to 512-align the table
+    L.buf = align_up(512 + blob_bytes, 128);
+    L.slots = L.buf + BUF;
+    L.stage = L.slots + KS * NT * 4;
     L.misc = L.stage + STAGE_CAP * 4;
     L.total = L.misc + 256;
     return L;
@@ -97,11 +99,19 @@ __host__ __device__ inline Layout make_layout(uint32_t blob_bytes)
 
 // misc region offsets
 constexpr uint32_t M_WARP = 0;      // u64[8] warp totals -> exclusive offsets
-constexpr uint32_t M_MBAR = 64;     // u64[2]
-constexpr uint32_t M_TILE = 80;     // u32[2]: next tile id, flags
-constexpr uint32_t M_G = 96;        // u64: tile's global output offset
-constexpr uint32_t M_TOT = 104;     // u64: tile total
-constexpr uint32_t M_FLAG = 112;    // u32: CTA flags
+constexpr uint32_t M_MBAR = 64;     // u64
+constexpr uint32_t M_TILE = 80;     // u32: next tile id
+constexpr uint32_t M_X = 84;        // u32: first cut at or past the tile end (relative)
+constexpr uint32_t M_G = 96;        // u64: resolved output offset
+constexpr uint32_t M_TOT = 104;     // u64: this tile's kept total
+constexpr uint32_t M_FPOS = 112;    // u64: this tile's first failure offset (NOPOS = none)
+constexpr uint32_t M_FIDX = 120;    // u64: kept tokens before it, within the tile
+constexpr uint32_t M_WMIN = 128;    // u32[8]: per-warp minimum chunk start
+constexpr uint32_t M_PTILE = 160;   // u32: pending tile (NONE32 = none)
+constexpr uint32_t M_PTOT = 168;    // u64: pending tile's kept total
+constexpr uint32_t M_PFPOS = 176;   // u64: pending tile's failure offset
+constexpr uint32_t M_PFIDX = 184;   // u64: pending tile's kept tokens before the failure
+constexpr uint32_t M_FLAGS = 192;   // u32: this tile: bit0 synchronous
 
 // ---- PTX helpers ----
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -120,21 +130,33 @@ __device__ __forceinline__ uint32_t lds_u16(uint32_t a)
     asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
     return v;
 }
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer()
 {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+// Status words carry a flag and a count in one 64-bit store; nothing else a
+// predecessor wrote is read, so relaxed gpu-scope accesses suffice.
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p)
 {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+__device__ __forceinline__ void st_status(unsigned long long *p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
 {
@@ -179,7 +201,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64
     }
 }
 
-// ---- the walk ----
+// ---- tables ----
 struct Env {
     uint32_t buf;          // shared address of the staged tile
     uint64_t tile_base;    // input offset of buf[0]
@@ -203,6 +225,19 @@ __device__ __forceinline__ uint32_t step(const Env &E, uint32_t e, uint32_t b)
     return lds_u16(e + (c << 1));
 }
 
+// Step on byte K of a little-endian word: the byte-indexed form folds the
+// extraction and the row address into one shift and one LOP3.
+template <int FORM, int K>
+__device__ __forceinline__ uint32_t step_w(const Env &E, uint32_t e, uint32_t w)
+{
+    if (FORM == FORM_BYTE) {
+        uint32_t x = K == 0 ? (w << 1) : (w >> (8 * K - 1));
+        return lds_u16(e ^ (x & 0x1FEu));
+    }
+    uint32_t c = lds_u8(E.cmap_s + ((w >> (8 * K)) & 0xFFu));
+    return lds_u16(e + (c << 1));
+}
+
 template <int FORM>
 __device__ __forceinline__ uint32_t kind_of(const Env &E, uint32_t e)
 {
@@ -212,26 +247,12 @@ __device__ __forceinline__ uint32_t kind_of(const Env &E, uint32_t e)
 
 __device__ __forceinline__ bool is_cut(const Env &E, uint32_t b) { return lds_u8(E.cert_s + b) != 0; }
 
-// Emission into shared slots (first pass).
-struct SlotEmit {
-    uint32_t slots;   // shared address of this thread's slot column
-    uint32_t count;
-    bool ovf;
-    __device__ __forceinline__ void operator()(uint32_t kw, uint64_t len)
-    {
-        if (!(kw & KIND_KEEP)) return;
-        uint32_t k = kw & 0x7FFFu;
-        if (count < KSLOT && len < (1u << 20) && k < 4096u) {
-            uint32_t v = (k << 20) | (uint32_t)len;
-            asm volatile("st.shared.u32 [%0], %1;" ::"r"(slots + count * NT * 4), "r"(v) : "memory");
-        } else {
-            ovf = true;
-        }
-        count++;
-    }
+// ---- generic walker (64-bit offsets, reads past the staged bytes) ----
+struct CountEmit {
+    uint64_t count = 0;
+    __device__ __forceinline__ void operator()(uint32_t kw, uint64_t) { count += (kw & KIND_KEEP) ? 1 : 0; }
 };
 
-// Emission straight to global memory (tiles that overflow their slots).
 struct DirectEmit {
     uint16_t *kinds;
     uint32_t *lens;
@@ -251,7 +272,8 @@ struct DirectEmit {
 // Longest-match walk of the chunks that start at `start` (a certified byte,
 // or offset 0) and run until a certified byte at or past `seg_end`, or the
 // end of the input.  Returns the failure offset (Section 3: the scan halts
-// where no positive-length accepting prefix exists) or NOPOS.
+// where no positive-length accepting prefix exists) or NOPOS.  Used for
+// ranges that leave the staged bytes or overflow their records.
 template <int FORM, class Emit>
 __device__ uint64_t walk(const Env &E, uint64_t start, uint64_t seg_end, Emit &emit)
 {
@@ -271,14 +293,12 @@ __device__ uint64_t walk(const Env &E, uint64_t start, uint64_t seg_end, Emit &e
             uint32_t b = byte_at(E, p);
             uint32_t e2 = step<FORM>(E, e, b);
             slow = false;
-            if (e2 >= E.P_flag) {
-                if (e2 >= E.P_slow) {
-                    slow = true;
-                } else {
-                    emit(kind_of<FORM>(E, e), p - tok);   // token [tok, p) ends before byte p
-                    tok = p;
-                    if (p >= seg_end && is_cut(E, b)) return NOPOS;
-                }
+            if (e2 == E.P_slow) {
+                slow = true;
+            } else if (e2 >= E.P_flag) {
+                emit(kind_of<FORM>(E, e), p - tok);   // token [tok, p) ends before byte p
+                tok = p;
+                if (p >= seg_end && is_cut(E, b)) return NOPOS;
             }
             if (!slow) {
                 e = e2;
@@ -307,37 +327,179 @@ __device__ uint64_t walk(const Env &E, uint64_t start, uint64_t seg_end, Emit &e
     }
 }
 
-// Decoupled look-back (thread 0): publish this tile's aggregate, accumulate
-// predecessors until an inclusive prefix, publish ours.  Bounded spin.
-__device__ uint64_t lookback(const Params &P, uint32_t tile, uint64_t agg, bool need, bool &timed_out)
+// ---- lockstep walker (staged bytes only, 32-bit offsets) ----
+enum { LS_WALK = 0, LS_SLOW = 1, LS_EOI = 2, LS_DONE = 3, LS_FAIL = 4, LS_OVF = 5 };
+
+// All lanes of a warp walk their ranges in lockstep, up to four bytes per
+// lane per iteration from one shared-memory word, with every per-byte
+// decision predicated so that the warp stays converged.  A lane's range is
+// [start, end]: `end` is the next chunk start (a certified byte, whose step
+// ends the last token) or, with `eoi`, the end of the input.  Every token
+// end is recorded as (row before the byte << 16 | end offset) in the lane's
+// record column `col` (stride NT words); kinds and the discard filter are
+// applied afterwards.  A lane that falls into the absorbing SLOW row leaves
+// the lockstep loop and replays its current token from q0 to its last
+// accepting position (longest match with backtracking), then rejoins.
+template <int FORM>
+__device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t start, uint32_t end, bool eoi,
+                                             uint32_t col, uint32_t &cnt, uint32_t &fail)
 {
-    if (tile == 0) {
-        st_release(&P.status[0], ST_INCL | agg);
-        return 0;
+    const uint32_t P_flag = E.P_flag, P_slow = E.P_slow;
+    const uint32_t col_end = col + (uint32_t)KS * NT * 4;
+    const uint32_t lim = eoi ? end : end + 1;
+    uint32_t e = E.P_start, p = start, rst = start, sp = col, sp0 = col;
+    int st = has ? LS_WALK : LS_DONE;
+    for (;;) {
+        while (__any_sync(0xffffffffu, st == LS_WALK)) {
+            if (st == LS_WALK) {
+                if (sp + 4 * NT * 4 > col_end) {
+                    st = LS_OVF;
+                } else {
+                    const uint32_t base = p & ~3u;
+                    const uint32_t w = lds_u32(E.buf + base);
+                    const uint32_t k0 = p & 3u;
+                    const uint32_t kend = lim - base < 4u ? lim - base : 4u;
+                    const uint32_t amask = (0xFu << k0) & (0xFu >> (4u - kend));
+                    uint32_t e2;
+#define LX_STEP(K)                                         \
+    if (amask & (1u << K)) {                               \
+        e2 = step_w<FORM, K>(E, e, w);                     \
+        if (e2 >= P_flag) {                                \
+            sts_u32(sp, (e << 16) | (base + K));           \
+            sp += NT * 4;                                  \
+        }                                                  \
+        e = e2;                                            \
     }
-    st_release(&P.status[tile], ST_AGG | agg);
-    if (!need) return 0;
+                    LX_STEP(0)
+                    LX_STEP(1)
+                    LX_STEP(2)
+                    LX_STEP(3)
+#undef LX_STEP
+                    p = base + kend;
+                    if (e == P_slow) st = LS_SLOW;
+                    else if (p >= lim) st = eoi ? LS_EOI : LS_DONE;
+                }
+            }
+        }
+        // events, one lane at a time where they occur
+        if (st == LS_EOI) {   // close the token in progress at the end of the input
+            if (e == E.P_start) {
+                st = LS_DONE;
+            } else if ((kind_of<FORM>(E, e) & 0x7FFFu) != KIND_NONE) {
+                if (sp + NT * 4 > col_end) {
+                    st = LS_OVF;
+                } else {
+                    sts_u32(sp, (e << 16) | p);
+                    sp += NT * 4;
+                    st = LS_DONE;
+                }
+            } else {
+                st = LS_SLOW;
+            }
+        }
+        if (st == LS_SLOW) {
+            // the token in progress began at the last recorded end (or the
+            // last restart); SLOW absorbs, so replaying up to p (never past
+            // the range's cut byte) finds the same last accepting position
+            const uint32_t tok = sp > sp0 ? (lds_u32(sp - NT * 4) & 0xFFFFu) : rst;
+            const uint32_t stop = (!eoi && p > end) ? end : p;
+            uint32_t q = E.P_start, r = NONE32, rq = 0;
+            for (uint32_t j = tok; j < stop; j++) {
+                q = step<FORM>(E, q, lds_u8(E.buf + j));
+                if ((kind_of<FORM>(E, q) & 0x7FFFu) != KIND_NONE) {
+                    r = j + 1;
+                    rq = q;
+                }
+            }
+            if (r == NONE32) {
+                fail = tok;
+                st = LS_FAIL;
+            } else if (sp + NT * 4 > col_end) {
+                st = LS_OVF;
+            } else {
+                sts_u32(sp, (rq << 16) | r);
+                sp += NT * 4;
+                sp0 = sp;
+                rst = p = r;
+                e = E.P_start;
+                st = r == end ? LS_DONE : LS_WALK;
+            }
+        }
+        if (!__any_sync(0xffffffffu, st == LS_WALK)) break;
+    }
+    cnt = (sp - col) / (NT * 4);
+    return st;
+}
+
+// Decoupled look-back, one warp.  Each tile first publishes its aggregate
+// (tile 0 its inclusive prefix) without waiting; later, one warp resolves
+// the exclusive prefix: each round its 32 lanes read 32 predecessor status
+// words at once, the round ends at the nearest inclusive prefix (summing the
+// aggregates before it) or, with none, adds all 32 aggregates and moves 32
+// tiles back.  A lane that sees an unpublished word before the nearest
+// inclusive prefix makes the round repeat, bounded by the time budget.
+__device__ __forceinline__ void publish_aggregate(const Params &P, uint32_t tile, uint64_t agg)
+{
+    st_status(&P.status[tile], (tile == 0 ? ST_INCL : ST_AGG) | agg);
+}
+
+constexpr int LB_PER_LANE = 8;   // predecessor words per lane and round: 256 tiles per round
+
+__device__ uint64_t resolve_prefix(const Params &P, uint32_t tile, uint64_t agg, bool &timed_out)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) return 0;
     uint64_t G = 0;
-    uint32_t k = tile - 1;
+    int64_t base = (int64_t)tile - 1;
     uint64_t t0 = globaltimer();
     uint32_t spins = 0;
     for (;;) {
-        unsigned long long v = ld_acquire(&P.status[k]);
-        unsigned long long f = v & ~ST_VAL;
-        if (f == 0) {
+        // lane l covers tiles base - 8l - j, j = 0..7 (descending)
+        unsigned long long v[LB_PER_LANE];
+#pragma unroll
+        for (int j = 0; j < LB_PER_LANE; j++) {
+            const int64_t k = base - (int64_t)LB_PER_LANE * lane - j;
+            v[j] = k >= 0 ? ld_status(&P.status[k]) : ST_INCL;
+        }
+        int jstar = LB_PER_LANE;   // first inclusive word of this lane
+        bool zero_before = false;
+        unsigned long long lsum = 0;
+#pragma unroll
+        for (int j = 0; j < LB_PER_LANE; j++) {
+            if (jstar == LB_PER_LANE) {
+                const unsigned long long f = v[j] & ~ST_VAL;
+                if (f == 0) zero_before = true;
+                lsum += v[j] & ST_VAL;
+                if (f == ST_INCL) jstar = j;
+            }
+        }
+        const unsigned incl = __ballot_sync(0xffffffffu, jstar < LB_PER_LANE);
+        const unsigned zero = __ballot_sync(0xffffffffu, zero_before);
+        const unsigned upto = incl ? (incl & (0u - incl)) : 0u;            // lowest lane holding one
+        const unsigned lanes = incl ? ((upto - 1u) | upto) : 0xffffffffu;  // lanes to sum
+        if (zero & lanes) {
             if ((++spins & 15) == 0 && globaltimer() - t0 > P.timeout_ns) {
                 timed_out = true;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
             continue;
         }
-        G += v & ST_VAL;
-        if (f == ST_INCL) break;
-        k--;
+        unsigned long long x = ((lanes >> lane) & 1u) ? lsum : 0ull;
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        G += x;
+        if (incl) break;
+        base -= 32 * LB_PER_LANE;
     }
-    st_release(&P.status[tile], ST_INCL | (G + agg));
+    if (lane == 0) st_status(&P.status[tile], ST_INCL | (G + agg));
     return G;
+}
+
+// 4-bit mask of the certified bytes of a little-endian word.
+__device__ __forceinline__ uint32_t cut_mask4(const Env &E, uint32_t w)
+{
+    return (uint32_t)is_cut(E, w & 0xFFu) | ((uint32_t)is_cut(E, (w >> 8) & 0xFFu) << 1) |
+           ((uint32_t)is_cut(E, (w >> 16) & 0xFFu) << 2) | ((uint32_t)is_cut(E, w >> 24) << 3);
 }
 
 template <int FORM>
@@ -349,9 +511,8 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     const uint32_t sbase = smem_u32(smem);
     const uint32_t tbase = align_up(sbase, 512);
     uint8_t *misc = smem + L.misc;
-    const uint32_t misc_s = sbase + L.misc;
-    const uint32_t mbar[2] = {misc_s + M_MBAR, misc_s + M_MBAR + 8};
-    const uint32_t bufs[2] = {sbase + L.buf0, sbase + L.buf1};
+    const uint32_t mbar = sbase + L.misc + M_MBAR;
+    const uint32_t buf = sbase + L.buf;
 
     if (tbase + P.table_bytes > 65536u) {   // u16 row pointers must reach every row
         if (tid == 0) atomicOr(&P.res->error, ERR_SMEM);
@@ -380,45 +541,81 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     E.cmap_s = tbase + P.cmap_off;
     E.cert_s = tbase + P.cert_off;
     E.kcol2 = 2 * (P.ncols - 1);
+    E.buf = buf;
 
     volatile uint32_t *s_tile = reinterpret_cast<volatile uint32_t *>(misc + M_TILE);
+    volatile uint32_t *s_x = reinterpret_cast<volatile uint32_t *>(misc + M_X);
+    volatile uint32_t *s_flags = reinterpret_cast<volatile uint32_t *>(misc + M_FLAGS);
+    uint32_t *s_wmin = reinterpret_cast<uint32_t *>(misc + M_WMIN);
+    unsigned long long *s_G = reinterpret_cast<unsigned long long *>(misc + M_G);
+    unsigned long long *s_tot = reinterpret_cast<unsigned long long *>(misc + M_TOT);
+    unsigned long long *s_fpos = reinterpret_cast<unsigned long long *>(misc + M_FPOS);
+    unsigned long long *s_fidx = reinterpret_cast<unsigned long long *>(misc + M_FIDX);
+    volatile uint32_t *s_ptile = reinterpret_cast<volatile uint32_t *>(misc + M_PTILE);
+    unsigned long long *s_ptot = reinterpret_cast<unsigned long long *>(misc + M_PTOT);
+    unsigned long long *s_pfpos = reinterpret_cast<unsigned long long *>(misc + M_PFPOS);
+    unsigned long long *s_pfidx = reinterpret_cast<unsigned long long *>(misc + M_PFIDX);
+    unsigned long long *warp_tot = reinterpret_cast<unsigned long long *>(misc + M_WARP);
+    uint32_t *stage32 = reinterpret_cast<uint32_t *>(smem + L.stage);
+    const uint32_t col = sbase + L.slots + tid * 4;   // this thread's record column
+
     if (tid == 0) {
-        mbar_init(mbar[0], 1);
-        mbar_init(mbar[1], 1);
+        mbar_init(mbar, 1);
         fence_proxy_async();
+        *s_ptile = NONE32;
     }
     __syncthreads();
 
-    auto issue = [&](uint32_t tile, int which) {   // thread 0
+    auto issue = [&](uint32_t tile) {   // one thread
         uint64_t base = (uint64_t)tile * TILE;
         uint64_t avail = P.n - base;
         uint32_t len = (uint32_t)(avail < (uint64_t)BUF ? avail : (uint64_t)BUF) & ~15u;
         if (len) {
             fence_proxy_async();
-            tma_load(bufs[which], P.in + base, len, mbar[which]);
+            tma_load(buf, P.in + base, len, mbar);
         }
+    };
+    // Resolve the pending tile's output offset (warp 0), then write its
+    // staged kept tokens with coalesced stores (all threads).
+    auto flush_pending = [&]() {
+        const uint32_t pt = *s_ptile;
+        if (pt == NONE32) return;
+        if (wid == 0) {
+            bool to = false;
+            const uint64_t G = resolve_prefix(P, pt, *s_ptot, to);
+            if (lane == 0) {
+                if (to) atomicOr(&P.res->error, ERR_TIMEOUT);
+                *s_G = G;
+                if (*s_pfpos != NOPOS) {
+                    atomicMax(&P.res->inv_fail_pos, ~(unsigned long long)*s_pfpos);
+                    atomicMax(&P.res->inv_fail_tok, ~(unsigned long long)(G + *s_pfidx));
+                }
+            }
+        }
+        __syncthreads();
+        const uint64_t G = *s_G, tot = *s_ptot;
+        for (uint32_t i = tid; i < tot; i += NT) {
+            const uint64_t idx = G + i;
+            if (idx < P.cap) {
+                const uint32_t v = stage32[i];
+                P.out_kinds[idx] = (uint16_t)(v >> 20);
+                P.out_lens[idx] = v & 0xFFFFFu;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) *s_ptile = NONE32;
     };
 
     if (tid == 0) {
         uint32_t t = atomicAdd(P.tile_counter, 1u);
         s_tile[0] = t;
-        if (t < P.n_tiles && P.tma) issue(t, 0);
+        if (t < P.n_tiles && P.tma) issue(t);
     }
     __syncthreads();
     uint32_t tile = s_tile[0];
-    uint32_t parity[2] = {0, 0};
-    int cur = 0;
-    uint32_t *slots32 = reinterpret_cast<uint32_t *>(smem + L.slots);
-    uint32_t *stage32 = reinterpret_cast<uint32_t *>(smem + L.stage);
-    unsigned long long *warp_tot = reinterpret_cast<unsigned long long *>(misc + M_WARP);
+    uint32_t par = 0;
 
     while (tile < P.n_tiles) {
-        __syncthreads();   // everyone has read s_tile
-        if (tid == 0) {
-            uint32_t t = atomicAdd(P.tile_counter, 1u);
-            s_tile[0] = t;
-            if (t < P.n_tiles && P.tma) issue(t, cur ^ 1);
-        }
         const uint64_t tile_base = (uint64_t)tile * TILE;
         const uint64_t avail = P.n - tile_base;
         uint32_t staged;
@@ -426,101 +623,190 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         if (P.tma) {
             staged = (uint32_t)(avail < (uint64_t)BUF ? avail : (uint64_t)BUF) & ~15u;
             if (staged) {
-                bad = !mbar_wait(mbar[cur], parity[cur], P.timeout_ns);
-                parity[cur] ^= 1;
+                bad = !mbar_wait(mbar, par, P.timeout_ns);
+                par ^= 1;
             }
         } else {
             staged = (uint32_t)(avail < (uint64_t)BUF ? avail : (uint64_t)BUF);
-            uint8_t *b = smem + (bufs[cur] - sbase);
+            uint8_t *b = smem + L.buf;
             for (uint32_t i = tid; i < staged; i += NT) b[i] = P.in[tile_base + i];
         }
         if (__syncthreads_or(bad)) {
             if (tid == 0) atomicOr(&P.res->error, ERR_TIMEOUT);
             break;
         }
-        E.buf = bufs[cur];
         E.tile_base = tile_base;
         E.sm_end = tile_base + staged;
+        const uint32_t n_rel = avail < 0x7FFFFFFFull ? (uint32_t)avail : 0x7FFFFFFFu;
 
-        // (b) plan: first certified byte of this thread's segment
-        const uint64_t seg_start = tile_base + (uint64_t)tid * SEG;
-        const uint64_t seg_end = seg_start + SEG;
-        uint64_t start = NOPOS;
+        // (b) plan: the first certified byte of this thread's segment, tested
+        // a word at a time
+        const uint32_t seg0 = (uint32_t)tid * SEG;
+        uint32_t start = NONE32;
         if (tile == 0 && tid == 0) {
             start = 0;
-        } else {
-            uint64_t lim = seg_end < P.n ? seg_end : P.n;
-            for (uint64_t p = seg_start; p < lim; p++)
-                if (is_cut(E, byte_at(E, p))) { start = p; break; }
-        }
-        // (c) walk
-        SlotEmit se{smem_u32(slots32 + tid), 0, false};
-        uint64_t fail = NOPOS;
-        if (start != NOPOS) fail = walk<FORM>(E, start, seg_end, se);
-
-        // (d) CTA scan of kept-token counts
-        uint32_t x = se.count;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        const uint32_t lane_excl = x - se.count;
-        if (lane == 31) warp_tot[wid] = x;
-        const int any_ovf = __syncthreads_or(se.ovf);
-        const int any_fail = __syncthreads_or(fail != NOPOS);
-        if (tid == 0) {
-            unsigned long long acc = 0;
-            for (int w = 0; w < NT / 32; w++) {
-                unsigned long long t = warp_tot[w];
-                warp_tot[w] = acc;
-                acc += t;
+        } else if (seg0 + SEG <= staged) {
+            for (uint32_t k = 0; k < SEG / 4; k++) {
+                const uint32_t m = cut_mask4(E, lds_u32(buf + seg0 + 4 * k));
+                if (m) { start = seg0 + 4 * k + __ffs(m) - 1; break; }
             }
-            bool to = false;
-            uint64_t G = lookback(P, tile, acc, acc > 0 || any_fail, to);
-            if (to) atomicOr(&P.res->error, ERR_TIMEOUT);
-            if (acc) atomicAdd(&P.res->total, acc);
-            *reinterpret_cast<unsigned long long *>(misc + M_G) = G;
-            *reinterpret_cast<unsigned long long *>(misc + M_TOT) = acc;
+            if (start >= n_rel) start = NONE32;
+        } else {
+            const uint32_t lim = seg0 + SEG < n_rel ? seg0 + SEG : n_rel;
+            for (uint32_t p = seg0; p < lim; p++) {
+                uint32_t b = p < staged ? lds_u8(buf + p) : (uint32_t)__ldg(P.in + tile_base + p);
+                if (is_cut(E, b)) { start = p; break; }
+            }
         }
+        if (wid == NW - 1) {   // first cut at or past the tile end, within the staged halo
+            const uint32_t hl = staged < n_rel ? staged : n_rel;
+            uint32_t x = NONE32;
+            for (uint32_t b0 = TILE; b0 < hl; b0 += 32) {
+                const uint32_t p = b0 + lane;
+                const unsigned m = __ballot_sync(0xffffffffu, p < hl && is_cut(E, lds_u8(buf + p)));
+                if (m) { x = b0 + __ffs(m) - 1; break; }
+            }
+            if (x == NONE32 && hl >= n_rel) x = n_rel;
+            if (lane == 0) *s_x = x;
+        }
+        // next chunk start after this thread's: suffix minimum over the starts
+        uint32_t smin = start;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_down_sync(0xffffffffu, smin, o);
+            if (lane + o < 32) smin = min(smin, y);
+        }
+        uint32_t nxt = __shfl_down_sync(0xffffffffu, smin, 1);
+        if (lane == 31) nxt = NONE32;
+        if (lane == 0) s_wmin[wid] = smin;
         __syncthreads();
-        const uint64_t G = *reinterpret_cast<unsigned long long *>(misc + M_G);
-        const uint64_t cta_total = *reinterpret_cast<unsigned long long *>(misc + M_TOT);
-        const uint64_t my_off = warp_tot[wid] + lane_excl;   // within the tile
+        for (int w = wid + 1; w < NW && nxt == NONE32; w++) nxt = s_wmin[w];
+        if (nxt == NONE32) nxt = *s_x;   // may still be NONE32: the range leaves the halo
 
-        if (!any_ovf && cta_total <= (uint64_t)STAGE_CAP) {
-            for (uint32_t k = 0; k < se.count; k++) stage32[my_off + k] = slots32[k * NT + tid];
-            __syncthreads();
-            for (uint32_t i = tid; i < cta_total; i += NT) {
-                uint64_t idx = G + i;
-                if (idx < P.cap) {
-                    uint32_t v = stage32[i];
-                    P.out_kinds[idx] = (uint16_t)(v >> 20);
-                    P.out_lens[idx] = v & 0xFFFFFu;
+        // (c) walk
+        uint32_t cnt = 0, kept = 0;
+        uint64_t kept_generic = 0;
+        uint64_t fail = NOPOS;
+        bool generic = false;
+        const bool has = start != NONE32;
+        const bool eoi = nxt == n_rel;
+        const bool fast = has && nxt != NONE32 && (eoi ? n_rel <= staged : nxt < staged);
+        uint32_t f32 = 0;
+        const int st = lockstep_walk<FORM>(E, fast, start, fast ? nxt : 0u, eoi, col, cnt, f32);
+        if (fast && st == LS_FAIL) fail = tile_base + f32;
+        if (has && (!fast || st == LS_OVF)) {
+            generic = true;
+            CountEmit ce;
+            fail = walk<FORM>(E, tile_base + start, tile_base + seg0 + SEG, ce);
+            kept_generic = ce.count;
+        } else if (has) {
+            // kinds, discard filter and lengths of the recorded token ends,
+            // compacted in place in the column as kind << 20 | length
+            uint32_t prev = start;
+            for (uint32_t k = 0; k < cnt; k++) {
+                const uint32_t v = lds_u32(col + k * NT * 4);
+                const uint32_t pos = v & 0xFFFFu;
+                const uint32_t kw = kind_of<FORM>(E, v >> 16);
+                const uint32_t len = pos - prev;
+                prev = pos;
+                if (kw & KIND_KEEP) {
+                    if ((kw & 0x7FFFu) >= 4096u) generic = true;
+                    sts_u32(col + kept * NT * 4, ((kw & 0x7FFFu) << 20) | len);
+                    kept++;
                 }
             }
-        } else if (se.count) {
-            if (!se.ovf) {
-                for (uint32_t k = 0; k < se.count; k++) {
-                    uint64_t idx = G + my_off + k;
+            if (generic) kept_generic = kept;
+        }
+        const uint32_t count32 = generic ? 0u : kept;
+
+        // (d) CTA scan of kept-token counts
+        const uint64_t mycount = generic ? kept_generic : (uint64_t)kept;
+        uint64_t x = mycount;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint64_t lane_excl = x - mycount;
+        if (lane == 31) warp_tot[wid] = x;
+        if (tid == 0) *s_fpos = NOPOS;
+        const int any_gen = __syncthreads_or(generic);
+        if (tid == 0) {
+            unsigned long long run = 0;
+            for (int w = 0; w < NW; w++) {
+                unsigned long long t = warp_tot[w];
+                warp_tot[w] = run;
+                run += t;
+            }
+            *s_tot = run;
+            *s_flags = (any_gen || run > (unsigned long long)STAGE_CAP) ? 1u : 0u;
+            // publish this tile's aggregate at once
+            publish_aggregate(P, tile, run);
+            if (run) atomicAdd(&P.res->total, run);
+        }
+        __syncthreads();
+        const uint64_t my_off = warp_tot[wid] + lane_excl;   // within the tile
+        if (fail != NOPOS) {
+            atomicMin(s_fpos, (unsigned long long)fail);
+        }
+        __syncthreads();
+        if (fail != NOPOS && *s_fpos == fail) *s_fidx = my_off + mycount;
+        __syncthreads();
+
+        // the previous tile's output: its predecessors have had a whole walk
+        // to publish, so its look-back rarely waits
+        flush_pending();
+
+        const bool sync_tile = *s_flags != 0;
+        if (!sync_tile) {
+            // stage this tile's kept tokens; they are written after the next walk
+            for (uint32_t k = 0; k < count32; k++) stage32[my_off + k] = lds_u32(col + k * NT * 4);
+            if (tid == 0) {
+                *s_ptot = *s_tot;
+                *s_pfpos = *s_fpos;
+                *s_pfidx = *s_fidx;
+                *s_ptile = tile;
+            }
+        } else {
+            // rare: record or stage overflow -- resolve now and write directly
+            if (wid == 0) {
+                bool to = false;
+                const uint64_t G = resolve_prefix(P, tile, *s_tot, to);
+                if (lane == 0) {
+                    if (to) atomicOr(&P.res->error, ERR_TIMEOUT);
+                    *s_G = G;
+                    if (*s_fpos != NOPOS) {
+                        atomicMax(&P.res->inv_fail_pos, ~(unsigned long long)*s_fpos);
+                        atomicMax(&P.res->inv_fail_tok, ~(unsigned long long)(G + *s_fidx));
+                    }
+                }
+            }
+            __syncthreads();
+            const uint64_t G = *s_G;
+            if (!generic) {
+                for (uint32_t k = 0; k < count32; k++) {
+                    const uint64_t idx = G + my_off + k;
                     if (idx < P.cap) {
-                        uint32_t v = slots32[k * NT + tid];
+                        const uint32_t v = lds_u32(col + k * NT * 4);
                         P.out_kinds[idx] = (uint16_t)(v >> 20);
                         P.out_lens[idx] = v & 0xFFFFFu;
                     }
                 }
             } else {
                 DirectEmit de{P.out_kinds, P.out_lens, P.cap, G + my_off};
-                walk<FORM>(E, start, seg_end, de);
+                walk<FORM>(E, tile_base + start, tile_base + seg0 + SEG, de);
             }
         }
-        if (fail != NOPOS) {
-            atomicMax(&P.res->inv_fail_pos, ~(unsigned long long)fail);
-            atomicMax(&P.res->inv_fail_tok, ~(unsigned long long)(G + my_off + se.count));
+        __syncthreads();   // records, stage and the input buffer are free
+        if (tid == 0) {
+            // claim the next tile only now: a claimed tile is walked at once, so
+            // no successor's look-back waits behind this CTA's other work
+            const uint32_t t = atomicAdd(P.tile_counter, 1u);
+            s_tile[0] = t;
+            if (t < P.n_tiles && P.tma) issue(t);
         }
-        __syncthreads();   // slots, stage and this buffer are free again
+        __syncthreads();
         tile = s_tile[0];
-        cur ^= 1;
     }
+    flush_pending();
 }
 
 // ---------------------------------------------------------------------------

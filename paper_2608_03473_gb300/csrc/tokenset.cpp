@@ -151,18 +151,20 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
     for (uint32_t b = 0; b < 256; b++)
         if (bit(cutmask, b)) cut_c[t.byte_class[b]] = 1;
 
-    // E rows: one per distinct delta(q0, c)
+    // Row order: SLOW, R[0..S-1], START, E[...].  SLOW sits below P_flag and
+    // absorbs every byte, so a lane that falls into it records nothing more
+    // and can be sent to the replay lazily.
+    const uint32_t SLOW = 0, R0 = 1, START = S + 1;
     std::vector<uint32_t> e_row(S, LX_NONE);
     std::vector<uint32_t> e_state;
     for (uint32_t c = 0; c < C; c++) {
         uint32_t d = nx(c, q0);
         if (d != LX_NONE && e_row[d] == LX_NONE) {
-            e_row[d] = S + 1 + (uint32_t)e_state.size();
+            e_row[d] = S + 2 + (uint32_t)e_state.size();
             e_state.push_back(d);
         }
     }
-    const uint32_t START = S, SLOW = S + 1 + (uint32_t)e_state.size();
-    const uint32_t R = SLOW + 1;
+    const uint32_t R = S + 2 + (uint32_t)e_state.size();
 
     std::vector<uint32_t> tgt((size_t)R * C);
     auto state_row = [&](uint32_t row, uint32_t s) {
@@ -171,19 +173,19 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
             bool acc = t.accept[s] != LX_NO_KIND;
             uint32_t r;
             if (cut_c[c]) r = acc ? e_row[d0] : SLOW;
-            else if (d != LX_NONE) r = d;
+            else if (d != LX_NONE) r = R0 + d;
             else if (acc && d0 != LX_NONE) r = e_row[d0];
             else r = SLOW;
             tgt[(size_t)row * C + c] = r;
         }
     };
-    for (uint32_t s = 0; s < S; s++) state_row(s, s);
+    for (uint32_t s = 0; s < S; s++) state_row(R0 + s, s);
     for (uint32_t c = 0; c < C; c++) {
         uint32_t d0 = nx(c, q0);
-        tgt[(size_t)START * C + c] = d0 != LX_NONE ? d0 : SLOW;
+        tgt[(size_t)START * C + c] = d0 != LX_NONE ? R0 + d0 : SLOW;
         tgt[(size_t)SLOW * C + c] = SLOW;
     }
-    for (uint32_t k = 0; k < e_state.size(); k++) state_row(S + 1 + k, e_state[k]);
+    for (uint32_t k = 0; k < e_state.size(); k++) state_row(S + 2 + k, e_state[k]);
 
     std::vector<uint16_t> kind(R, (uint16_t)lx::KIND_NONE);
     auto kind_word = [&](uint32_t s) -> uint16_t {
@@ -192,8 +194,8 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
         bool keep = (mode == LX_FULL_EXACT) || !t.discard[a];
         return (uint16_t)(a | (keep ? lx::KIND_KEEP : 0));
     };
-    for (uint32_t s = 0; s < S; s++) kind[s] = kind_word(s);
-    for (uint32_t k = 0; k < e_state.size(); k++) kind[S + 1 + k] = kind_word(e_state[k]);
+    for (uint32_t s = 0; s < S; s++) kind[R0 + s] = kind_word(s);
+    for (uint32_t k = 0; k < e_state.size(); k++) kind[S + 2 + k] = kind_word(e_state[k]);
 
     ht = HostTable();
     ht.n_rows = R;
@@ -204,14 +206,14 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
         ht.ncols = 256;
         ht.row_bytes = 512;
         for (uint32_t r = 0; r < R; r++) P[r] = 512 * r + 4 * (r & 31);
-        ht.p_flag = 512 * (S + 1);
-        ht.p_slow = 512 * SLOW;
+        ht.p_flag = 512 * (S + 2);
+        ht.p_slow = P[SLOW];
     } else {
         ht.form = lx::FORM_CLASS;
         ht.ncols = C + 1;
         ht.row_bytes = 2 * (C + 1);
         for (uint32_t r = 0; r < R; r++) P[r] = ht.row_bytes * r;
-        ht.p_flag = P[S + 1];
+        ht.p_flag = ht.row_bytes * (S + 2);
         ht.p_slow = P[SLOW];
     }
     ht.p_start = P[START];

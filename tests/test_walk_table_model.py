@@ -61,10 +61,10 @@ class TableModel:
             else:
                 b = w[p]
                 e2 = self.step(e, b)
-                if e2 >= P_flag:
-                    if e2 >= P_slow:
-                        slow = True
-                    else:
+                if e2 == P_slow:
+                    slow = True
+                elif e2 >= P_flag:
+                    if True:
                         self.emit(out, self.kind(e), p - tok)
                         tok = p
                         if p >= seg_end and self.cert[b]:
