@@ -189,6 +189,44 @@ int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_
                 uint16_t *h_kinds, uint32_t *h_lens, uint64_t capacity, uint64_t *n_tokens,
                 uint64_t *consumed, void *stream);
 
+/*
+ * lx_lex_noalloc -- lx_lex for callers that cannot allocate memory.
+ *
+ * The paper has no counterpart to this entry point; it exists for library
+ * users, not for the method.  Some callers must not allocate device or
+ * pinned host memory on the lexing path: a service that hands all device
+ * memory to its own allocator under a fixed budget, or latency-sensitive
+ * code for which cudaMalloc (which can synchronize the device) is not
+ * acceptable.  lx_lex needs a context whose scratch grows with cudaMalloc and
+ * uploads each token set's tables to device memory on first use; this entry
+ * point does neither.  It calls no cudaMalloc, cudaFree, cudaMallocHost or
+ * other allocating routine.
+ *
+ * Scratch lives in one fixed array of LX_NOALLOC_SCRATCH_BYTES of device
+ * memory, defined at file scope in the library, which every GPU that loads
+ * the library holds until the process exits.  It holds the token set's walk
+ * tables (copied in on each call), the result record, the tile counter and
+ * one status word per 17408-byte tile; the parts that must start at zero are
+ * cleared on each call.  Hence n must not exceed LX_NOALLOC_MAX_INPUT
+ * (larger inputs return LX_E_INVAL before any GPU work).
+ *
+ * The first call on a device does a one-time set-up with that device
+ * current: it looks up the array's device address and sets the kernel's
+ * shared-memory attribute.  Make that first call before any stream capture.
+ * Every call uses the same array and leaves the last call's contents in it,
+ * so calls that overlap on the GPU (for example on two streams at once, or
+ * from two host threads) race and must be serialized by the caller.
+ *
+ * Arguments, results and other errors are those of lx_lex (without a
+ * context; the device-wait bound is the default 20 s).  The call
+ * synchronizes `stream` once to read back the 32-byte result record.
+ */
+#define LX_NOALLOC_SCRATCH_BYTES (512u * 1024u)
+/* (LX_NOALLOC_SCRATCH_BYTES - 64 KiB of tables - 64 B) / 8 status words, 17408 bytes per tile */
+#define LX_NOALLOC_MAX_INPUT (57336ull * 17408ull)
+int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                   uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed, void *stream);
+
 /* Message for a status code (static string). */
 const char *lx_strerror(int code);
 

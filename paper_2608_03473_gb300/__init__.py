@@ -48,7 +48,7 @@ LX_FILTERED_MODULO = 2
 EXPORTED = (
     "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
-    "lx_lex", "lx_lex_host",
+    "lx_lex", "lx_lex_host", "lx_lex_noalloc",
     "lx_strerror",
 )
 
@@ -95,6 +95,7 @@ def load_library(path: Optional[str] = None):
             "lx_ctx_last_kernel_ms": (i32, [vp, vp]),
             "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_host": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
+            "lx_lex_noalloc": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_strerror": (ctypes.c_char_p, [i32]),
         }
         for name, (res, args) in sig.items():
@@ -258,4 +259,23 @@ def lx_lex_host(ctx: Ctx, ts: Tokenset, h_in, mode: int, h_kinds, h_lens, n: Opt
     nt, con = ctypes.c_uint64(), ctypes.c_uint64()
     rc = lib.lx_lex_host(ctx.handle, ts.handle, ptr(h_in), n, int(mode), ptr(h_kinds), ptr(h_lens), cap,
                          ctypes.byref(nt), ctypes.byref(con), _stream_handle(stream))
+    return rc, nt.value, con.value
+
+
+LX_NOALLOC_SCRATCH_BYTES = 512 * 1024
+LX_NOALLOC_MAX_INPUT = 57336 * 17408
+
+
+def lx_lex_noalloc(ts: Tokenset, d_in, mode: int, d_kinds, d_lens, n: Optional[int] = None,
+                   capacity: Optional[int] = None, stream=None) -> Tuple[int, int, int]:
+    """``lx_lex`` without any allocation: for callers that may not allocate
+    device or pinned memory while lexing (fixed-budget allocators,
+    latency-sensitive code).  Uses one fixed device scratch array shared by
+    every call, so overlapping calls race.  Returns (status, n_tokens, consumed)."""
+    lib = load_library()
+    n = d_in.numel() if n is None else int(n)
+    cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
+    nt, con = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib.lx_lex_noalloc(ts.handle, d_in.data_ptr(), n, int(mode), d_kinds.data_ptr(), d_lens.data_ptr(), cap,
+                            ctypes.byref(nt), ctypes.byref(con), _stream_handle(stream))
     return rc, nt.value, con.value

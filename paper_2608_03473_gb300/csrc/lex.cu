@@ -1104,3 +1104,133 @@ extern "C" const char *lx_strerror(int code)
     default: return "unknown error";
     }
 }
+
+// ---------------------------------------------------------------------------
+// lx_lex_noalloc: the same tile kernel, with every piece of scratch in one
+// fixed device array instead of context allocations.
+// ---------------------------------------------------------------------------
+namespace lx {
+
+constexpr size_t NA_TABLE_BYTES = 64 * 1024;            // walk-table blob of one mode
+constexpr size_t NA_RESULT = NA_TABLE_BYTES;            // Result, then the tile counter
+constexpr size_t NA_STATUS = NA_TABLE_BYTES + 64;       // one u64 status word per tile
+constexpr uint64_t NA_MAX_TILES = (LX_NOALLOC_SCRATCH_BYTES - NA_STATUS) / 8;
+static_assert(NA_MAX_TILES * TILE == LX_NOALLOC_MAX_INPUT, "LX_NOALLOC_MAX_INPUT out of date");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LX_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *scratch = nullptr;   // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+};
+static std::mutex g_noalloc_mu;
+static NoallocDevice g_noalloc_dev[NA_MAX_DEVICES];
+
+// One-time set-up on the current device: the host-side name of the array is
+// not a device address, so ask the runtime for it.
+static int noalloc_setup(int dev, NoallocDevice &d)
+{
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (d.ready) return LX_OK;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return LX_E_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LX_E_CUDA;
+    if (cudaFuncSetAttribute(lex_tiles<FORM_BYTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(lex_tiles<FORM_CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess)
+        return LX_E_CUDA;
+    d.scratch = static_cast<unsigned char *>(ptr);
+    d.num_sms = sms;
+    d.ready = true;
+    return LX_OK;
+}
+
+}  // namespace lx
+
+extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                              uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed,
+                              void *stream)
+{
+    if (!ts || !n_tokens || !consumed) return LX_E_INVAL;
+    if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
+    if (n && !d_in) return LX_E_INVAL;
+    if (capacity && (!d_kinds || !d_lens)) return LX_E_INVAL;
+    if (n > LX_NOALLOC_MAX_INPUT) return LX_E_INVAL;
+    const HostTable &h = ts->tab[mode];
+    if (h.status != LX_OK) return h.status;
+    if (h.blob.size() > NA_TABLE_BYTES) return LX_E_TOOBIG;
+    if (n == 0) {
+        *n_tokens = 0;
+        *consumed = 0;
+        return LX_OK;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return LX_E_CUDA;
+    NoallocDevice &d = g_noalloc_dev[dev];
+    int rc = noalloc_setup(dev, d);
+    if (rc != LX_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    const uint32_t n_tiles = (uint32_t)((n + TILE - 1) / TILE);
+    unsigned char *scr = d.scratch;
+    // zero the result record, the tile counter and this call's status words;
+    // bring in this token set's tables for `mode`
+    rc = cuda_err(cudaMemsetAsync(scr + NA_RESULT, 0, 64 + 8 * (size_t)n_tiles, st));
+    if (rc == LX_OK)
+        rc = cuda_err(cudaMemcpyAsync(scr, h.blob.data(), h.blob.size(), cudaMemcpyHostToDevice, st));
+    if (rc != LX_OK) return rc;
+
+    Params P;
+    P.in = d_in;
+    P.n = n;
+    P.blob = scr;
+    P.blob_bytes = (uint32_t)h.blob.size();
+    P.table_bytes = h.table_bytes;
+    P.kind_off = h.kind_off;
+    P.cmap_off = h.cmap_off;
+    P.cert_off = h.cert_off;
+    P.ncols = h.ncols;
+    P.p_start = h.p_start;
+    P.p_flag = h.p_flag;
+    P.p_slow = h.p_slow;
+    P.out_kinds = d_kinds;
+    P.out_lens = d_lens;
+    P.cap = capacity;
+    P.res = reinterpret_cast<Result *>(scr + NA_RESULT);
+    P.tile_counter = reinterpret_cast<unsigned int *>(scr + NA_RESULT + 32);
+    P.status = reinterpret_cast<unsigned long long *>(scr + NA_STATUS);
+    P.n_tiles = n_tiles;
+    P.tma = ((reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1 : 0;
+    P.timeout_ns = 20ull * 1000 * 1000 * 1000;
+
+    const Layout L = make_layout(P.blob_bytes);
+    int occ = 0;
+    cudaError_t e = h.form == FORM_BYTE
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lex_tiles<FORM_BYTE>, NT, L.total)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lex_tiles<FORM_CLASS>, NT, L.total);
+    if (e != cudaSuccess) return LX_E_CUDA;
+    if (occ < 1) occ = 1;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(n_tiles, (uint64_t)occ * d.num_sms);
+    if (h.form == FORM_BYTE) lex_tiles<FORM_BYTE><<<grid, NT, L.total, st>>>(P);
+    else lex_tiles<FORM_CLASS><<<grid, NT, L.total, st>>>(P);
+    rc = cuda_err(cudaGetLastError());
+    if (rc != LX_OK) return rc;
+    Result r;
+    rc = cuda_err(cudaMemcpyAsync(&r, P.res, sizeof(Result), cudaMemcpyDeviceToHost, st));
+    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(st));
+    if (rc != LX_OK) return rc;
+    if (r.error & ERR_TIMEOUT) return LX_E_TIMEOUT;
+    if (r.error & ERR_SMEM) return LX_E_TOOBIG;
+    uint64_t tokens = r.total, con = n;
+    if (r.inv_fail_pos) {
+        con = ~r.inv_fail_pos;
+        tokens = ~r.inv_fail_tok;
+    }
+    *n_tokens = tokens;
+    *consumed = con;
+    return tokens > capacity ? LX_E_CAPACITY : LX_OK;
+}
