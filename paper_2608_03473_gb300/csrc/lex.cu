@@ -327,6 +327,83 @@ __device__ uint64_t walk(const Env &E, uint64_t start, uint64_t seg_end, Emit &e
     }
 }
 
+// One lockstep iteration of a lane: up to four byte steps from the word `w`
+// (bytes base .. base+3, the ones in `amask`), written as branch-free,
+// predicated PTX.  The loop-carried chain per byte is only the row address
+// (one LOP3 or LEA) and the shared-memory load of the next row; the token-end
+// test, the record packing (PRMT) and its store hang off that chain:
+//   a_k  = e_k ^ ((w >> 8k) << 1 & 0x1FE)        (byte form)
+//   a_k  = e_k + 2 * class(byte k)                (class form, class loaded off-chain)
+//   e_k+1 = amask_k ? [a_k] : e_k
+//   if amask_k and e_k+1 >= P_flag: record (e_k << 16 | base + k); sp += 4 NT
+#define LX_BIT(K) LX_BIT_##K
+#define LX_BIT_0 "1"
+#define LX_BIT_1 "2"
+#define LX_BIT_2 "4"
+#define LX_BIT_3 "8"
+template <int FORM>
+__device__ __forceinline__ void walk_word(const Env &E, uint32_t &e, uint32_t &sp, uint32_t w, uint32_t amask,
+                                          uint32_t base)
+{
+    const uint32_t P_flag = E.P_flag;
+    if (FORM == FORM_BYTE) {
+#define LX_PSTEP(K, XOP)                                           \
+        "and.b32 t, %3, " LX_BIT(K) ";\n\t"                           \
+        "setp.ne.u32 pa, t, 0;\n\t"                                \
+        XOP                                                        \
+        "and.b32 x, x, 0x1FE;\n\t"                                 \
+        "xor.b32 a, %0, x;\n\t"                                    \
+        "mov.b32 e2, %0;\n\t"                                      \
+        "@pa ld.shared.u16 e2, [a];\n\t"                           \
+        "setp.ge.and.u32 pf, e2, %4, pa;\n\t"                      \
+        "add.u32 t, %5, " #K ";\n\t"                               \
+        "prmt.b32 v, t, %0, 0x5410;\n\t"                           \
+        "@pf st.shared.u32 [%1], v;\n\t"                           \
+        "@pf add.u32 %1, %1, %6;\n\t"                              \
+        "mov.b32 %0, e2;\n\t"
+        asm volatile(
+            "{\n\t.reg .pred pa, pf;\n\t.reg .b32 t, x, a, e2, v;\n\t"
+            LX_PSTEP(0, "shl.b32 x, %2, 1;\n\t")
+            LX_PSTEP(1, "shr.b32 x, %2, 7;\n\t")
+            LX_PSTEP(2, "shr.b32 x, %2, 15;\n\t")
+            LX_PSTEP(3, "shr.b32 x, %2, 23;\n\t")
+            "}"
+            : "+r"(e), "+r"(sp)
+            : "r"(w), "r"(amask), "r"(P_flag), "r"(base), "n"(NT * 4)
+            : "memory");
+#undef LX_PSTEP
+    } else {
+        const uint32_t cm = E.cmap_s;
+#define LX_CSTEP(K, SH)                                            \
+        "and.b32 t, %3, " LX_BIT(K) ";\n\t"                           \
+        "setp.ne.u32 pa, t, 0;\n\t"                                \
+        "bfe.u32 x, %2, " #SH ", 8;\n\t"                           \
+        "add.u32 x, x, %7;\n\t"                                    \
+        "ld.shared.u8 c, [x];\n\t"                                 \
+        "shl.b32 c, c, 1;\n\t"                                     \
+        "add.u32 a, %0, c;\n\t"                                    \
+        "mov.b32 e2, %0;\n\t"                                      \
+        "@pa ld.shared.u16 e2, [a];\n\t"                           \
+        "setp.ge.and.u32 pf, e2, %4, pa;\n\t"                      \
+        "add.u32 t, %5, " #K ";\n\t"                               \
+        "prmt.b32 v, t, %0, 0x5410;\n\t"                           \
+        "@pf st.shared.u32 [%1], v;\n\t"                           \
+        "@pf add.u32 %1, %1, %6;\n\t"                              \
+        "mov.b32 %0, e2;\n\t"
+        asm volatile(
+            "{\n\t.reg .pred pa, pf;\n\t.reg .b32 t, x, a, c, e2, v;\n\t"
+            LX_CSTEP(0, 0)
+            LX_CSTEP(1, 8)
+            LX_CSTEP(2, 16)
+            LX_CSTEP(3, 24)
+            "}"
+            : "+r"(e), "+r"(sp)
+            : "r"(w), "r"(amask), "r"(P_flag), "r"(base), "n"(NT * 4), "r"(cm)
+            : "memory");
+#undef LX_CSTEP
+    }
+}
+
 // ---- lockstep walker (staged bytes only, 32-bit offsets) ----
 enum { LS_WALK = 0, LS_SLOW = 1, LS_EOI = 2, LS_DONE = 3, LS_FAIL = 4, LS_OVF = 5 };
 
@@ -360,21 +437,7 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
                     const uint32_t k0 = p & 3u;
                     const uint32_t kend = lim - base < 4u ? lim - base : 4u;
                     const uint32_t amask = (0xFu << k0) & (0xFu >> (4u - kend));
-                    uint32_t e2;
-#define LX_STEP(K)                                         \
-    if (amask & (1u << K)) {                               \
-        e2 = step_w<FORM, K>(E, e, w);                     \
-        if (e2 >= P_flag) {                                \
-            sts_u32(sp, (e << 16) | (base + K));           \
-            sp += NT * 4;                                  \
-        }                                                  \
-        e = e2;                                            \
-    }
-                    LX_STEP(0)
-                    LX_STEP(1)
-                    LX_STEP(2)
-                    LX_STEP(3)
-#undef LX_STEP
+                    walk_word<FORM>(E, e, sp, w, amask, base);
                     p = base + kend;
                     if (e == P_slow) st = LS_SLOW;
                     else if (p >= lim) st = eoi ? LS_EOI : LS_DONE;
