@@ -115,10 +115,10 @@ int lx_tokenset_info(const lx_tokenset *ts, int mode, uint32_t *n_states, uint32
 /*
  * lx_tokenset_table -- the packed shared-memory walk table built for `mode`
  * (for inspection and host-side tests).  Copies min(cap, size) bytes of the
- * blob to `out` (host, may be NULL) and fills meta[10] (host, may be NULL):
+ * blob to `out` (host, may be NULL) and fills the first meta_len (<= 12)
+ * entries of meta (host, may be NULL):
  *   { blob bytes, table_form, n_rows, ncols, row_bytes, table_bytes,
- *     p_start, p_flag, p_slow, kind_off | cmap_off << 16 } and meta[10] =
- *   cert_off when the array holds 11 entries (pass meta_len).
+ *     p_start, p_flag, p_slow, kind_off | cmap_off << 16, cert_off, p_pre }.
  * Row pointers in the blob are offsets from the start of the blob.
  */
 int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,

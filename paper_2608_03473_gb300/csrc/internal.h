@@ -19,7 +19,9 @@ namespace lx {
 // previous token ended just before the current byte and the new token moved
 // q0 -> q' on it; SLOW means "the fast loop cannot decide" (backtrack to the
 // last accepting position, or fail) and absorbs every byte.  Rows are ordered
-//     SLOW, R[0..S-1], START, E[...]
+//     SLOW, R[0..S-1], START, PRE, E[...]
+// (PRE lets a lane begin at the word-aligned byte before its chunk start: it
+// absorbs bytes outside the cut set and on a cut byte moves as START does),
 // so "a token ended here" is one comparison of the row pointer with P_flag
 // and "take the slow path" one equality with P_slow.  A table entry is the
 // 16-bit shared-memory address of the target row (relative offsets here; the
@@ -53,7 +55,7 @@ struct HostTable {
     uint32_t ncols = 0;          // 256 (byte form) or C + 1 (class form)
     uint32_t row_bytes = 0;
     uint32_t table_bytes = 0;    // bytes of row entries
-    uint32_t p_start = 0, p_flag = 0, p_slow = 0;   // relative row pointers
+    uint32_t p_start = 0, p_flag = 0, p_slow = 0, p_pre = 0;   // relative row pointers
     uint32_t kind_off = 0;       // byte form: u16 kind word per row
     uint32_t cmap_off = 0;       // class form: u8 class per byte
     uint32_t cert_off = 0;       // u8 per byte: 1 = cut byte in this mode

@@ -65,7 +65,7 @@ struct Params {
     const uint8_t *blob;
     uint32_t blob_bytes, table_bytes, kind_off, cmap_off, cert_off;
     uint32_t ncols;
-    uint32_t p_start, p_flag, p_slow;
+    uint32_t p_start, p_flag, p_slow, p_pre;
     uint16_t *out_kinds;
     uint32_t *out_lens;
     uint64_t cap;
@@ -208,7 +208,7 @@ struct Env {
     uint64_t sm_end;       // input offset one past the last staged byte
     const uint8_t *in;
     uint64_t n;
-    uint32_t P_start, P_flag, P_slow;
+    uint32_t P_start, P_flag, P_slow, P_pre;
     uint32_t tbase, kind_s, cmap_s, cert_s, kcol2;
 };
 
@@ -327,136 +327,150 @@ __device__ uint64_t walk(const Env &E, uint64_t start, uint64_t seg_end, Emit &e
     }
 }
 
-// One lockstep iteration of a lane: up to four byte steps from the word `w`
-// (bytes base .. base+3, the ones in `amask`), written as branch-free,
-// predicated PTX.  The loop-carried chain per byte is only the row address
-// (one LOP3 or LEA) and the shared-memory load of the next row; the token-end
-// test, the record packing (PRMT) and its store hang off that chain:
-//   a_k  = e_k ^ ((w >> 8k) << 1 & 0x1FE)        (byte form)
-//   a_k  = e_k + 2 * class(byte k)                (class form, class loaded off-chain)
-//   e_k+1 = amask_k ? [a_k] : e_k
-//   if amask_k and e_k+1 >= P_flag: record (e_k << 16 | base + k); sp += 4 NT
-#define LX_BIT(K) LX_BIT_##K
-#define LX_BIT_0 "1"
-#define LX_BIT_1 "2"
-#define LX_BIT_2 "4"
-#define LX_BIT_3 "8"
+// One lockstep iteration of a lane: four byte steps over the word `w` (bytes
+// base .. base+3), as branch-free PTX.  The loop-carried chain per byte is
+// only the row address (one LOP3 or LEA) and the shared-memory load of the
+// next row; the token-end test, the record packing (PRMT) and its predicated
+// store hang off that chain:
+//   a_k   = e_k ^ ((w >> 8k) << 1 & 0x1FE)       (byte form)
+//   a_k   = e_k + 2 * class(byte k)               (class form, class loaded off-chain)
+//   e_k+1 = [a_k]
+//   if e_k+1 >= P_flag: record (e_k << 16 | base + k); sp += 4 NT
 template <int FORM>
-__device__ __forceinline__ void walk_word(const Env &E, uint32_t &e, uint32_t &sp, uint32_t w, uint32_t amask,
-                                          uint32_t base)
+__device__ __forceinline__ void walk_word(const Env &E, uint32_t &e, uint32_t &sp, uint32_t w, uint32_t base)
 {
     const uint32_t P_flag = E.P_flag;
     if (FORM == FORM_BYTE) {
 #define LX_PSTEP(K, XOP)                                           \
-        "and.b32 t, %3, " LX_BIT(K) ";\n\t"                           \
-        "setp.ne.u32 pa, t, 0;\n\t"                                \
         XOP                                                        \
         "and.b32 x, x, 0x1FE;\n\t"                                 \
         "xor.b32 a, %0, x;\n\t"                                    \
-        "mov.b32 e2, %0;\n\t"                                      \
-        "@pa ld.shared.u16 e2, [a];\n\t"                           \
-        "setp.ge.and.u32 pf, e2, %4, pa;\n\t"                      \
-        "add.u32 t, %5, " #K ";\n\t"                               \
+        "ld.shared.u16 e2, [a];\n\t"                               \
+        "setp.ge.u32 pf, e2, %3;\n\t"                              \
+        "add.u32 t, %4, " #K ";\n\t"                               \
         "prmt.b32 v, t, %0, 0x5410;\n\t"                           \
         "@pf st.shared.u32 [%1], v;\n\t"                           \
-        "@pf add.u32 %1, %1, %6;\n\t"                              \
+        "@pf add.u32 %1, %1, %5;\n\t"                              \
         "mov.b32 %0, e2;\n\t"
         asm volatile(
-            "{\n\t.reg .pred pa, pf;\n\t.reg .b32 t, x, a, e2, v;\n\t"
+            "{\n\t.reg .pred pf;\n\t.reg .b32 t, x, a, e2, v;\n\t"
             LX_PSTEP(0, "shl.b32 x, %2, 1;\n\t")
             LX_PSTEP(1, "shr.b32 x, %2, 7;\n\t")
             LX_PSTEP(2, "shr.b32 x, %2, 15;\n\t")
             LX_PSTEP(3, "shr.b32 x, %2, 23;\n\t")
             "}"
             : "+r"(e), "+r"(sp)
-            : "r"(w), "r"(amask), "r"(P_flag), "r"(base), "n"(NT * 4)
+            : "r"(w), "r"(P_flag), "r"(base), "n"(NT * 4)
             : "memory");
 #undef LX_PSTEP
     } else {
         const uint32_t cm = E.cmap_s;
 #define LX_CSTEP(K, SH)                                            \
-        "and.b32 t, %3, " LX_BIT(K) ";\n\t"                           \
-        "setp.ne.u32 pa, t, 0;\n\t"                                \
         "bfe.u32 x, %2, " #SH ", 8;\n\t"                           \
-        "add.u32 x, x, %7;\n\t"                                    \
+        "add.u32 x, x, %6;\n\t"                                    \
         "ld.shared.u8 c, [x];\n\t"                                 \
         "shl.b32 c, c, 1;\n\t"                                     \
         "add.u32 a, %0, c;\n\t"                                    \
-        "mov.b32 e2, %0;\n\t"                                      \
-        "@pa ld.shared.u16 e2, [a];\n\t"                           \
-        "setp.ge.and.u32 pf, e2, %4, pa;\n\t"                      \
-        "add.u32 t, %5, " #K ";\n\t"                               \
+        "ld.shared.u16 e2, [a];\n\t"                               \
+        "setp.ge.u32 pf, e2, %3;\n\t"                              \
+        "add.u32 t, %4, " #K ";\n\t"                               \
         "prmt.b32 v, t, %0, 0x5410;\n\t"                           \
         "@pf st.shared.u32 [%1], v;\n\t"                           \
-        "@pf add.u32 %1, %1, %6;\n\t"                              \
+        "@pf add.u32 %1, %1, %5;\n\t"                              \
         "mov.b32 %0, e2;\n\t"
         asm volatile(
-            "{\n\t.reg .pred pa, pf;\n\t.reg .b32 t, x, a, c, e2, v;\n\t"
+            "{\n\t.reg .pred pf;\n\t.reg .b32 t, x, a, c, e2, v;\n\t"
             LX_CSTEP(0, 0)
             LX_CSTEP(1, 8)
             LX_CSTEP(2, 16)
             LX_CSTEP(3, 24)
             "}"
             : "+r"(e), "+r"(sp)
-            : "r"(w), "r"(amask), "r"(P_flag), "r"(base), "n"(NT * 4), "r"(cm)
+            : "r"(w), "r"(P_flag), "r"(base), "n"(NT * 4), "r"(cm)
             : "memory");
 #undef LX_CSTEP
     }
 }
 
 // ---- lockstep walker (staged bytes only, 32-bit offsets) ----
-enum { LS_WALK = 0, LS_SLOW = 1, LS_EOI = 2, LS_DONE = 3, LS_FAIL = 4, LS_OVF = 5 };
+enum { LS_WALK = 0, LS_SLOW = 1, LS_END = 2, LS_TAIL = 3, LS_DONE = 4, LS_FAIL = 5, LS_OVF = 6 };
 
-// All lanes of a warp walk their ranges in lockstep, up to four bytes per
-// lane per iteration from one shared-memory word, with every per-byte
-// decision predicated so that the warp stays converged.  A lane's range is
-// [start, end]: `end` is the next chunk start (a certified byte, whose step
-// ends the last token) or, with `eoi`, the end of the input.  Every token
-// end is recorded as (row before the byte << 16 | end offset) in the lane's
-// record column `col` (stride NT words); kinds and the discard filter are
-// applied afterwards.  A lane that falls into the absorbing SLOW row leaves
-// the lockstep loop and replays its current token from q0 to its last
-// accepting position (longest match with backtracking), then rejoins.
+// All lanes of a warp walk their ranges in lockstep, four bytes of one
+// aligned shared-memory word per lane per iteration, with no per-byte
+// predicate: a lane whose chunk starts inside a word begins at the word in
+// the PRE row (the bytes between the word start and the chunk start are not
+// certified, PRE absorbs them), and a lane runs over the word holding its
+// range end, whose recorded token ends past that cut are dropped afterwards.
+// A lane's range is [start, end]: `end` is the next chunk start (a certified
+// byte, whose step ends the last token) or, with `eoi`, the end of the
+// input.  Every token end is recorded as (row before the byte << 16 | end
+// offset) in the lane's record column `col` (stride NT words).  A lane that
+// falls into the absorbing SLOW row leaves the lockstep loop and replays its
+// current token from q0 to its last accepting position (longest match with
+// backtracking), then rejoins; a restart inside a word, and the last partial
+// word of the input, are stepped byte by byte.
 template <int FORM>
 __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t start, uint32_t end, bool eoi,
                                              uint32_t col, uint32_t &cnt, uint32_t &fail)
 {
     const uint32_t P_flag = E.P_flag, P_slow = E.P_slow;
     const uint32_t col_end = col + (uint32_t)KS * NT * 4;
-    const uint32_t lim = eoi ? end : end + 1;
-    uint32_t e = E.P_start, p = start, rst = start, sp = col, sp0 = col;
-    int st = has ? LS_WALK : LS_DONE;
+    const uint32_t lim = eoi ? end : end + 1;             // bytes [start, lim) are stepped
+    const uint32_t mlim = eoi ? (lim & ~3u) : lim;        // whole words while p < mlim
+    uint32_t p = start & ~3u;
+    uint32_t e = (start & 3u) ? E.P_pre : E.P_start;
+    uint32_t rst = start, sp = col, sp0 = col;
+    int st = !has ? LS_DONE : (p < mlim ? LS_WALK : LS_TAIL);
+
+    // byte-by-byte steps over [p, stop) with the same recording rule
+    auto scalar = [&](uint32_t stop) {
+        for (; p < stop && e != P_slow; p++) {
+            const uint32_t e2 = step<FORM>(E, e, lds_u8(E.buf + p));
+            if (e2 >= P_flag) {
+                sts_u32(sp, (e << 16) | p);
+                sp += NT * 4;
+            }
+            e = e2;
+        }
+    };
     for (;;) {
         while (__any_sync(0xffffffffu, st == LS_WALK)) {
             if (st == LS_WALK) {
                 if (sp + 4 * NT * 4 > col_end) {
                     st = LS_OVF;
                 } else {
-                    const uint32_t base = p & ~3u;
-                    const uint32_t w = lds_u32(E.buf + base);
-                    const uint32_t k0 = p & 3u;
-                    const uint32_t kend = lim - base < 4u ? lim - base : 4u;
-                    const uint32_t amask = (0xFu << k0) & (0xFu >> (4u - kend));
-                    walk_word<FORM>(E, e, sp, w, amask, base);
-                    p = base + kend;
-                    if (e == P_slow) st = LS_SLOW;
-                    else if (p >= lim) st = eoi ? LS_EOI : LS_DONE;
+                    walk_word<FORM>(E, e, sp, lds_u32(E.buf + p), p);
+                    p += 4;
+                    if (p >= mlim) st = eoi ? (e == P_slow ? LS_SLOW : LS_TAIL) : LS_END;
+                    else if (e == P_slow) st = LS_SLOW;
                 }
             }
         }
         // events, one lane at a time where they occur
-        if (st == LS_EOI) {   // close the token in progress at the end of the input
-            if (e == E.P_start) {
-                st = LS_DONE;
-            } else if ((kind_of<FORM>(E, e) & 0x7FFFu) != KIND_NONE) {
-                if (sp + NT * 4 > col_end) {
-                    st = LS_OVF;
-                } else {
+        if (st == LS_TAIL) {   // the input's last partial word, then close at the end
+            if (sp + 4 * NT * 4 > col_end) {
+                st = LS_OVF;
+            } else {
+                scalar(lim);
+                if (e == P_slow) {
+                    st = LS_SLOW;
+                } else if (e == E.P_start) {
+                    st = LS_DONE;
+                } else if ((kind_of<FORM>(E, e) & 0x7FFFu) != KIND_NONE) {
                     sts_u32(sp, (e << 16) | p);
                     sp += NT * 4;
                     st = LS_DONE;
+                } else {
+                    st = LS_SLOW;
                 }
+            }
+        }
+        if (st == LS_END) {   // stepped through the cut at `end` (and maybe past it)
+            while (sp > sp0 && (lds_u32(sp - NT * 4) & 0xFFFFu) > end) sp -= NT * 4;
+            if (sp > sp0 && (lds_u32(sp - NT * 4) & 0xFFFFu) == end) {
+                st = LS_DONE;   // the last token ended exactly at the cut
             } else {
+                p = end;        // it did not: the state at the cut (or before) is SLOW
                 st = LS_SLOW;
             }
         }
@@ -477,7 +491,7 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
             if (r == NONE32) {
                 fail = tok;
                 st = LS_FAIL;
-            } else if (sp + NT * 4 > col_end) {
+            } else if (sp + 8 * NT * 4 > col_end) {
                 st = LS_OVF;
             } else {
                 sts_u32(sp, (rq << 16) | r);
@@ -485,10 +499,17 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
                 sp0 = sp;
                 rst = p = r;
                 e = E.P_start;
-                st = r == end ? LS_DONE : LS_WALK;
+                if (r == end) {
+                    st = LS_DONE;
+                } else {
+                    scalar(((r + 3u) & ~3u) < mlim ? ((r + 3u) & ~3u) : mlim);   // up to a word boundary
+                    if (e == P_slow) st = LS_SLOW;
+                    else if (p < mlim) st = LS_WALK;
+                    else st = eoi ? LS_TAIL : LS_END;
+                }
             }
         }
-        if (!__any_sync(0xffffffffu, st == LS_WALK)) break;
+        if (!__any_sync(0xffffffffu, st < LS_DONE)) break;   // no lane walking or with an event
     }
     cnt = (sp - col) / (NT * 4);
     return st;
@@ -599,6 +620,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     E.P_start = tbase + P.p_start;
     E.P_flag = tbase + P.p_flag;
     E.P_slow = tbase + P.p_slow;
+    E.P_pre = tbase + P.p_pre;
     E.tbase = tbase;
     E.kind_s = tbase + P.kind_off;
     E.cmap_s = tbase + P.cmap_off;
@@ -1051,6 +1073,7 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     P.p_start = h.p_start;
     P.p_flag = h.p_flag;
     P.p_slow = h.p_slow;
+    P.p_pre = h.p_pre;
     P.out_kinds = d_kinds;
     P.out_lens = d_lens;
     P.cap = capacity;
@@ -1260,6 +1283,7 @@ extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64
     P.p_start = h.p_start;
     P.p_flag = h.p_flag;
     P.p_slow = h.p_slow;
+    P.p_pre = h.p_pre;
     P.out_kinds = d_kinds;
     P.out_lens = d_lens;
     P.cap = capacity;

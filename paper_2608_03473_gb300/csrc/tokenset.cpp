@@ -151,20 +151,22 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
     for (uint32_t b = 0; b < 256; b++)
         if (bit(cutmask, b)) cut_c[t.byte_class[b]] = 1;
 
-    // Row order: SLOW, R[0..S-1], START, E[...].  SLOW sits below P_flag and
-    // absorbs every byte, so a lane that falls into it records nothing more
-    // and can be sent to the replay lazily.
-    const uint32_t SLOW = 0, R0 = 1, START = S + 1;
+    // Row order: SLOW, R[0..S-1], START, PRE, E[...].  SLOW sits below P_flag
+    // and absorbs every byte, so a lane that falls into it records nothing
+    // more and can be sent to the replay lazily.  PRE lets a lane begin at the
+    // aligned word before its chunk start: it absorbs bytes outside the cut
+    // set and, on a cut byte, moves as START does.
+    const uint32_t SLOW = 0, R0 = 1, START = S + 1, PRE = S + 2;
     std::vector<uint32_t> e_row(S, LX_NONE);
     std::vector<uint32_t> e_state;
     for (uint32_t c = 0; c < C; c++) {
         uint32_t d = nx(c, q0);
         if (d != LX_NONE && e_row[d] == LX_NONE) {
-            e_row[d] = S + 2 + (uint32_t)e_state.size();
+            e_row[d] = S + 3 + (uint32_t)e_state.size();
             e_state.push_back(d);
         }
     }
-    const uint32_t R = S + 2 + (uint32_t)e_state.size();
+    const uint32_t R = S + 3 + (uint32_t)e_state.size();
 
     std::vector<uint32_t> tgt((size_t)R * C);
     auto state_row = [&](uint32_t row, uint32_t s) {
@@ -183,9 +185,10 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
     for (uint32_t c = 0; c < C; c++) {
         uint32_t d0 = nx(c, q0);
         tgt[(size_t)START * C + c] = d0 != LX_NONE ? R0 + d0 : SLOW;
+        tgt[(size_t)PRE * C + c] = cut_c[c] ? R0 + d0 : PRE;
         tgt[(size_t)SLOW * C + c] = SLOW;
     }
-    for (uint32_t k = 0; k < e_state.size(); k++) state_row(S + 2 + k, e_state[k]);
+    for (uint32_t k = 0; k < e_state.size(); k++) state_row(S + 3 + k, e_state[k]);
 
     std::vector<uint16_t> kind(R, (uint16_t)lx::KIND_NONE);
     auto kind_word = [&](uint32_t s) -> uint16_t {
@@ -195,7 +198,7 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
         return (uint16_t)(a | (keep ? lx::KIND_KEEP : 0));
     };
     for (uint32_t s = 0; s < S; s++) kind[R0 + s] = kind_word(s);
-    for (uint32_t k = 0; k < e_state.size(); k++) kind[S + 2 + k] = kind_word(e_state[k]);
+    for (uint32_t k = 0; k < e_state.size(); k++) kind[S + 3 + k] = kind_word(e_state[k]);
 
     ht = HostTable();
     ht.n_rows = R;
@@ -206,17 +209,18 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
         ht.ncols = 256;
         ht.row_bytes = 512;
         for (uint32_t r = 0; r < R; r++) P[r] = 512 * r + 4 * (r & 31);
-        ht.p_flag = 512 * (S + 2);
+        ht.p_flag = 512 * (S + 3);
         ht.p_slow = P[SLOW];
     } else {
         ht.form = lx::FORM_CLASS;
         ht.ncols = C + 1;
         ht.row_bytes = 2 * (C + 1);
         for (uint32_t r = 0; r < R; r++) P[r] = ht.row_bytes * r;
-        ht.p_flag = ht.row_bytes * (S + 2);
+        ht.p_flag = ht.row_bytes * (S + 3);
         ht.p_slow = P[SLOW];
     }
     ht.p_start = P[START];
+    ht.p_pre = P[PRE];
     ht.table_bytes = R * ht.row_bytes;
     if (ht.table_bytes > lx::MAX_TABLE_BYTES) {
         ht.status = LX_E_TOOBIG;
@@ -325,9 +329,9 @@ extern "C" int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uin
     if (!ts || mode < 0 || mode > 2) return LX_E_INVAL;
     const HostTable &h = ts->tab[mode];
     if (out && cap) std::memcpy(out, h.blob.data(), std::min<size_t>(cap, h.blob.size()));
-    const uint32_t m[11] = {(uint32_t)h.blob.size(), (uint32_t)h.form, h.n_rows, h.ncols, h.row_bytes,
+    const uint32_t m[12] = {(uint32_t)h.blob.size(), (uint32_t)h.form, h.n_rows, h.ncols, h.row_bytes,
                             h.table_bytes, h.p_start, h.p_flag, h.p_slow, h.kind_off | (h.cmap_off << 16),
-                            h.cert_off};
-    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 11));
+                            h.cert_off, h.p_pre};
+    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 12));
     return h.status;
 }
