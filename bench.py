@@ -26,9 +26,18 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "input GB/s lexed (512 MiB JSON, filtered modulo I, bit-exact)"
-WORKLOAD = "json_512mib_filtered_modulo"
 MiB = 1 << 20
+CUTS = {"json": "tab, newline, carriage return (certified modulo I = {ws})",
+        "clike": "newline (certified modulo I = {ws, line comment})"}
+
+
+def metric_name(workload, mib):
+    label = {"json": "JSON", "clike": "C-like"}[workload]
+    return f"input GB/s lexed ({mib} MiB {label}, filtered modulo I, bit-exact)"
+
+
+def workload_name(workload, mib):
+    return f"{workload}_{mib}mib_filtered_modulo"
 
 
 def dist_env():
@@ -123,10 +132,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from lexinputs import corpus, tokensets
-    dfa = tokensets.tokenset("json")
-    disc = tokensets.discarded_kinds("json")
+    dfa = tokensets.tokenset(args.workload)
+    disc = tokensets.discarded_kinds(args.workload)
     sample = args.ref_sample_mib * MiB
-    w = corpus.generate("json", sample)
+    w = corpus.generate(args.workload, sample)
     times = []
     for i in range(args.warmup + args.steps):
         n, tok, dt = time_oracle(w, dfa, disc, sample)
@@ -135,10 +144,12 @@ def run_reference(args, rank, world):
     total = sum(times)
     value = n * len(times) / total / 1e9
     line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "sample": f"first {args.ref_sample_mib} MiB of the 512 MiB corpus",
+        "metric": metric_name(args.workload, args.size_mib), "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": workload_name(args.workload, args.size_mib),
+                   "sample": f"first {args.ref_sample_mib} MiB of the {args.size_mib} MiB corpus",
                    "bytes_per_step": n},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {args.ref_sample_mib} MiB of the corpus per step, serial scan + pi_I"},
@@ -156,6 +167,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--size-mib", type=int, default=512)
+    ap.add_argument("--workload", default="json", choices=["json", "clike"])
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="also compare the output with the oracle")
@@ -179,10 +191,10 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
     n = args.size_mib * MiB
-    w = corpus.generate("json", n)
+    w = corpus.generate(args.workload, n)
     sha = corpus.sha256(w) if rank == 0 else None
-    dfa = tokensets.tokenset("json")
-    disc = tokensets.discarded_kinds("json")
+    dfa = tokensets.tokenset(args.workload)
+    disc = tokensets.discarded_kinds(args.workload)
     ts = lg.lx_compile_tokenset(dfa, disc)
     ctx = lg.lx_ctx_create()
     lg.lx_ctx_enable_timing(ctx, True)
@@ -275,13 +287,13 @@ def main():
                    "sample": f"first {sample // MiB} MiB of the corpus, one pass, serial scan + pi_I "
                              f"({sdt:.1f} s, {stok} kept tokens)"}
         line = {
-            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "metric": metric_name(args.workload, args.size_mib), "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "bytes": n, "tokens_kept": nt, "mode": "LX_FILTERED_MODULO",
-                       "cuts": "tab, newline, carriage return (certified modulo I = {ws})",
-                       "seed": "0x1EC50002", "sha256": sha,
-                       "l2": "inputs (512 MiB) larger than L2 (129 MB); no flush between steps",
+            "config": {"workload": workload_name(args.workload, args.size_mib), "bytes": n, "tokens_kept": nt,
+                       "mode": "LX_FILTERED_MODULO", "cuts": CUTS[args.workload],
+                       "seed": hex(corpus.WORKLOADS[args.workload][2]), "sha256": sha,
+                       "l2": f"inputs ({args.size_mib} MiB) larger than L2 (129 MB); no flush between steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "tokens_per_s": tokens_per_s,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

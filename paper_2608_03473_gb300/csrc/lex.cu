@@ -41,6 +41,7 @@ constexpr int HALO = 1024;              // extra staged bytes for ranges that ru
 constexpr int BUF = TILE + HALO;        // 18432, a multiple of 16
 constexpr int KS = 40;                  // token-end records per thread
 constexpr int STAGE_CAP = 4096;         // kept tokens per tile that take the deferred coalesced path
+constexpr int SPILL_WORDS = 8192;       // global spill region per CTA (kept tokens of long ranges)
 constexpr uint64_t NOPOS = ~0ull;
 constexpr uint32_t NONE32 = 0xFFFFFFFFu;
 
@@ -75,6 +76,8 @@ struct Params {
     uint32_t n_tiles;
     int tma;
     uint64_t timeout_ns;
+    uint32_t *spill;       // per-CTA spill regions for long ranges' kept tokens
+    uint32_t spill_cap;    // words per CTA (0: no spilling)
 };
 
 // ---- shared-memory layout (bytes from the dynamic shared base) ----
@@ -112,6 +115,7 @@ constexpr uint32_t M_PTOT = 168;    // u64: pending tile's kept total
 constexpr uint32_t M_PFPOS = 176;   // u64: pending tile's failure offset
 constexpr uint32_t M_PFIDX = 184;   // u64: pending tile's kept tokens before the failure
 constexpr uint32_t M_FLAGS = 192;   // u32: this tile: bit0 synchronous
+constexpr uint32_t M_SPILL = 196;   // u32: words of this CTA's spill region used by this tile
 
 // ---- PTX helpers ----
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -210,6 +214,9 @@ struct Env {
     uint64_t n;
     uint32_t P_start, P_flag, P_slow, P_pre;
     uint32_t tbase, kind_s, cmap_s, cert_s, kcol2;
+    uint32_t *spill;            // this CTA's spill region (global)
+    uint32_t spill_cap;         // its size in words
+    unsigned *spill_used;       // shared allocation counter, reset per tile
 };
 
 __device__ __forceinline__ uint32_t byte_at(const Env &E, uint64_t p)
@@ -248,9 +255,27 @@ __device__ __forceinline__ uint32_t kind_of(const Env &E, uint32_t e)
 __device__ __forceinline__ bool is_cut(const Env &E, uint32_t b) { return lds_u8(E.cert_s + b) != 0; }
 
 // ---- generic walker (64-bit offsets, reads past the staged bytes) ----
+// Counts kept tokens; `big` is set when one does not fit the packed staging
+// word (kind << 20 | length: kind < 4096, length < 2^20).
 struct CountEmit {
     uint64_t count = 0;
-    __device__ __forceinline__ void operator()(uint32_t kw, uint64_t) { count += (kw & KIND_KEEP) ? 1 : 0; }
+    bool big = false;
+    __device__ __forceinline__ void operator()(uint32_t kw, uint64_t len)
+    {
+        if (!(kw & KIND_KEEP)) return;
+        count++;
+        big |= (kw & 0x7FFFu) >= 4096u || len >= (1ull << 20);
+    }
+};
+
+// Writes kept tokens, packed, to consecutive shared staging words.
+struct StageEmit {
+    uint32_t *stage;
+    __device__ __forceinline__ void operator()(uint32_t kw, uint64_t len)
+    {
+        if (!(kw & KIND_KEEP)) return;
+        *stage++ = ((kw & 0x7FFFu) << 20) | (uint32_t)len;
+    }
 };
 
 struct DirectEmit {
@@ -393,7 +418,7 @@ __device__ __forceinline__ void walk_word(const Env &E, uint32_t &e, uint32_t &s
 }
 
 // ---- lockstep walker (staged bytes only, 32-bit offsets) ----
-enum { LS_WALK = 0, LS_SLOW = 1, LS_END = 2, LS_TAIL = 3, LS_DONE = 4, LS_FAIL = 5, LS_OVF = 6 };
+enum { LS_WALK = 0, LS_SLOW = 1, LS_END = 2, LS_TAIL = 3, LS_FULL = 4, LS_DONE = 5, LS_FAIL = 6, LS_OVF = 7 };
 
 // All lanes of a warp walk their ranges in lockstep, four bytes of one
 // aligned shared-memory word per lane per iteration, with no per-byte
@@ -404,14 +429,24 @@ enum { LS_WALK = 0, LS_SLOW = 1, LS_END = 2, LS_TAIL = 3, LS_DONE = 4, LS_FAIL =
 // A lane's range is [start, end]: `end` is the next chunk start (a certified
 // byte, whose step ends the last token) or, with `eoi`, the end of the
 // input.  Every token end is recorded as (row before the byte << 16 | end
-// offset) in the lane's record column `col` (stride NT words).  A lane that
-// falls into the absorbing SLOW row leaves the lockstep loop and replays its
-// current token from q0 to its last accepting position (longest match with
-// backtracking), then rejoins; a restart inside a word, and the last partial
-// word of the input, are stepped byte by byte.
+// offset) in the lane's record column `col` (stride NT words).  When the
+// column fills, its raw records are compacted in place into kept tokens
+// (kind << 20 | length, discarded kinds dropped) and the walk goes on; when
+// compacted tokens fill half of it, they move to a block of the CTA's global
+// spill region (blocks of one lane are chained: count, next, tokens).  A
+// lane that falls into the absorbing SLOW row leaves the lockstep loop and
+// replays its current token from q0 to its last accepting position (longest
+// match with backtracking), then rejoins; a restart inside a word, and the
+// last partial word of the input, are stepped byte by byte.
+//
+// On return the lane's first `spilled` kept tokens are in the spill blocks
+// chained from `sp_first`, the column holds the next `nc` compacted kept
+// tokens followed by raw records up to index `cnt`; `prev` is the offset
+// where the first of those raw records' tokens begins.
 template <int FORM>
 __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t start, uint32_t end, bool eoi,
-                                             uint32_t col, uint32_t &cnt, uint32_t &fail)
+                                             uint32_t col, uint32_t &cnt, uint32_t &nc, uint32_t &prev,
+                                             uint32_t &fail, uint32_t &sp_first, uint32_t &spilled)
 {
     const uint32_t P_flag = E.P_flag, P_slow = E.P_slow;
     const uint32_t col_end = col + (uint32_t)KS * NT * 4;
@@ -419,7 +454,13 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
     const uint32_t mlim = eoi ? (lim & ~3u) : lim;        // whole words while p < mlim
     uint32_t p = start & ~3u;
     uint32_t e = (start & 3u) ? E.P_pre : E.P_start;
-    uint32_t rst = start, sp = col, sp0 = col;
+    // sp: next record; raw0: first raw record (after nc compacted tokens);
+    // sp_lo: first record of the current token run (after the last restart or
+    // compaction), tok_base: where that run's first token begins
+    uint32_t sp = col, raw0 = col, sp_lo = col, tok_base = start;
+    uint32_t ncomp = 0, prev_pos = start;
+    uint32_t sp_last = NONE32, nspill = 0;
+    sp_first = NONE32;
     int st = !has ? LS_DONE : (p < mlim ? LS_WALK : LS_TAIL);
 
     // byte-by-byte steps over [p, stop) with the same recording rule
@@ -433,11 +474,49 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
             e = e2;
         }
     };
+    // Make room in the column: compact its raw records into kept tokens
+    // and, when those fill half of it, move them to a spill block.  False
+    // when a kept kind does not pack or the spill region is full.
+    auto make_room = [&]() -> bool {
+        uint32_t wr = raw0;
+        bool big = false;
+        for (uint32_t a = raw0; a < sp; a += NT * 4) {
+            const uint32_t v = lds_u32(a);
+            const uint32_t pos = v & 0xFFFFu;
+            const uint32_t kw = kind_of<FORM>(E, v >> 16);
+            const uint32_t len = pos - prev_pos;
+            prev_pos = pos;
+            if (kw & KIND_KEEP) {
+                big |= (kw & 0x7FFFu) >= 4096u;
+                sts_u32(wr, ((kw & 0x7FFFu) << 20) | len);
+                wr += NT * 4;
+                ncomp++;
+            }
+        }
+        raw0 = sp = sp_lo = wr;
+        tok_base = prev_pos;   // the token in progress began at the last end
+        if (big) return false;
+        if (sp > col + (uint32_t)(KS / 2) * NT * 4) {   // move the kept tokens out
+            const uint32_t off = atomicAdd(E.spill_used, ncomp + 2);
+            if (off + ncomp + 2 > E.spill_cap) return false;
+            uint32_t *blk = E.spill + off;
+            blk[0] = ncomp;
+            blk[1] = NONE32;
+            for (uint32_t i = 0; i < ncomp; i++) blk[2 + i] = lds_u32(col + i * NT * 4);
+            if (sp_last == NONE32) sp_first = off;
+            else E.spill[sp_last + 1] = off;
+            sp_last = off;
+            nspill += ncomp;
+            ncomp = 0;
+            raw0 = sp = sp_lo = col;
+        }
+        return true;
+    };
     for (;;) {
         while (__any_sync(0xffffffffu, st == LS_WALK)) {
             if (st == LS_WALK) {
                 if (sp + 4 * NT * 4 > col_end) {
-                    st = LS_OVF;
+                    st = LS_FULL;
                 } else {
                     walk_word<FORM>(E, e, sp, lds_u32(E.buf + p), p);
                     p += 4;
@@ -447,8 +526,9 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
             }
         }
         // events, one lane at a time where they occur
+        if (st == LS_FULL) st = make_room() ? LS_WALK : LS_OVF;
         if (st == LS_TAIL) {   // the input's last partial word, then close at the end
-            if (sp + 4 * NT * 4 > col_end) {
+            if (sp + 4 * NT * 4 > col_end && !make_room()) {
                 st = LS_OVF;
             } else {
                 scalar(lim);
@@ -466,8 +546,8 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
             }
         }
         if (st == LS_END) {   // stepped through the cut at `end` (and maybe past it)
-            while (sp > sp0 && (lds_u32(sp - NT * 4) & 0xFFFFu) > end) sp -= NT * 4;
-            if (sp > sp0 && (lds_u32(sp - NT * 4) & 0xFFFFu) == end) {
+            while (sp > sp_lo && (lds_u32(sp - NT * 4) & 0xFFFFu) > end) sp -= NT * 4;
+            if (sp > sp_lo && (lds_u32(sp - NT * 4) & 0xFFFFu) == end) {
                 st = LS_DONE;   // the last token ended exactly at the cut
             } else {
                 p = end;        // it did not: the state at the cut (or before) is SLOW
@@ -478,7 +558,7 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
             // the token in progress began at the last recorded end (or the
             // last restart); SLOW absorbs, so replaying up to p (never past
             // the range's cut byte) finds the same last accepting position
-            const uint32_t tok = sp > sp0 ? (lds_u32(sp - NT * 4) & 0xFFFFu) : rst;
+            const uint32_t tok = sp > sp_lo ? (lds_u32(sp - NT * 4) & 0xFFFFu) : tok_base;
             const uint32_t stop = (!eoi && p > end) ? end : p;
             uint32_t q = E.P_start, r = NONE32, rq = 0;
             for (uint32_t j = tok; j < stop; j++) {
@@ -491,13 +571,13 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
             if (r == NONE32) {
                 fail = tok;
                 st = LS_FAIL;
-            } else if (sp + 8 * NT * 4 > col_end) {
+            } else if (sp + 8 * NT * 4 > col_end && !make_room()) {
                 st = LS_OVF;
             } else {
                 sts_u32(sp, (rq << 16) | r);
                 sp += NT * 4;
-                sp0 = sp;
-                rst = p = r;
+                sp_lo = sp;
+                tok_base = p = r;
                 e = E.P_start;
                 if (r == end) {
                     st = LS_DONE;
@@ -512,6 +592,9 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
         if (!__any_sync(0xffffffffu, st < LS_DONE)) break;   // no lane walking or with an event
     }
     cnt = (sp - col) / (NT * 4);
+    nc = ncomp;
+    prev = prev_pos;
+    spilled = nspill;
     return st;
 }
 
@@ -627,6 +710,9 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     E.cert_s = tbase + P.cert_off;
     E.kcol2 = 2 * (P.ncols - 1);
     E.buf = buf;
+    E.spill = P.spill + (size_t)blockIdx.x * P.spill_cap;
+    E.spill_cap = P.spill_cap;
+    E.spill_used = reinterpret_cast<unsigned *>(misc + M_SPILL);
 
     volatile uint32_t *s_tile = reinterpret_cast<volatile uint32_t *>(misc + M_TILE);
     volatile uint32_t *s_x = reinterpret_cast<volatile uint32_t *>(misc + M_X);
@@ -648,6 +734,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         mbar_init(mbar, 1);
         fence_proxy_async();
         *s_ptile = NONE32;
+        *E.spill_used = 0;
     }
     __syncthreads();
 
@@ -771,30 +858,36 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         uint32_t cnt = 0, kept = 0;
         uint64_t kept_generic = 0;
         uint64_t fail = NOPOS;
-        bool generic = false;
+        bool generic = false;   // this lane's tokens come from the generic walker
+        bool big = false;       // ... and one of them does not fit a staging word
         const bool has = start != NONE32;
         const bool eoi = nxt == n_rel;
         const bool fast = has && nxt != NONE32 && (eoi ? n_rel <= staged : nxt < staged);
-        uint32_t f32 = 0;
-        const int st = lockstep_walk<FORM>(E, fast, start, fast ? nxt : 0u, eoi, col, cnt, f32);
+        uint32_t f32 = 0, ncomp = 0, prev0 = start, sp_first = NONE32, spilled = 0;
+        const int st = lockstep_walk<FORM>(E, fast, start, fast ? nxt : 0u, eoi, col, cnt, ncomp, prev0, f32,
+                                           sp_first, spilled);
         if (fast && st == LS_FAIL) fail = tile_base + f32;
         if (has && (!fast || st == LS_OVF)) {
             generic = true;
+            sp_first = NONE32;   // blocks spilled before the overflow are not used
+            spilled = 0;
             CountEmit ce;
             fail = walk<FORM>(E, tile_base + start, tile_base + seg0 + SEG, ce);
             kept_generic = ce.count;
+            big = ce.big;
         } else if (has) {
             // kinds, discard filter and lengths of the recorded token ends,
             // compacted in place in the column as kind << 20 | length
-            uint32_t prev = start;
-            for (uint32_t k = 0; k < cnt; k++) {
+            uint32_t prev = prev0;
+            kept = ncomp;
+            for (uint32_t k = ncomp; k < cnt; k++) {
                 const uint32_t v = lds_u32(col + k * NT * 4);
                 const uint32_t pos = v & 0xFFFFu;
                 const uint32_t kw = kind_of<FORM>(E, v >> 16);
                 const uint32_t len = pos - prev;
                 prev = pos;
                 if (kw & KIND_KEEP) {
-                    if ((kw & 0x7FFFu) >= 4096u) generic = true;
+                    if ((kw & 0x7FFFu) >= 4096u) generic = big = true;
                     sts_u32(col + kept * NT * 4, ((kw & 0x7FFFu) << 20) | len);
                     kept++;
                 }
@@ -804,7 +897,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         const uint32_t count32 = generic ? 0u : kept;
 
         // (d) CTA scan of kept-token counts
-        const uint64_t mycount = generic ? kept_generic : (uint64_t)kept;
+        const uint64_t mycount = generic ? kept_generic : (uint64_t)(spilled + kept);
         uint64_t x = mycount;
         for (int o = 1; o < 32; o <<= 1) {
             uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -813,7 +906,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         const uint64_t lane_excl = x - mycount;
         if (lane == 31) warp_tot[wid] = x;
         if (tid == 0) *s_fpos = NOPOS;
-        const int any_gen = __syncthreads_or(generic);
+        const int any_big = __syncthreads_or(big);
         if (tid == 0) {
             unsigned long long run = 0;
             for (int w = 0; w < NW; w++) {
@@ -822,7 +915,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
                 run += t;
             }
             *s_tot = run;
-            *s_flags = (any_gen || run > (unsigned long long)STAGE_CAP) ? 1u : 0u;
+            *s_flags = (any_big || run > (unsigned long long)STAGE_CAP) ? 1u : 0u;
             // publish this tile's aggregate at once
             publish_aggregate(P, tile, run);
             if (run) atomicAdd(&P.res->total, run);
@@ -840,10 +933,29 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         // to publish, so its look-back rarely waits
         flush_pending();
 
+        // this lane's packed kept tokens in order: spill blocks, then the column
+        auto for_lane_tokens = [&](auto put) {
+            uint32_t i = 0;
+            for (uint32_t off = sp_first; off != NONE32;) {
+                const uint32_t *blk = E.spill + off;
+                const uint32_t nb = blk[0];
+                for (uint32_t j = 0; j < nb; j++) put(i++, blk[2 + j]);
+                off = blk[1];
+            }
+            for (uint32_t k = 0; k < count32; k++) put(i++, lds_u32(col + k * NT * 4));
+        };
         const bool sync_tile = *s_flags != 0;
         if (!sync_tile) {
-            // stage this tile's kept tokens; they are written after the next walk
-            for (uint32_t k = 0; k < count32; k++) stage32[my_off + k] = lds_u32(col + k * NT * 4);
+            // stage this tile's kept tokens; they are written after the next walk.
+            // A lane whose range overflowed its records or left the staged
+            // bytes walks it again, writing straight into the stage (the
+            // input tile is still staged).
+            if (!generic) {
+                for_lane_tokens([&](uint32_t i, uint32_t v) { stage32[my_off + i] = v; });
+            } else {
+                StageEmit se{stage32 + my_off};
+                walk<FORM>(E, tile_base + start, tile_base + seg0 + SEG, se);
+            }
             if (tid == 0) {
                 *s_ptot = *s_tot;
                 *s_pfpos = *s_fpos;
@@ -851,7 +963,8 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
                 *s_ptile = tile;
             }
         } else {
-            // rare: record or stage overflow -- resolve now and write directly
+            // rare: stage overflow or a token that does not pack -- resolve
+            // now and write directly
             if (wid == 0) {
                 bool to = false;
                 const uint64_t G = resolve_prefix(P, tile, *s_tot, to);
@@ -867,14 +980,13 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
             __syncthreads();
             const uint64_t G = *s_G;
             if (!generic) {
-                for (uint32_t k = 0; k < count32; k++) {
-                    const uint64_t idx = G + my_off + k;
+                for_lane_tokens([&](uint32_t i, uint32_t v) {
+                    const uint64_t idx = G + my_off + i;
                     if (idx < P.cap) {
-                        const uint32_t v = lds_u32(col + k * NT * 4);
                         P.out_kinds[idx] = (uint16_t)(v >> 20);
                         P.out_lens[idx] = v & 0xFFFFFu;
                     }
-                }
+                });
             } else {
                 DirectEmit de{P.out_kinds, P.out_lens, P.cap, G + my_off};
                 walk<FORM>(E, tile_base + start, tile_base + seg0 + SEG, de);
@@ -886,6 +998,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
             // no successor's look-back waits behind this CTA's other work
             const uint32_t t = atomicAdd(P.tile_counter, 1u);
             s_tile[0] = t;
+            *E.spill_used = 0;
             if (t < P.n_tiles && P.tma) issue(t);
         }
         __syncthreads();
@@ -1056,9 +1169,8 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     const uint64_t n_tiles64 = (n + TILE - 1) / TILE;
     if (n_tiles64 > 0xFFFFFFF0ull) return LX_E_INVAL;
     const uint32_t n_tiles = (uint32_t)n_tiles64;
-    const size_t need = 64 + sizeof(unsigned long long) * (size_t)n_tiles;
-    rc = grow(&c->scratch, &c->scratch_bytes, need);
-    if (rc != LX_OK) return rc;
+    const size_t need = 64 + sizeof(unsigned long long) * (size_t)n_tiles;   // zeroed per call
+    const size_t spill_off = (need + 255) & ~(size_t)255;
 
     Params P;
     P.in = d_in;
@@ -1077,10 +1189,6 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     P.out_kinds = d_kinds;
     P.out_lens = d_lens;
     P.cap = capacity;
-    uint8_t *scr = static_cast<uint8_t *>(c->scratch);
-    P.res = reinterpret_cast<Result *>(scr);
-    P.tile_counter = reinterpret_cast<unsigned int *>(scr + 32);
-    P.status = reinterpret_cast<unsigned long long *>(scr + 64);
     P.n_tiles = n_tiles;
     P.tma = ((reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1 : 0;
     P.timeout_ns = c->timeout_ns;
@@ -1102,6 +1210,16 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
         if (c->occupancy[form] < 1) c->occupancy[form] = 1;
     }
     const uint32_t grid = (uint32_t)std::min<uint64_t>(n_tiles, (uint64_t)c->occupancy[form] * c->num_sms);
+
+    // scratch: result record, tile counter, status words, then the spill regions
+    rc = grow(&c->scratch, &c->scratch_bytes, spill_off + sizeof(uint32_t) * (size_t)SPILL_WORDS * grid);
+    if (rc != LX_OK) return rc;
+    uint8_t *scr = static_cast<uint8_t *>(c->scratch);
+    P.res = reinterpret_cast<Result *>(scr);
+    P.tile_counter = reinterpret_cast<unsigned int *>(scr + 32);
+    P.status = reinterpret_cast<unsigned long long *>(scr + 64);
+    P.spill = reinterpret_cast<uint32_t *>(scr + spill_off);
+    P.spill_cap = SPILL_WORDS;
 
     rc = cuda_err(cudaMemsetAsync(c->scratch, 0, need, st));
     if (rc != LX_OK) return rc;
@@ -1290,6 +1408,8 @@ extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64
     P.res = reinterpret_cast<Result *>(scr + NA_RESULT);
     P.tile_counter = reinterpret_cast<unsigned int *>(scr + NA_RESULT + 32);
     P.status = reinterpret_cast<unsigned long long *>(scr + NA_STATUS);
+    P.spill = nullptr;   // no spill region: long ranges take the generic walker
+    P.spill_cap = 0;
     P.n_tiles = n_tiles;
     P.tma = ((reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1 : 0;
     P.timeout_ns = 20ull * 1000 * 1000 * 1000;

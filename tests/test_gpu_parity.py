@@ -178,3 +178,57 @@ def test_full_size_json_512mib(gpu):
     w = corpus.generate("json")
     nt = check(lg, ctx, "json", w, 2)
     assert nt > 50_000_000
+
+
+def _dense_lines(rng, n_bytes, min_len, max_len, alphabet):
+    """Newline-separated lines of back-to-back short C-like tokens: ranges
+    (newline to newline) far longer than a lane's record column."""
+    out = bytearray()
+    while len(out) < n_bytes:
+        ln = rng.randint(min_len, max_len)
+        line = bytearray()
+        while len(line) < ln:
+            line += rng.choice(alphabet)
+        out += line[:ln] + b"\n"
+    return bytes(out[:n_bytes])
+
+
+EXPR = [b"a", b"b1", b"x_2", b"+", b"-", b"*", b"/", b"(", b")", b"42", b"0x1f", b" ", b"==", b";", b",", b"if", b"1.5"]
+
+
+def test_long_ranges_spill(gpu):
+    """Ranges of hundreds of kept tokens: compaction plus spill blocks."""
+    lg, ctx = gpu
+    rng = random.Random(77)
+    w = _dense_lines(rng, 3 << 20, 50, 1000, EXPR)
+    check(lg, ctx, "clike", w, 2)
+    check(lg, ctx, "clike_row1", w, 2)
+
+
+def test_long_ranges_overflow_fallbacks(gpu):
+    """More kept tokens per tile than the stage and the spill region hold
+    (one-byte tokens, no separators), and lines longer than the staged halo."""
+    lg, ctx = gpu
+    rng = random.Random(78)
+    dense = _dense_lines(rng, 1 << 20, 900, 1000, [b"+-", b"*", b"%", b"~"])
+    check(lg, ctx, "clike", dense, 2)
+    long_lines = _dense_lines(rng, 1 << 20, 3000, 9000, EXPR)
+    check(lg, ctx, "clike", long_lines, 2)
+    check(lg, ctx, "clike", long_lines[: 5 * TILE + 11], 1)
+
+
+def test_long_ranges_noalloc(gpu):
+    """lx_lex_noalloc has no spill region: long ranges take the generic walker."""
+    lg, _ = gpu
+    import torch
+    rng = random.Random(79)
+    w = np.frombuffer(_dense_lines(rng, 1 << 20, 50, 1000, EXPR), np.uint8)
+    ts = tokenset(lg, "clike")
+    d = torch.from_numpy(w.copy()).cuda()
+    k = torch.zeros(w.size, dtype=torch.int16, device="cuda")
+    l = torch.zeros(w.size, dtype=torch.int32, device="cuda")
+    rc, nt, con = lg.lx_lex_noalloc(ts, d, 2, k, l)
+    ek, el, econ = expected("clike", w, 2)
+    assert rc == 0 and con == econ and nt == ek.size
+    assert np.array_equal(k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), ek)
+    assert np.array_equal(l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), el)
