@@ -104,6 +104,23 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
+def profiled_traffic(workload_key):
+    """DRAM bytes of one launch from the committed ncu summary, or None when
+    the kernel source changed since the counters were taken."""
+    import hashlib
+    import re
+    try:
+        src = open(os.path.join(ROOT, "paper_2608_03473_gb300", "csrc", "lex.cu"), "rb").read()
+        text = open(os.path.join(ROOT, "profiles", "lex_tiles_dram_512mib.md")).read()
+    except OSError:
+        return None
+    h = hashlib.sha256(src).hexdigest()
+    for key, val, sha in re.findall(r"<!-- traffic (\S+) (\d+) ([0-9a-f]{64}) -->", text):
+        if key == workload_key and sha == h:
+            return int(val)
+    return None
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -297,7 +314,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "tokens_per_s": tokens_per_s,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": profiled_traffic(workload_name(args.workload, args.size_mib)),
                          "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "kernel": "lex_tiles", "kernel_ms": k_ms,
                          "algorithmic_bytes": alg_bytes, "frac_of_nominal_8tbs": achieved / 8000.0},
