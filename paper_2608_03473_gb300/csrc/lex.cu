@@ -4,22 +4,25 @@
 // One persistent CTA per resident slot loops over tiles of TILE input bytes.
 // Per tile:
 //   (a) stage: a 1-D bulk copy (cp.async.bulk, TMA) brings the tile plus a
-//       halo into shared memory, double-buffered against the previous tile;
+//       halo into shared memory; it is issued as soon as the previous tile's
+//       aggregate is published, so it overlaps that tile's output writes;
 //   (b) plan:  each of NT threads owns the equal-division target of its
 //       SEG-byte segment and slides it forward to the first byte of the
 //       mode's certified set in the segment (the planner of Section 6 with
 //       k = one target per thread); a segment holding no certified byte
 //       yields no chunk and the previous chunk runs on;
-//   (c) walk:  from its start each thread runs the longest-match loop of
-//       Section 3 from q0 over the shared-memory walk table (internal.h),
-//       every certified byte ending the token in progress, until it reaches
-//       a certified byte at or past its segment end (the next chunk start) or
-//       the end of the input; tokens go to per-thread shared slots;
-//   (d) emit:  a CTA scan of kept-token counts, a decoupled look-back over
-//       per-tile status words for the global offset, compaction through a
-//       shared staging array and coalesced writes of kinds (u16) and
-//       lengths (u32).  The first lexing failure (Corollary 1) is combined
-//       with device atomics.
+//   (c) walk:  all lanes run the longest-match loop of Section 3 in lockstep
+//       over the shared-memory walk table (internal.h), every certified byte
+//       ending the token in progress, each from its chunk start to the next
+//       chunk start (or the end of the input); token ends go to per-thread
+//       record columns, compacted in place and spilled to a per-CTA global
+//       region when a range has more tokens than a column holds;
+//   (d) emit:  a CTA scan of kept-token counts, the tile's aggregate published
+//       at once for a decoupled look-back over per-tile status words; the
+//       kept tokens wait in a shared stage and are written (coalesced kinds
+//       u16, lengths u32) one iteration later, once the look-back has
+//       resolved the tile's output offset.  The first lexing failure
+//       (Corollary 1) is combined with device atomics.
 // Every device-side wait is bounded by a %globaltimer budget.
 
 #include <cuda_runtime.h>
@@ -919,6 +922,11 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
             // publish this tile's aggregate at once
             publish_aggregate(P, tile, run);
             if (run) atomicAdd(&P.res->total, run);
+            // claim the next tile now that this one's aggregate is out, and
+            // stage it while this tile's output is written
+            const uint32_t t = atomicAdd(P.tile_counter, 1u);
+            s_tile[0] = t;
+            if (t < P.n_tiles && P.tma) issue(t);
         }
         __syncthreads();
         const uint64_t my_off = warp_tot[wid] + lane_excl;   // within the tile
@@ -944,6 +952,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
             }
             for (uint32_t k = 0; k < count32; k++) put(i++, lds_u32(col + k * NT * 4));
         };
+        E.sm_end = E.tile_base;   // the staged buffer now receives the next tile: re-walks read global
         const bool sync_tile = *s_flags != 0;
         if (!sync_tile) {
             // stage this tile's kept tokens; they are written after the next walk.
@@ -992,15 +1001,8 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
                 walk<FORM>(E, tile_base + start, tile_base + seg0 + SEG, de);
             }
         }
-        __syncthreads();   // records, stage and the input buffer are free
-        if (tid == 0) {
-            // claim the next tile only now: a claimed tile is walked at once, so
-            // no successor's look-back waits behind this CTA's other work
-            const uint32_t t = atomicAdd(P.tile_counter, 1u);
-            s_tile[0] = t;
-            *E.spill_used = 0;
-            if (t < P.n_tiles && P.tma) issue(t);
-        }
+        __syncthreads();   // records, stage and spill blocks are free
+        if (tid == 0) *E.spill_used = 0;
         __syncthreads();
         tile = s_tile[0];
     }
