@@ -190,6 +190,56 @@ int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_
                 uint64_t *consumed, void *stream);
 
 /*
+ * lx_lex_batch -- lex many documents, each with its own token set, in one
+ * graph launch (the batched form of lx_lex; the paper lexes one input, this
+ * applies its method per document).
+ *
+ * docs[i] names a device buffer of docs[i].n bytes and the index of its
+ * token set in sets[0 .. n_sets).  Every document is lexed exactly as
+ * lx_lex would lex it alone (cuts at the mode's certificates of its own
+ * token set, Theorems 1 and 3; failures per Corollary 1).  Documents are
+ * grouped by token set: one persistent kernel per set runs over the tiles of
+ * all that set's documents, and the groups follow each other in set order.
+ * The output stream d_kinds / d_lens (capacity entries) holds the groups in
+ * set order and, within a group, the documents in their order in docs[].
+ * results[i] (host array of n_docs) receives the output index of document
+ * i's first token (out_off), its kept-token count n_tokens (tokens before
+ * its first lexing error) and consumed = con(w) of the document; when
+ * consumed < n, entries after out_off + n_tokens up to the next document's
+ * out_off are unspecified.  *n_total is the length of the whole stream
+ * (the end of the last group).  Empty documents get out_off 0, n_tokens 0,
+ * consumed 0.
+ *
+ * The launch sequence (zeroing, descriptor upload, the per-set kernels,
+ * result read-back) is captured once into a CUDA graph held by the context
+ * and replayed while the batch shape (number of documents and tiles per
+ * set, the sets, mode, output buffers and capacity) stays the same; the
+ * descriptors themselves (buffers, lengths) may change between calls.
+ *
+ * Errors: LX_E_INVAL (null arguments, set index out of range, null buffer
+ * for a non-empty document), LX_E_MODE, LX_E_TOOBIG, LX_E_NOMEM, LX_E_CUDA,
+ * LX_E_TIMEOUT; LX_E_CAPACITY when *n_total > capacity (results[] are
+ * still filled, so the caller can size the buffers and call again).
+ * Synchronizes `stream` before returning.
+ */
+typedef struct {
+    const uint8_t *data;   /* device pointer to the document's bytes       */
+    uint64_t n;            /* its length in bytes                          */
+    uint32_t set;          /* index of its token set in `sets`             */
+    uint32_t reserved;     /* must be 0                                    */
+} lx_doc;
+
+typedef struct {
+    uint64_t out_off;      /* output index of the document's first token   */
+    uint64_t n_tokens;     /* kept tokens, up to its first lexing error    */
+    uint64_t consumed;     /* con(w) of the document                       */
+} lx_doc_result;
+
+int lx_lex_batch(lx_ctx *ctx, const lx_tokenset *const *sets, uint32_t n_sets, const lx_doc *docs,
+                 uint32_t n_docs, int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity,
+                 lx_doc_result *results, uint64_t *n_total, void *stream);
+
+/*
  * lx_lex_noalloc -- lx_lex for callers that cannot allocate memory.
  *
  * The paper has no counterpart to this entry point; it exists for library

@@ -81,3 +81,55 @@ def generate(name: str, n: int | None = None, seed: int | None = None,
 
 def sha256(buf: np.ndarray) -> str:
     return hashlib.sha256(memoryview(np.ascontiguousarray(buf))).hexdigest()
+
+
+# ---------------------------------------------------------------------------
+# Document batches: many documents of mixed token sets (the batched launch)
+# ---------------------------------------------------------------------------
+BATCH_SEED = 0x1EC50004
+
+
+def _splitmix64(x: int) -> int:
+    x = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = x
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return z ^ (z >> 31)
+
+
+def batch_spec(n_docs: int = 4096, seed: int = BATCH_SEED, median: int = 128 << 10, sigma: float = 1.66,
+               lo: int = 1 << 10, hi: int = 16 << 20, names=("json", "clike")):
+    """(name, size, seed) of each document: sizes lognormal (median, sigma)
+    clamped to [lo, hi], the workload drawn uniformly from ``names``; every
+    draw comes from a splitmix64 stream, so the batch is the same on any
+    machine."""
+    import math
+    state = seed
+    out = []
+    for i in range(n_docs):
+        state = _splitmix64(state)
+        u1 = ((state >> 11) + 1) / float(1 << 53)          # (0, 1]
+        state = _splitmix64(state)
+        u2 = (state >> 11) / float(1 << 53)                # [0, 1)
+        state = _splitmix64(state)
+        which = names[state % len(names)]
+        z = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+        size = int(round(median * math.exp(sigma * z)))
+        size = min(max(size, lo), hi)
+        out.append((which, size, (seed << 16) ^ (i + 1)))
+    return out
+
+
+def generate_batch(spec, align: int = 16):
+    """Generate every document of ``spec`` into one buffer; returns (buffer,
+    offsets).  Document i occupies buffer[offsets[i] : offsets[i] + size_i];
+    offsets are multiples of ``align``."""
+    offs, pos = [], 0
+    for _, size, _ in spec:
+        offs.append(pos)
+        pos += (size + align - 1) // align * align
+    buf = np.zeros(max(pos, 1), dtype=np.uint8)
+    for (name, size, s), o in zip(spec, offs):
+        if size:
+            generate(name, size, seed=s, out=buf[o:o + size])
+    return buf, offs

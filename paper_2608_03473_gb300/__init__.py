@@ -48,7 +48,7 @@ LX_FILTERED_MODULO = 2
 EXPORTED = (
     "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
-    "lx_lex", "lx_lex_host", "lx_lex_noalloc",
+    "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch",
     "lx_strerror",
 )
 
@@ -65,6 +65,15 @@ class _Dfa(ctypes.Structure):
         ("n_kinds", ctypes.c_uint32), ("byte_class", ctypes.c_void_p), ("next", ctypes.c_void_p),
         ("accept_kind", ctypes.c_void_p),
     ]
+
+
+class _Doc(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n", ctypes.c_uint64), ("set", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class _DocResult(ctypes.Structure):
+    _fields_ = [("out_off", ctypes.c_uint64), ("n_tokens", ctypes.c_uint64), ("consumed", ctypes.c_uint64)]
 
 
 _lib = None
@@ -96,6 +105,7 @@ def load_library(path: Optional[str] = None):
             "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_host": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_noalloc": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
+            "lx_lex_batch": (i32, [vp, vp, u32, vp, u32, i32, vp, vp, u64, vp, vp, vp]),
             "lx_strerror": (ctypes.c_char_p, [i32]),
         }
         for name, (res, args) in sig.items():
@@ -279,3 +289,28 @@ def lx_lex_noalloc(ts: Tokenset, d_in, mode: int, d_kinds, d_lens, n: Optional[i
     rc = lib.lx_lex_noalloc(ts.handle, d_in.data_ptr(), n, int(mode), d_kinds.data_ptr(), d_lens.data_ptr(), cap,
                             ctypes.byref(nt), ctypes.byref(con), _stream_handle(stream))
     return rc, nt.value, con.value
+
+
+def lx_lex_batch(ctx: Ctx, sets, docs, mode: int, d_kinds, d_lens, capacity: Optional[int] = None,
+                 stream=None):
+    """Lex many documents in one graph launch.  ``sets`` is a sequence of
+    Tokenset; ``docs`` a sequence of (device uint8 tensor or (pointer, n),
+    set index).  Returns (status, n_total, results) with results a list of
+    (out_off, n_tokens, consumed) per document, in the order given."""
+    lib = load_library()
+    n_sets, n_docs = len(sets), len(docs)
+    set_arr = (ctypes.c_void_p * max(n_sets, 1))(*[ts.handle for ts in sets])
+    doc_arr = (_Doc * max(n_docs, 1))()
+    for i, (buf, set_idx) in enumerate(docs):
+        if isinstance(buf, tuple):
+            ptr, n = buf
+        else:
+            ptr, n = buf.data_ptr(), buf.numel()
+        doc_arr[i] = _Doc(ptr if n else None, int(n), int(set_idx), 0)
+    res_arr = (_DocResult * max(n_docs, 1))()
+    cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
+    total = ctypes.c_uint64()
+    rc = lib.lx_lex_batch(ctx.handle, set_arr, n_sets, doc_arr, n_docs, int(mode), d_kinds.data_ptr(),
+                          d_lens.data_ptr(), cap, res_arr, ctypes.byref(total), _stream_handle(stream))
+    results = [(res_arr[i].out_off, res_arr[i].n_tokens, res_arr[i].consumed) for i in range(n_docs)]
+    return rc, total.value, results

@@ -55,17 +55,39 @@ constexpr unsigned long long ST_AGG = 1ull << 62;
 constexpr unsigned long long ST_INCL = 2ull << 62;
 constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 
+// One launch's record.  With a single document it is also that document's
+// record (the first three fields are laid out as in DocResult).
 struct Result {
     unsigned long long total;          // kept tokens over all chunks (atomicAdd)
     unsigned long long inv_fail_pos;   // ~min failure offset (atomicMax), 0 = none
-    unsigned long long inv_fail_tok;   // ~min token index at the failure
+    unsigned long long inv_fail_tok;   // ~min output index at the failure
     unsigned int error;
     unsigned int pad;
 };
 
-struct Params {
+// A document of a batched launch: its tiles are consecutive in the launch's
+// tile sequence, starting at first_tile.
+struct DocDesc {
     const uint8_t *in;
     uint64_t n;
+    uint32_t first_tile;
+    uint32_t tma;           // input 16-byte aligned: tiles are staged by TMA
+};
+
+struct DocResult {
+    unsigned long long total;          // kept tokens of the document, including any after a failure
+    unsigned long long inv_fail_pos;   // ~min failure offset within the document, 0 = none
+    unsigned long long inv_fail_tok;   // ~min output index at the failure
+    unsigned long long out_off1;       // output index of its first token + 1 (0 = not yet written)
+};
+
+struct Params {
+    DocDesc one;                 // the document when docs == nullptr
+    const DocDesc *docs;         // batched: documents of this launch
+    const uint32_t *tile_doc;    // batched: document index of every tile
+    DocResult *dres;             // batched: per-document records
+    const Result *prev;          // batched: records of the launches before this one
+    uint32_t n_prev;             // (their token totals offset this launch's output)
     const uint8_t *blob;
     uint32_t blob_bytes, table_bytes, kind_off, cmap_off, cert_off;
     uint32_t ncols;
@@ -77,7 +99,6 @@ struct Params {
     unsigned int *tile_counter;
     Result *res;
     uint32_t n_tiles;
-    int tma;
     uint64_t timeout_ns;
     uint32_t *spill;       // per-CTA spill regions for long ranges' kept tokens
     uint32_t spill_cap;    // words per CTA (0: no spilling)
@@ -119,6 +140,9 @@ constexpr uint32_t M_PFPOS = 176;   // u64: pending tile's failure offset
 constexpr uint32_t M_PFIDX = 184;   // u64: pending tile's kept tokens before the failure
 constexpr uint32_t M_FLAGS = 192;   // u32: this tile: bit0 synchronous
 constexpr uint32_t M_SPILL = 196;   // u32: words of this CTA's spill region used by this tile
+constexpr uint32_t M_PDOC = 200;    // u32: pending tile's document
+constexpr uint32_t M_PFIRST = 204;  // u32: pending tile is its document's first
+constexpr uint32_t M_TREF = 208;    // TileRef of the claimed tile (40 bytes)
 
 // ---- PTX helpers ----
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -665,6 +689,33 @@ __device__ uint64_t resolve_prefix(const Params &P, uint32_t tile, uint64_t agg,
     return G;
 }
 
+// Where global tile g of a launch lies: its document and the document-relative
+// offset of its first byte.
+struct TileRef {
+    const uint8_t *in;
+    uint64_t n;
+    uint64_t base;
+    uint32_t doc;
+    uint32_t tma;
+    bool first;
+};
+
+static_assert(sizeof(TileRef) <= 40, "TileRef must fit its shared slot");
+
+__device__ __forceinline__ TileRef tile_ref(const Params &P, uint32_t g)
+{
+    uint32_t d = 0;
+    const DocDesc D = P.docs ? P.docs[d = P.tile_doc[g]] : P.one;
+    TileRef r;
+    r.in = D.in;
+    r.n = D.n;
+    r.doc = d;
+    r.tma = D.tma;
+    r.base = (uint64_t)(g - D.first_tile) * TILE;
+    r.first = g == D.first_tile;
+    return r;
+}
+
 // 4-bit mask of the certified bytes of a little-endian word.
 __device__ __forceinline__ uint32_t cut_mask4(const Env &E, uint32_t w)
 {
@@ -701,8 +752,6 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         }
     }
     Env E;
-    E.in = P.in;
-    E.n = P.n;
     E.P_start = tbase + P.p_start;
     E.P_flag = tbase + P.p_flag;
     E.P_slow = tbase + P.p_slow;
@@ -730,6 +779,24 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     unsigned long long *s_pfpos = reinterpret_cast<unsigned long long *>(misc + M_PFPOS);
     unsigned long long *s_pfidx = reinterpret_cast<unsigned long long *>(misc + M_PFIDX);
     unsigned long long *warp_tot = reinterpret_cast<unsigned long long *>(misc + M_WARP);
+    volatile uint32_t *s_pdoc = reinterpret_cast<volatile uint32_t *>(misc + M_PDOC);
+    volatile uint32_t *s_pfirst = reinterpret_cast<volatile uint32_t *>(misc + M_PFIRST);
+    // the launch's output starts after the tokens of the launches before it
+    uint64_t out_base = 0;
+    for (uint32_t k = 0; k < P.n_prev; k++) out_base += P.prev[k].total;
+    // per-document record (the launch record itself for a single document)
+    auto rec = [&](uint32_t d) -> DocResult * {
+        return P.dres ? P.dres + d : reinterpret_cast<DocResult *>(P.res);
+    };
+    // a resolved tile: its failure and, for a document's first tile, the
+    // document's output offset
+    auto report = [&](uint32_t d, bool first, uint64_t G, uint64_t fpos, uint64_t fidx) {
+        if (fpos != NOPOS) {
+            atomicMax(&rec(d)->inv_fail_pos, ~(unsigned long long)fpos);
+            atomicMax(&rec(d)->inv_fail_tok, ~(unsigned long long)(out_base + G + fidx));
+        }
+        if (first && P.dres) P.dres[d].out_off1 = out_base + G + 1;
+    };
     uint32_t *stage32 = reinterpret_cast<uint32_t *>(smem + L.stage);
     const uint32_t col = sbase + L.slots + tid * 4;   // this thread's record column
 
@@ -741,13 +808,20 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     }
     __syncthreads();
 
-    auto issue = [&](uint32_t tile) {   // one thread
-        uint64_t base = (uint64_t)tile * TILE;
-        uint64_t avail = P.n - base;
+    TileRef *s_tref = reinterpret_cast<TileRef *>(misc + M_TREF);
+    // one thread: claim the next tile, note where it lies, start its copy
+    auto claim = [&]() {
+        const uint32_t t = atomicAdd(P.tile_counter, 1u);
+        s_tile[0] = t;
+        if (t >= P.n_tiles) return;
+        const TileRef R = tile_ref(P, t);
+        *s_tref = R;
+        if (!R.tma) return;
+        uint64_t avail = R.n - R.base;
         uint32_t len = (uint32_t)(avail < (uint64_t)BUF ? avail : (uint64_t)BUF) & ~15u;
         if (len) {
             fence_proxy_async();
-            tma_load(buf, P.in + base, len, mbar);
+            tma_load(buf, R.in + R.base, len, mbar);
         }
     };
     // Resolve the pending tile's output offset (warp 0), then write its
@@ -761,16 +835,13 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
             if (lane == 0) {
                 if (to) atomicOr(&P.res->error, ERR_TIMEOUT);
                 *s_G = G;
-                if (*s_pfpos != NOPOS) {
-                    atomicMax(&P.res->inv_fail_pos, ~(unsigned long long)*s_pfpos);
-                    atomicMax(&P.res->inv_fail_tok, ~(unsigned long long)(G + *s_pfidx));
-                }
+                report(*s_pdoc, *s_pfirst != 0, G, *s_pfpos, *s_pfidx);
             }
         }
         __syncthreads();
         const uint64_t G = *s_G, tot = *s_ptot;
         for (uint32_t i = tid; i < tot; i += NT) {
-            const uint64_t idx = G + i;
+            const uint64_t idx = out_base + G + i;
             if (idx < P.cap) {
                 const uint32_t v = stage32[i];
                 P.out_kinds[idx] = (uint16_t)(v >> 20);
@@ -781,21 +852,20 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         if (tid == 0) *s_ptile = NONE32;
     };
 
-    if (tid == 0) {
-        uint32_t t = atomicAdd(P.tile_counter, 1u);
-        s_tile[0] = t;
-        if (t < P.n_tiles && P.tma) issue(t);
-    }
+    if (tid == 0) claim();
     __syncthreads();
     uint32_t tile = s_tile[0];
     uint32_t par = 0;
 
     while (tile < P.n_tiles) {
-        const uint64_t tile_base = (uint64_t)tile * TILE;
-        const uint64_t avail = P.n - tile_base;
+        const TileRef T = *s_tref;
+        const uint64_t tile_base = T.base;   // offsets below are relative to the document
+        const uint64_t avail = T.n - tile_base;
+        E.in = T.in;
+        E.n = T.n;
         uint32_t staged;
         bool bad = false;
-        if (P.tma) {
+        if (T.tma) {
             staged = (uint32_t)(avail < (uint64_t)BUF ? avail : (uint64_t)BUF) & ~15u;
             if (staged) {
                 bad = !mbar_wait(mbar, par, P.timeout_ns);
@@ -804,7 +874,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         } else {
             staged = (uint32_t)(avail < (uint64_t)BUF ? avail : (uint64_t)BUF);
             uint8_t *b = smem + L.buf;
-            for (uint32_t i = tid; i < staged; i += NT) b[i] = P.in[tile_base + i];
+            for (uint32_t i = tid; i < staged; i += NT) b[i] = T.in[tile_base + i];
         }
         if (__syncthreads_or(bad)) {
             if (tid == 0) atomicOr(&P.res->error, ERR_TIMEOUT);
@@ -818,7 +888,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         // a word at a time
         const uint32_t seg0 = (uint32_t)tid * SEG;
         uint32_t start = NONE32;
-        if (tile == 0 && tid == 0) {
+        if (T.first && tid == 0) {
             start = 0;
         } else if (seg0 + SEG <= staged) {
             for (uint32_t k = 0; k < SEG / 4; k++) {
@@ -829,7 +899,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
         } else {
             const uint32_t lim = seg0 + SEG < n_rel ? seg0 + SEG : n_rel;
             for (uint32_t p = seg0; p < lim; p++) {
-                uint32_t b = p < staged ? lds_u8(buf + p) : (uint32_t)__ldg(P.in + tile_base + p);
+                uint32_t b = p < staged ? lds_u8(buf + p) : (uint32_t)__ldg(T.in + tile_base + p);
                 if (is_cut(E, b)) { start = p; break; }
             }
         }
@@ -921,12 +991,13 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
             *s_flags = (any_big || run > (unsigned long long)STAGE_CAP) ? 1u : 0u;
             // publish this tile's aggregate at once
             publish_aggregate(P, tile, run);
-            if (run) atomicAdd(&P.res->total, run);
+            if (run) {
+                atomicAdd(&rec(T.doc)->total, run);
+                if (P.dres) atomicAdd(&P.res->total, run);
+            }
             // claim the next tile now that this one's aggregate is out, and
             // stage it while this tile's output is written
-            const uint32_t t = atomicAdd(P.tile_counter, 1u);
-            s_tile[0] = t;
-            if (t < P.n_tiles && P.tma) issue(t);
+            claim();
         }
         __syncthreads();
         const uint64_t my_off = warp_tot[wid] + lane_excl;   // within the tile
@@ -969,6 +1040,8 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
                 *s_ptot = *s_tot;
                 *s_pfpos = *s_fpos;
                 *s_pfidx = *s_fidx;
+                *s_pdoc = T.doc;
+                *s_pfirst = T.first ? 1u : 0u;
                 *s_ptile = tile;
             }
         } else {
@@ -980,24 +1053,21 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
                 if (lane == 0) {
                     if (to) atomicOr(&P.res->error, ERR_TIMEOUT);
                     *s_G = G;
-                    if (*s_fpos != NOPOS) {
-                        atomicMax(&P.res->inv_fail_pos, ~(unsigned long long)*s_fpos);
-                        atomicMax(&P.res->inv_fail_tok, ~(unsigned long long)(G + *s_fidx));
-                    }
+                    report(T.doc, T.first, G, *s_fpos, *s_fidx);
                 }
             }
             __syncthreads();
             const uint64_t G = *s_G;
             if (!generic) {
                 for_lane_tokens([&](uint32_t i, uint32_t v) {
-                    const uint64_t idx = G + my_off + i;
+                    const uint64_t idx = out_base + G + my_off + i;
                     if (idx < P.cap) {
                         P.out_kinds[idx] = (uint16_t)(v >> 20);
                         P.out_lens[idx] = v & 0xFFFFFu;
                     }
                 });
             } else {
-                DirectEmit de{P.out_kinds, P.out_lens, P.cap, G + my_off};
+                DirectEmit de{P.out_kinds, P.out_lens, P.cap, out_base + G + my_off};
                 walk<FORM>(E, tile_base + start, tile_base + seg0 + SEG, de);
             }
         }
@@ -1029,7 +1099,16 @@ struct lx_ctx {
     size_t scratch_bytes = 0;
     Result *h_res = nullptr;   // pinned
     uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;
-    int occupancy[2] = {0, 0};
+    std::vector<std::pair<uint64_t, int>> occupancy;   // (form << 32 | shared bytes) -> CTAs per SM
+    // lx_lex_batch: device scratch, pinned staging (descriptors up, records
+    // down), the capture stream and the cached graph with its shape key
+    void *b_dev = nullptr;
+    size_t b_dev_bytes = 0;
+    void *b_host = nullptr;
+    size_t b_host_bytes = 0;
+    cudaStream_t b_stream = nullptr;
+    cudaGraphExec_t b_exec = nullptr;
+    std::vector<uint64_t> b_key;
     // device buffers of lx_lex_host
     void *d_in = nullptr;
     size_t d_in_bytes = 0;
@@ -1107,6 +1186,10 @@ extern "C" void lx_ctx_free(lx_ctx *c)
     if (!c) return;
     cudaDeviceSynchronize();
     if (c->scratch) cudaFree(c->scratch);
+    if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+    if (c->b_stream) cudaStreamDestroy(c->b_stream);
+    if (c->b_dev) cudaFree(c->b_dev);
+    if (c->b_host) cudaFreeHost(c->b_host);
     if (c->d_in) cudaFree(c->d_in);
     if (c->d_out) cudaFree(c->d_out);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -1150,6 +1233,54 @@ static int grow(void **p, size_t *have, size_t need)
     return rc;
 }
 
+// CTAs per SM of the tile kernel for a table form and dynamic shared size
+// (also raises the kernel's dynamic shared-memory limit on first use).
+static int occupancy_for(lx_ctx *c, int form, uint32_t smem, int *occ)
+{
+    const uint64_t key = ((uint64_t)form << 32) | smem;
+    for (auto &kv : c->occupancy)
+        if (kv.first == key) {
+            *occ = kv.second;
+            return LX_OK;
+        }
+    cudaError_t e;
+    int o = 0;
+    if (form == FORM_BYTE) {
+        e = cudaFuncSetAttribute(lex_tiles<FORM_BYTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_tiles<FORM_BYTE>, NT, smem);
+    } else {
+        e = cudaFuncSetAttribute(lex_tiles<FORM_CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_tiles<FORM_CLASS>, NT, smem);
+    }
+    if (e != cudaSuccess) return LX_E_CUDA;
+    if (o < 1) o = 1;
+    c->occupancy.emplace_back(key, o);
+    *occ = o;
+    return LX_OK;
+}
+
+// Table fields of the launch parameters for one token set and mode.
+static void set_table_params(Params &P, const HostTable &h, const void *blob)
+{
+    P.blob = static_cast<const uint8_t *>(blob);
+    P.blob_bytes = (uint32_t)h.blob.size();
+    P.table_bytes = h.table_bytes;
+    P.kind_off = h.kind_off;
+    P.cmap_off = h.cmap_off;
+    P.cert_off = h.cert_off;
+    P.ncols = h.ncols;
+    P.p_start = h.p_start;
+    P.p_flag = h.p_flag;
+    P.p_slow = h.p_slow;
+    P.p_pre = h.p_pre;
+}
+
+static void launch_tiles(int form, uint32_t grid, uint32_t smem, cudaStream_t st, const Params &P)
+{
+    if (form == FORM_BYTE) lex_tiles<FORM_BYTE><<<grid, NT, smem, st>>>(P);
+    else lex_tiles<FORM_CLASS><<<grid, NT, smem, st>>>(P);
+}
+
 // Launch the tile kernel and read back its result record.
 static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
                       uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
@@ -1175,43 +1306,28 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     const size_t spill_off = (need + 255) & ~(size_t)255;
 
     Params P;
-    P.in = d_in;
-    P.n = n;
-    P.blob = static_cast<const uint8_t *>(blobs[mode]);
-    P.blob_bytes = (uint32_t)h.blob.size();
-    P.table_bytes = h.table_bytes;
-    P.kind_off = h.kind_off;
-    P.cmap_off = h.cmap_off;
-    P.cert_off = h.cert_off;
-    P.ncols = h.ncols;
-    P.p_start = h.p_start;
-    P.p_flag = h.p_flag;
-    P.p_slow = h.p_slow;
-    P.p_pre = h.p_pre;
+    P.one.in = d_in;
+    P.one.n = n;
+    P.one.first_tile = 0;
+    P.one.tma = ((reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1u : 0u;
+    P.docs = nullptr;
+    P.tile_doc = nullptr;
+    P.dres = nullptr;
+    P.prev = nullptr;
+    P.n_prev = 0;
+    set_table_params(P, h, blobs[mode]);
     P.out_kinds = d_kinds;
     P.out_lens = d_lens;
     P.cap = capacity;
     P.n_tiles = n_tiles;
-    P.tma = ((reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1 : 0;
     P.timeout_ns = c->timeout_ns;
 
     const Layout L = make_layout(P.blob_bytes);
     const int form = h.form;
-    if (!c->occupancy[form]) {
-        cudaError_t e;
-        if (form == FORM_BYTE) {
-            e = cudaFuncSetAttribute(lex_tiles<FORM_BYTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occupancy[form], lex_tiles<FORM_BYTE>, NT, L.total);
-        } else {
-            e = cudaFuncSetAttribute(lex_tiles<FORM_CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occupancy[form], lex_tiles<FORM_CLASS>, NT, L.total);
-        }
-        if (e != cudaSuccess) return LX_E_CUDA;
-        if (c->occupancy[form] < 1) c->occupancy[form] = 1;
-    }
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(n_tiles, (uint64_t)c->occupancy[form] * c->num_sms);
+    int occ = 0;
+    rc = occupancy_for(c, form, L.total, &occ);
+    if (rc != LX_OK) return rc;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(n_tiles, (uint64_t)occ * c->num_sms);
 
     // scratch: result record, tile counter, status words, then the spill regions
     rc = grow(&c->scratch, &c->scratch_bytes, spill_off + sizeof(uint32_t) * (size_t)SPILL_WORDS * grid);
@@ -1226,8 +1342,7 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     rc = cuda_err(cudaMemsetAsync(c->scratch, 0, need, st));
     if (rc != LX_OK) return rc;
     if (c->timing) cudaEventRecord(c->ev[0], st);
-    if (form == FORM_BYTE) lex_tiles<FORM_BYTE><<<grid, NT, L.total, st>>>(P);
-    else lex_tiles<FORM_CLASS><<<grid, NT, L.total, st>>>(P);
+    launch_tiles(form, grid, L.total, st, P);
     rc = cuda_err(cudaGetLastError());
     if (c->timing) cudaEventRecord(c->ev[1], st);
     if (rc != LX_OK) return rc;
@@ -1294,6 +1409,236 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
         if (r2 != LX_OK) return r2;
     }
     return rc;
+}
+
+
+// ---------------------------------------------------------------------------
+// lx_lex_batch
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchGroup {
+    uint32_t set;
+    uint32_t doc_begin, doc_end;   // range in the grouped document order
+    uint32_t tile_begin, n_tiles;  // range in the concatenated status / tile_doc arrays
+};
+
+// Byte offsets of the batch scratch (device) and staging (pinned host).
+struct BatchLayout {
+    size_t res, cnt, dres, status, zero_end;   // zeroed per call: [0, zero_end)
+    size_t docs, tdoc, up_end;                 // uploaded per call: [docs, up_end)
+    size_t spill, dev_total;
+    // host staging: [0, up_bytes) descriptors, then [down, down + zero_end) records
+    size_t up_bytes, down, host_total;
+};
+
+BatchLayout batch_layout(uint32_t G, uint32_t D, uint64_t TT, uint32_t grid)
+{
+    auto al = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
+    BatchLayout B;
+    B.res = 0;
+    B.cnt = al(sizeof(Result) * G, 64);
+    B.dres = al(B.cnt + 4 * (size_t)G, 64);
+    B.status = al(B.dres + sizeof(DocResult) * D, 64);
+    B.zero_end = B.status + 8 * TT;
+    B.docs = al(B.zero_end, 256);
+    B.tdoc = al(B.docs + sizeof(DocDesc) * D, 64);
+    B.up_end = B.tdoc + 4 * TT;
+    B.spill = al(B.up_end, 256);
+    B.dev_total = B.spill + sizeof(uint32_t) * (size_t)SPILL_WORDS * grid;
+    B.up_bytes = B.up_end - B.docs;
+    B.down = al(B.up_bytes, 64);
+    B.host_total = B.down + B.status;
+    return B;
+}
+
+int grow_host(void **p, size_t *have, size_t need)
+{
+    if (*have >= need) return LX_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *have = 0;
+    if (cudaMallocHost(p, need) != cudaSuccess) return LX_E_NOMEM;
+    *have = need;
+    return LX_OK;
+}
+
+}  // namespace
+
+extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, const lx_doc *docs,
+                            uint32_t n_docs, int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity,
+                            lx_doc_result *results, uint64_t *n_total, void *stream)
+{
+    if (!c || !n_total || (n_docs && (!docs || !results)) || (n_sets && !sets)) return LX_E_INVAL;
+    if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
+    if (capacity && (!d_kinds || !d_lens)) return LX_E_INVAL;
+    for (uint32_t s = 0; s < n_sets; s++) {
+        if (!sets[s]) return LX_E_INVAL;
+        if (sets[s]->tab[mode].status != LX_OK) return sets[s]->tab[mode].status;
+    }
+    for (uint32_t i = 0; i < n_docs; i++) {
+        if (docs[i].set >= n_sets || docs[i].reserved != 0) return LX_E_INVAL;
+        if (docs[i].n && !docs[i].data) return LX_E_INVAL;
+        results[i] = lx_doc_result{0, 0, 0};
+    }
+    *n_total = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
+
+    // group the non-empty documents by token set, keeping their order
+    std::vector<uint32_t> order;
+    std::vector<BatchGroup> groups;
+    uint64_t TT = 0;
+    for (uint32_t s = 0; s < n_sets; s++) {
+        BatchGroup g{s, (uint32_t)order.size(), 0, (uint32_t)0, 0};
+        uint64_t tiles = 0;
+        for (uint32_t i = 0; i < n_docs; i++)
+            if (docs[i].set == s && docs[i].n) {
+                order.push_back(i);
+                tiles += (docs[i].n + TILE - 1) / TILE;
+            }
+        g.doc_end = (uint32_t)order.size();
+        if (g.doc_end == g.doc_begin) continue;
+        if (tiles > 0xFFFFFFF0ull || TT + tiles > 0xFFFFFFF0ull) return LX_E_INVAL;
+        g.tile_begin = (uint32_t)TT;
+        g.n_tiles = (uint32_t)tiles;
+        TT += tiles;
+        groups.push_back(g);
+    }
+    if (groups.empty()) return LX_OK;
+    const uint32_t G = (uint32_t)groups.size(), D = (uint32_t)order.size();
+
+    // tables, occupancy and grid per group
+    std::vector<void *> blob(G);
+    std::vector<uint32_t> grid(G), smem(G);
+    uint32_t grid_max = 0;
+    for (uint32_t k = 0; k < G; k++) {
+        const lx_tokenset *ts = sets[groups[k].set];
+        void *blobs[3];
+        int rc = ensure_device_tables(ts, dev, blobs);
+        if (rc != LX_OK) return rc;
+        blob[k] = blobs[mode];
+        const HostTable &h = ts->tab[mode];
+        smem[k] = make_layout((uint32_t)h.blob.size()).total;
+        int occ = 0;
+        rc = occupancy_for(c, h.form, smem[k], &occ);
+        if (rc != LX_OK) return rc;
+        grid[k] = (uint32_t)std::min<uint64_t>(groups[k].n_tiles, (uint64_t)occ * c->num_sms);
+        grid_max = std::max(grid_max, grid[k]);
+    }
+    const BatchLayout B = batch_layout(G, D, TT, grid_max);
+    bool moved = false;
+    {
+        void *old_d = c->b_dev, *old_h = c->b_host;
+        int rc = grow(&c->b_dev, &c->b_dev_bytes, B.dev_total);
+        if (rc == LX_OK) rc = grow_host(&c->b_host, &c->b_host_bytes, B.host_total);
+        if (rc != LX_OK) return rc;
+        moved = old_d != c->b_dev || old_h != c->b_host;
+    }
+    uint8_t *dv = static_cast<uint8_t *>(c->b_dev);
+    uint8_t *hs = static_cast<uint8_t *>(c->b_host);
+
+    // descriptors into the pinned staging area
+    DocDesc *h_docs = reinterpret_cast<DocDesc *>(hs);
+    uint32_t *h_tdoc = reinterpret_cast<uint32_t *>(hs + (B.tdoc - B.docs));
+    for (const BatchGroup &g : groups) {
+        uint32_t t = 0;
+        for (uint32_t j = g.doc_begin; j < g.doc_end; j++) {
+            const lx_doc &d = docs[order[j]];
+            const uint32_t nt = (uint32_t)((d.n + TILE - 1) / TILE);
+            h_docs[j] = DocDesc{d.data, d.n, t, (reinterpret_cast<uintptr_t>(d.data) & 15u) == 0 ? 1u : 0u};
+            for (uint32_t k = 0; k < nt; k++) h_tdoc[g.tile_begin + t + k] = j - g.doc_begin;
+            t += nt;
+        }
+    }
+
+    // the graph's shape: everything baked into its nodes
+    std::vector<uint64_t> key = {G, D, TT, (uint64_t)mode, (uint64_t)(uintptr_t)d_kinds, (uint64_t)(uintptr_t)d_lens,
+                                 capacity, (uint64_t)(uintptr_t)dv, (uint64_t)(uintptr_t)hs, c->timeout_ns};
+    for (uint32_t k = 0; k < G; k++) {
+        key.push_back((uint64_t)(uintptr_t)blob[k]);
+        key.push_back(groups[k].doc_begin);
+        key.push_back(groups[k].n_tiles);
+        key.push_back(grid[k]);
+    }
+    if (moved || key != c->b_key || !c->b_exec) {
+        if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+        c->b_exec = nullptr;
+        c->b_key.clear();
+        if (!c->b_stream && cudaStreamCreateWithFlags(&c->b_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return LX_E_CUDA;
+        cudaStream_t cs = c->b_stream;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LX_E_CUDA;
+        cudaMemsetAsync(dv, 0, B.zero_end, cs);
+        cudaMemcpyAsync(dv + B.docs, hs, B.up_bytes, cudaMemcpyHostToDevice, cs);
+        Result *res = reinterpret_cast<Result *>(dv + B.res);
+        for (uint32_t k = 0; k < G; k++) {
+            const BatchGroup &g = groups[k];
+            const HostTable &h = sets[g.set]->tab[mode];
+            Params P;
+            P.one = DocDesc{nullptr, 0, 0, 0};
+            P.docs = reinterpret_cast<const DocDesc *>(dv + B.docs) + g.doc_begin;
+            P.tile_doc = reinterpret_cast<const uint32_t *>(dv + B.tdoc) + g.tile_begin;
+            P.dres = reinterpret_cast<DocResult *>(dv + B.dres) + g.doc_begin;
+            P.prev = res;
+            P.n_prev = k;
+            set_table_params(P, h, blob[k]);
+            P.out_kinds = d_kinds;
+            P.out_lens = d_lens;
+            P.cap = capacity;
+            P.status = reinterpret_cast<unsigned long long *>(dv + B.status) + g.tile_begin;
+            P.tile_counter = reinterpret_cast<unsigned int *>(dv + B.cnt) + k;
+            P.res = res + k;
+            P.n_tiles = g.n_tiles;
+            P.spill = reinterpret_cast<uint32_t *>(dv + B.spill);
+            P.spill_cap = SPILL_WORDS;
+            P.timeout_ns = c->timeout_ns;
+            launch_tiles(h.form, grid[k], smem[k], cs, P);
+        }
+        cudaMemcpyAsync(hs + B.down, dv, B.zero_end - 8 * TT, cudaMemcpyDeviceToHost, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->b_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->b_exec = nullptr;
+            cudaGetLastError();
+            return LX_E_CUDA;
+        }
+        c->b_key = key;
+    }
+    if (c->timing) cudaEventRecord(c->ev[0], st);
+    int rc = cuda_err(cudaGraphLaunch(c->b_exec, st));
+    if (c->timing) cudaEventRecord(c->ev[1], st);
+    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(st));
+    if (rc != LX_OK) return rc;
+
+    // records
+    const Result *h_res = reinterpret_cast<const Result *>(hs + B.down + B.res);
+    const DocResult *h_dres = reinterpret_cast<const DocResult *>(hs + B.down + B.dres);
+    uint64_t total = 0;
+    for (uint32_t k = 0; k < G; k++) {
+        if (h_res[k].error & ERR_TIMEOUT) return LX_E_TIMEOUT;
+        if (h_res[k].error & ERR_SMEM) return LX_E_TOOBIG;
+        total += h_res[k].total;
+    }
+    for (uint32_t j = 0; j < D; j++) {
+        const DocResult &r = h_dres[j];
+        const lx_doc &d = docs[order[j]];
+        lx_doc_result &o = results[order[j]];
+        if (r.out_off1 == 0) return LX_E_CUDA;   // every document's first tile reports its offset
+        o.out_off = r.out_off1 - 1;
+        if (r.inv_fail_pos) {
+            o.consumed = ~r.inv_fail_pos;
+            o.n_tokens = ~r.inv_fail_tok - o.out_off;
+        } else {
+            o.consumed = d.n;
+            o.n_tokens = r.total;
+        }
+    }
+    *n_total = total;
+    return total > capacity ? LX_E_CAPACITY : LX_OK;
 }
 
 extern "C" const char *lx_strerror(int code)
@@ -1391,8 +1736,15 @@ extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64
     if (rc != LX_OK) return rc;
 
     Params P;
-    P.in = d_in;
-    P.n = n;
+    P.one.in = d_in;
+    P.one.n = n;
+    P.one.first_tile = 0;
+    P.one.tma = ((reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1u : 0u;
+    P.docs = nullptr;
+    P.tile_doc = nullptr;
+    P.dres = nullptr;
+    P.prev = nullptr;
+    P.n_prev = 0;
     P.blob = scr;
     P.blob_bytes = (uint32_t)h.blob.size();
     P.table_bytes = h.table_bytes;
@@ -1413,7 +1765,6 @@ extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64
     P.spill = nullptr;   // no spill region: long ranges take the generic walker
     P.spill_cap = 0;
     P.n_tiles = n_tiles;
-    P.tma = ((reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1 : 0;
     P.timeout_ns = 20ull * 1000 * 1000 * 1000;
 
     const Layout L = make_layout(P.blob_bytes);
