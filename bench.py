@@ -176,6 +176,170 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+BATCH_NAMES = ("json", "clike")
+
+
+def run_batch(args, rank, world, local):
+    """The batched workload: 4096 documents (lognormal sizes, median 128 KiB,
+    sigma 1.66, clamped to [1 KiB, 16 MiB]), each JSON or C-like, lexed
+    filtered modulo I by one lx_lex_batch call per step; also timed as 4096
+    separate lx_lex calls."""
+    import numpy as np
+    from lexinputs import corpus, tokensets
+    spec = corpus.batch_spec()
+    n_docs = len(spec)
+    total = sum(sz for _, sz, _ in spec)
+    metric = f"input GB/s lexed ({n_docs}-document batch, JSON + C-like, filtered modulo I, bit-exact)"
+    wl = f"batch_{n_docs}docs_json_clike_filtered_modulo"
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        sample, tok, times = 0, 0, []
+        host, offs = corpus.generate_batch(spec[:256])
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            nb = nt = 0
+            for (nm, sz, _), o in zip(spec[:256], offs):
+                if nb >= args.ref_sample_mib * MiB:
+                    break
+                dfa = tokensets.tokenset(nm)
+                k, l, con = oracle.lex(dfa, host[o:o + sz])
+                k, _ = oracle.discard(k, l, tokensets.discarded_kinds(nm), dfa.n_kinds)
+                nb += sz
+                nt += k.size
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+            sample, tok = nb, nt
+        value = sample * len(times) / sum(times) / 1e9
+        print(json.dumps({
+            "metric": metric, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl, "sample": f"leading documents of the batch, {sample} bytes per step"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"leading documents, {sample} bytes per step, serial scan + pi_I"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2608_03473_gb300 as lg
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    host, offs = corpus.generate_batch(spec)
+    sets = [lg.lx_compile_tokenset(tokensets.tokenset(n), tokensets.discarded_kinds(n)) for n in BATCH_NAMES]
+    ctx = lg.lx_ctx_create()
+    lg.lx_ctx_enable_timing(ctx, True)
+    stream = torch.cuda.current_stream()
+    d = torch.from_numpy(host).to("cuda")
+    cap = total // 3 + 4096
+    d_k = torch.empty(cap, dtype=torch.int16, device="cuda")
+    d_l = torch.empty(cap, dtype=torch.int32, device="cuda")
+    docs = [((d.data_ptr() + o, sz), BATCH_NAMES.index(nm)) for (nm, sz, _), o in zip(spec, offs)]
+    mode = lg.LX_FILTERED_MODULO
+    rc, n_tok, res = lg.lx_lex_batch(ctx, sets, docs, mode, d_k, d_l, stream=stream)
+    assert rc == 0, lg.lx_strerror(rc)
+    assert all(con == sz for (_, sz, _), (_, _, con) in zip(spec, res))
+    if args.check:
+        import oracle
+        kk = d_k[:n_tok].cpu().numpy().view(np.uint16)
+        ll = d_l[:n_tok].cpu().numpy().view(np.uint32)
+        for (nm, sz, _), o, (off, nt, con) in zip(spec, offs, res):
+            dfa = tokensets.tokenset(nm)
+            k, l, c = oracle.lex(dfa, host[o:o + sz])
+            k, l = oracle.discard(k, l, tokensets.discarded_kinds(nm), dfa.n_kinds)
+            assert c == con and k.size == nt
+            assert np.array_equal(kk[off:off + nt], k) and np.array_equal(ll[off:off + nt], l)
+    batch = lg.BatchDocs(sets, docs)   # descriptors built once, as a serving loop would
+    for _ in range(args.warmup):
+        lg.lx_lex_batch(ctx, sets, batch, mode, d_k, d_l, stream=stream, want_results=False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    graph_ms = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rc, nt2, _ = lg.lx_lex_batch(ctx, sets, batch, mode, d_k, d_l, stream=stream, want_results=False)
+        graph_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
+        if rc != 0 or nt2 != n_tok:
+            raise RuntimeError(f"step failed: {rc} {nt2}")
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * total * args.steps / (total_ms / 1e3) / 1e9
+    g_ms = statistics.mean(graph_ms)
+    alg = total + 6 * n_tok
+    peak, peak_src = measured_peak_gbs()
+
+    # the same documents as separate lx_lex calls (one pass)
+    views = [(d[o:o + sz], BATCH_NAMES.index(nm)) for (nm, sz, _), o in zip(spec, offs)]
+    for v, si in views[:64]:
+        lg.lx_lex(ctx, sets[si], v, mode, d_k, d_l, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for v, si in views:
+        rc, _, _ = lg.lx_lex(ctx, sets[si], v, mode, d_k, d_l, stream=stream)
+        assert rc == 0
+    torch.cuda.synchronize()
+    sep_s = time.perf_counter() - t0
+
+    # end to end: pinned host documents in, tokens out, through the binding
+    h_in = torch.from_numpy(host).pin_memory()
+    h_k = torch.empty(cap, dtype=torch.int16).pin_memory()
+    h_l = torch.empty(cap, dtype=torch.int32).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        d.copy_(h_in, non_blocking=True)
+        rc, nt3, _ = lg.lx_lex_batch(ctx, sets, batch, mode, d_k, d_l, stream=stream, want_results=False)
+        h_k[:nt3].copy_(d_k[:nt3], non_blocking=True)
+        h_l[:nt3].copy_(d_l[:nt3], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": wl, "documents": n_docs, "bytes": total, "tokens_kept": n_tok,
+                       "sizes": "lognormal median 128 KiB sigma 1.66 clamped to [1 KiB, 16 MiB]",
+                       "seed": hex(corpus.BATCH_SEED), "mode": "LX_FILTERED_MODULO",
+                       "l2": "inputs larger than L2; no flush between steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "tokens_per_s": world * n_tok * args.steps / (total_ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": alg / (g_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (g_ms / 1e3) / 1e9 / peak, "traffic": None,
+                         "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "kernel": "lex_tiles (one launch per token set, in one CUDA graph)",
+                         "kernel_ms": g_ms, "algorithmic_bytes": alg},
+            "separate_calls": {"value": total / sep_s / 1e9, "unit": "GB/s", "ms": 1e3 * sep_s,
+                               "what": f"{n_docs} lx_lex calls, one per document"},
+            "cpu_baseline": None,
+            "e2e": {"value": world * total / (e2e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": total,
+                    "d2h_bytes_per_step": 6 * n_tok, "ms_per_step": e2e_ms,
+                    "api": "torch pinned copies + lx_lex_batch"},
+            "gpu_launches": len(BATCH_NAMES) * args.steps,
+            "clocks": clocks,
+        }), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,7 +348,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--size-mib", type=int, default=512)
-    ap.add_argument("--workload", default="json", choices=["json", "clike"])
+    ap.add_argument("--workload", default="json", choices=["json", "clike", "batch"])
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="also compare the output with the oracle")
@@ -192,6 +356,9 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     rank, world, local = dist_env()
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

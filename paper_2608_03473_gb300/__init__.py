@@ -291,26 +291,41 @@ def lx_lex_noalloc(ts: Tokenset, d_in, mode: int, d_kinds, d_lens, n: Optional[i
     return rc, nt.value, con.value
 
 
+class BatchDocs:
+    """The C arrays of one batch (token sets, document descriptors, result
+    records), built once so that repeated lx_lex_batch calls on the same
+    batch do no per-document Python work.  ``docs`` is a sequence of (device
+    uint8 tensor or (pointer, n), set index)."""
+
+    def __init__(self, sets, docs):
+        self.sets = list(sets)
+        self.n_sets, self.n_docs = len(self.sets), len(docs)
+        self.set_arr = (ctypes.c_void_p * max(self.n_sets, 1))(*[ts.handle for ts in self.sets])
+        self.doc_arr = (_Doc * max(self.n_docs, 1))()
+        for i, (buf, set_idx) in enumerate(docs):
+            if isinstance(buf, tuple):
+                ptr, n = buf
+            else:
+                ptr, n = buf.data_ptr(), buf.numel()
+            self.doc_arr[i] = _Doc(ptr if n else None, int(n), int(set_idx), 0)
+        self.res_arr = (_DocResult * max(self.n_docs, 1))()
+
+    def results(self):
+        r = self.res_arr
+        return [(r[i].out_off, r[i].n_tokens, r[i].consumed) for i in range(self.n_docs)]
+
+
 def lx_lex_batch(ctx: Ctx, sets, docs, mode: int, d_kinds, d_lens, capacity: Optional[int] = None,
-                 stream=None):
+                 stream=None, want_results: bool = True):
     """Lex many documents in one graph launch.  ``sets`` is a sequence of
-    Tokenset; ``docs`` a sequence of (device uint8 tensor or (pointer, n),
-    set index).  Returns (status, n_total, results) with results a list of
-    (out_off, n_tokens, consumed) per document, in the order given."""
+    Tokenset (ignored when ``docs`` is a BatchDocs); ``docs`` a BatchDocs or
+    a sequence of (device uint8 tensor or (pointer, n), set index).  Returns
+    (status, n_total, results) with results a list of (out_off, n_tokens,
+    consumed) per document, in the order given (None if not wanted)."""
     lib = load_library()
-    n_sets, n_docs = len(sets), len(docs)
-    set_arr = (ctypes.c_void_p * max(n_sets, 1))(*[ts.handle for ts in sets])
-    doc_arr = (_Doc * max(n_docs, 1))()
-    for i, (buf, set_idx) in enumerate(docs):
-        if isinstance(buf, tuple):
-            ptr, n = buf
-        else:
-            ptr, n = buf.data_ptr(), buf.numel()
-        doc_arr[i] = _Doc(ptr if n else None, int(n), int(set_idx), 0)
-    res_arr = (_DocResult * max(n_docs, 1))()
+    b = docs if isinstance(docs, BatchDocs) else BatchDocs(sets, docs)
     cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
     total = ctypes.c_uint64()
-    rc = lib.lx_lex_batch(ctx.handle, set_arr, n_sets, doc_arr, n_docs, int(mode), d_kinds.data_ptr(),
-                          d_lens.data_ptr(), cap, res_arr, ctypes.byref(total), _stream_handle(stream))
-    results = [(res_arr[i].out_off, res_arr[i].n_tokens, res_arr[i].consumed) for i in range(n_docs)]
-    return rc, total.value, results
+    rc = lib.lx_lex_batch(ctx.handle, b.set_arr, b.n_sets, b.doc_arr, b.n_docs, int(mode), d_kinds.data_ptr(),
+                          d_lens.data_ptr(), cap, b.res_arr, ctypes.byref(total), _stream_handle(stream))
+    return rc, total.value, (b.results() if want_results else None)

@@ -141,3 +141,12 @@ def test_batch_matches_single_calls(env):
         assert rc1 == 0 and nt1 == nt and con1 == con
         assert np.array_equal(kk[:nt].cpu().numpy().view(np.uint16), k[out_off:out_off + nt])
         assert np.array_equal(ll[:nt].cpu().numpy().view(np.uint32), l[out_off:out_off + nt])
+
+
+def test_full_size_batch_4096_documents(env):
+    """The batched bench workload (4096 documents, ~1.9 GiB, JSON + C-like)
+    in the bench's launch configuration, every document compared in full."""
+    spec = corpus.batch_spec()
+    host, offs = corpus.generate_batch(spec)
+    out = _run_batch(env, spec, host, offs, 2, capacity=sum(s for _, s, _ in spec) // 3 + 4096)
+    _check(spec, host, offs, 2, *out)
