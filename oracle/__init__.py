@@ -15,8 +15,12 @@ reference run used by the tests:
                         side of Theorems 1 and 3.
 * ``plan``           -- the planner of Section 6: slide each of k-1 equal-division
                         targets forward to the next useful certified byte.
+* ``contexts``       -- (submodule) entry contexts of the serial scan, their
+                        candidate sets and chunk runs entered in a context:
+                        splitting a token set with no certified byte.
 
 Parity pins: tests/test_oracle_pins.py (worked examples of the paper),
+tests/test_oracle_contexts.py (exhaustive checks of the entry contexts),
 tests/test_oracle_bruteforce.py (exhaustive checks on tiny token sets),
 tests/test_oracle_re.py (Python ``re.fullmatch`` cross-check of the scanner).
 """
