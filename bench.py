@@ -28,15 +28,20 @@ sys.path.insert(0, ROOT)
 
 MiB = 1 << 20
 CUTS = {"json": "tab, newline, carriage return (certified modulo I = {ws})",
-        "clike": "newline (certified modulo I = {ws, line comment})"}
+        "clike": "newline (certified modulo I = {ws, line comment})",
+        "clike_block": "none certified: chunk starts every 4096 B after the byte with the fewest entry contexts"}
 
 
 def metric_name(workload, mib):
+    if workload == "clike_block":
+        return f"input GB/s lexed ({mib} MiB C-like with block comments, full stream, entry-context enumeration, bit-exact)"
     label = {"json": "JSON", "clike": "C-like"}[workload]
     return f"input GB/s lexed ({mib} MiB {label}, filtered modulo I, bit-exact)"
 
 
 def workload_name(workload, mib):
+    if workload == "clike_block":
+        return f"clike_block_{mib}mib_full_enumerative"
     return f"{workload}_{mib}mib_filtered_modulo"
 
 
@@ -137,7 +142,7 @@ def time_oracle(w, dfa, disc, sample_bytes, reps=1):
     for _ in range(reps):
         t0 = time.perf_counter()
         k, l, con = oracle.lex(dfa, s)
-        k2, _ = oracle.discard(k, l, disc, dfa.n_kinds)
+        k2 = k if disc is None else oracle.discard(k, l, disc, dfa.n_kinds)[0]
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
         tokens = k2.size
@@ -150,7 +155,7 @@ def run_reference(args, rank, world):
         return
     from lexinputs import corpus, tokensets
     dfa = tokensets.tokenset(args.workload)
-    disc = tokensets.discarded_kinds(args.workload)
+    disc = None if args.workload == "clike_block" else tokensets.discarded_kinds(args.workload)
     sample = args.ref_sample_mib * MiB
     w = corpus.generate(args.workload, sample)
     times = []
@@ -348,7 +353,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--size-mib", type=int, default=512)
-    ap.add_argument("--workload", default="json", choices=["json", "clike", "batch"])
+    ap.add_argument("--workload", default="json", choices=["json", "clike", "clike_block", "batch"])
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="also compare the output with the oracle")
@@ -383,26 +388,29 @@ def main():
     ctx = lg.lx_ctx_create()
     lg.lx_ctx_enable_timing(ctx, True)
     stream = torch.cuda.current_stream()
+    refused = args.workload == "clike_block"
+    lex_fn = lg.lx_lex_enumerative if refused else lg.lx_lex
 
     d_in = torch.from_numpy(w).to("cuda")
-    cap = n // 4 + 1024
+    cap = (n // 2 if refused else n // 4) + 1024   # the full stream keeps whitespace tokens
     d_k = torch.empty(cap, dtype=torch.int16, device="cuda")
     d_l = torch.empty(cap, dtype=torch.int32, device="cuda")
-    mode = lg.LX_FILTERED_MODULO
-    rc, nt, con = lg.lx_lex(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
+    mode = lg.LX_FULL_EXACT if refused else lg.LX_FILTERED_MODULO
+    rc, nt, con = lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
     assert rc == 0, lg.lx_strerror(rc)
     assert con == n
 
     if args.check:
         import oracle
         k, l, c = oracle.lex(dfa, w)
-        k, l = oracle.discard(k, l, disc, dfa.n_kinds)
+        if not refused:
+            k, l = oracle.discard(k, l, disc, dfa.n_kinds)
         assert c == con and k.size == nt
         assert np.array_equal(d_k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), k)
         assert np.array_equal(d_l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), l)
 
     for _ in range(args.warmup):
-        lg.lx_lex(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
+        lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -415,7 +423,7 @@ def main():
     kernel_ms = []
     ev0.record(stream)
     for _ in range(args.steps):
-        rc, nt2, con2 = lg.lx_lex(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
+        rc, nt2, con2 = lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
         kernel_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
         if rc != 0 or nt2 != nt or con2 != con:
             raise RuntimeError(f"step failed: {rc} {nt2} {con2}")
@@ -444,14 +452,24 @@ def main():
     h_in = torch.from_numpy(w).pin_memory()
     h_k = torch.empty(cap, dtype=torch.int16).pin_memory()
     h_l = torch.empty(cap, dtype=torch.int32).pin_memory()
+    def host_step():
+        if not refused:
+            return lg.lx_lex_host(ctx, ts, h_in, mode, h_k, h_l, stream=stream)
+        d_in.copy_(h_in, non_blocking=True)
+        r = lg.lx_lex_enumerative(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
+        h_k[:r[1]].copy_(d_k[:r[1]], non_blocking=True)
+        h_l[:r[1]].copy_(d_l[:r[1]], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return r
+
     for _ in range(2):
-        lg.lx_lex_host(ctx, ts, h_in, mode, h_k, h_l, stream=stream)
+        host_step()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.e2e_steps):
-        rc, nt3, con3 = lg.lx_lex_host(ctx, ts, h_in, mode, h_k, h_l, stream=stream)
+        rc, nt3, con3 = host_step()
         assert rc == 0 and nt3 == nt and con3 == con
     e1.record(stream)
     torch.cuda.synchronize()
@@ -466,6 +484,7 @@ def main():
         cpu = None
         if not args.no_cpu_baseline:
             sample = min(n, 256 * MiB)
+            sample = min(sample, 64 * MiB) if refused else sample
             sb, stok, sdt = time_oracle(w, dfa, disc, sample)
             cpu = {"value": sb / sdt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                    "sample": f"first {sample // MiB} MiB of the corpus, one pass, serial scan + pi_I "
@@ -475,7 +494,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": workload_name(args.workload, args.size_mib), "bytes": n, "tokens_kept": nt,
-                       "mode": "LX_FILTERED_MODULO", "cuts": CUTS[args.workload],
+                       "mode": "LX_FULL_EXACT" if refused else "LX_FILTERED_MODULO", "cuts": CUTS[args.workload],
                        "seed": hex(corpus.WORKLOADS[args.workload][2]), "sha256": sha,
                        "l2": f"inputs ({args.size_mib} MiB) larger than L2 (129 MB); no flush between steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -484,12 +503,14 @@ def main():
                          "frac": achieved / peak,
                          "traffic": profiled_traffic(workload_name(args.workload, args.size_mib)),
                          "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                         "kernel": "lex_tiles", "kernel_ms": k_ms,
+                         "kernel": "en_plan + en_enumerate + en_resolve + en_emit" if refused else "lex_tiles",
+                         "kernel_ms": k_ms,
                          "algorithmic_bytes": alg_bytes, "frac_of_nominal_8tbs": achieved / 8000.0},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": n, "d2h_bytes_per_step": 6 * nt + 32,
-                    "ms_per_step": e2e_ms, "api": "lx_lex_host"},
-            "gpu_launches": args.steps,
+                    "ms_per_step": e2e_ms,
+                    "api": "torch pinned copies + lx_lex_enumerative" if refused else "lx_lex_host"},
+            "gpu_launches": (4 if refused else 1) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -128,6 +128,20 @@ int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, 
 void lx_tokenset_free(lx_tokenset *ts);
 
 /*
+ * lx_tokenset_scan_table -- copy the plain DFA scan table that
+ * lx_lex_enumerative stages in shared memory (for host-side inspection and
+ * tests): up to `cap` bytes into `out`, and meta[0..8] = {bytes, states,
+ * classes, q0, next offset, accept offset, candidate-begin offset, candidate
+ * offset, longest candidate list}.  Layout: class u8[256]; next u16[C*S]
+ * (0xFFFF = undefined or leaving Q+); accept u16[S] (kind | 0x8000 when not
+ * discarded, 0x7FFF = not accepting); cand_begin u16[257]; cand u16[...]:
+ * for byte b the ascending states delta+(q, b), q in Q+, at
+ * [cand_begin[b], cand_begin[b+1]).  Returns LX_E_TOOBIG when no such table
+ * was built (too large), else LX_OK.
+ */
+int lx_tokenset_scan_table(const lx_tokenset *ts, void *out, uint32_t cap, uint32_t *meta, uint32_t meta_len);
+
+/*
  * lx_ctx_create -- a lexing context bound to the current CUDA device.  It owns
  * the scratch memory of lx_lex (per-tile look-back status words, a tile
  * counter and a result record), grown on demand with cudaMalloc.
@@ -188,6 +202,26 @@ int lx_lex(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
 int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_t n, int mode,
                 uint16_t *h_kinds, uint32_t *h_lens, uint64_t capacity, uint64_t *n_tokens,
                 uint64_t *consumed, void *stream);
+
+/*
+ * lx_lex_enumerative -- lx_lex for token sets that certify no byte (the
+ * paper's refused sets, Table 2, where lx_lex can only run one chunk).
+ *
+ * The input is split every 4096 bytes, each start placed within the first
+ * 256 bytes of its target right after the byte with the fewest possible entry
+ * contexts (at most 8: BOUNDARY or a state delta+(q, b) of Q+).  Every chunk
+ * is scanned from every candidate context (counting kept tokens, recording
+ * the context at the next start); the chain of exit contexts from BOUNDARY at
+ * offset 0 then fixes each chunk's true context and output offset, and each
+ * chunk is scanned once more to write its tokens.  Output and errors as
+ * lx_lex: tok(w) with LX_FULL_EXACT, pi_I(tok(w)) with either filtered mode
+ * (the certificates play no part), con(w) in *consumed (Corollary 1).
+ * Works for any token set; LX_E_TOOBIG when its plain DFA table exceeds the
+ * shared-memory budget.  Synchronizes `stream`.
+ */
+int lx_lex_enumerative(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+                       uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
+                       uint64_t *consumed, void *stream);
 
 /*
  * lx_lex_batch -- lex many documents, each with its own token set, in one

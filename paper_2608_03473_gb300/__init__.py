@@ -46,9 +46,10 @@ LX_FILTERED_MODULO = 2
 
 # every function declared in include/lexgpu.h
 EXPORTED = (
-    "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_free",
+    "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_scan_table",
+    "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
-    "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch",
+    "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative",
     "lx_strerror",
 )
 
@@ -96,6 +97,7 @@ def load_library(path: Optional[str] = None):
             "lx_certificates": (i32, [vp, vp, vp]),
             "lx_tokenset_info": (i32, [vp, i32, vp, vp, vp, vp, vp]),
             "lx_tokenset_table": (i32, [vp, i32, vp, u32, vp, u32]),
+            "lx_tokenset_scan_table": (i32, [vp, vp, u32, vp, u32]),
             "lx_tokenset_free": (None, [vp]),
             "lx_ctx_create": (i32, [vp]),
             "lx_ctx_free": (None, [vp]),
@@ -106,6 +108,7 @@ def load_library(path: Optional[str] = None):
             "lx_lex_host": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_noalloc": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_batch": (i32, [vp, vp, u32, vp, u32, i32, vp, vp, u64, vp, vp, vp]),
+            "lx_lex_enumerative": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_strerror": (ctypes.c_char_p, [i32]),
         }
         for name, (res, args) in sig.items():
@@ -329,3 +332,27 @@ def lx_lex_batch(ctx: Ctx, sets, docs, mode: int, d_kinds, d_lens, capacity: Opt
     rc = lib.lx_lex_batch(ctx.handle, b.set_arr, b.n_sets, b.doc_arr, b.n_docs, int(mode), d_kinds.data_ptr(),
                           d_lens.data_ptr(), cap, b.res_arr, ctypes.byref(total), _stream_handle(stream))
     return rc, total.value, (b.results() if want_results else None)
+
+
+def lx_lex_enumerative(ctx: Ctx, ts: Tokenset, d_in, mode: int, d_kinds, d_lens, n: Optional[int] = None,
+                       capacity: Optional[int] = None, stream=None) -> Tuple[int, int, int]:
+    """Lex a device buffer whose token set certifies no byte by enumerating
+    chunk entry contexts.  Returns (status, n_tokens, consumed) as lx_lex."""
+    lib = load_library()
+    n = d_in.numel() if n is None else int(n)
+    cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
+    nt, con = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib.lx_lex_enumerative(ctx.handle, ts.handle, d_in.data_ptr(), n, int(mode), d_kinds.data_ptr(),
+                                d_lens.data_ptr(), cap, ctypes.byref(nt), ctypes.byref(con), _stream_handle(stream))
+    return rc, nt.value, con.value
+
+
+def lx_tokenset_scan_table(ts: Tokenset):
+    """(status, blob uint8 array, meta dict) of the plain DFA scan table."""
+    lib = load_library()
+    meta = (ctypes.c_uint32 * 9)()
+    lib.lx_tokenset_scan_table(ts.handle, None, 0, meta, 9)
+    blob = np.zeros(max(meta[0], 1), np.uint8)
+    rc = lib.lx_tokenset_scan_table(ts.handle, blob.ctypes.data, meta[0], meta, 9)
+    keys = ("bytes", "S", "C", "q0", "next_off", "acc_off", "cbeg_off", "cand_off", "max_cand")
+    return rc, blob[:meta[0]], dict(zip(keys, list(meta)))

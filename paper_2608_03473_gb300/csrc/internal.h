@@ -62,9 +62,28 @@ struct HostTable {
     std::vector<uint8_t> blob;   // everything above, 16-byte padded
 };
 
+// Plain DFA tables for scans entered in a context (splitting an input whose
+// token set certifies no byte): the class map, the next state per (class,
+// state) with targets outside Q+ made undefined (no accepting state is
+// reachable from them, so the longest match is unchanged), an accept word per
+// state (bits 0..14 kind or KIND_NONE, bit 15 kept modulo I), and for every
+// byte b the ascending list of states delta+(q, b), q in Q+ -- the mid-token
+// contexts possible right after b.
+//   [class u8 x 256][next u16 x C*S][accept u16 x S][cand_begin u16 x 257][cand u16 ...]
+struct ScanTable {
+    int status = LX_OK;          // LX_E_TOOBIG when it does not fit shared memory
+    uint32_t S = 0, C = 0, q0 = 0;
+    uint32_t next_off = 0, acc_off = 0, cbeg_off = 0, cand_off = 0;
+    uint32_t max_cand = 0;       // longest candidate list (BOUNDARY not counted)
+    std::vector<uint8_t> cand_count;   // [b]: 1 + list length (BOUNDARY counted)
+    std::vector<uint8_t> blob;
+};
+constexpr uint16_t SCAN_NONE = 0xFFFFu;
+
 struct DeviceTables {
     int device = -1;
     void *d_blob[3] = {nullptr, nullptr, nullptr};
+    void *d_scan = nullptr;
 };
 
 }  // namespace lx
@@ -79,6 +98,7 @@ struct lx_tokenset {
     bool reentrant = false;
     uint32_t exact[8] = {0}, modulo[8] = {0};
     lx::HostTable tab[3];
+    lx::ScanTable scan;
     std::mutex mu;
     std::vector<lx::DeviceTables> dev;
 };

@@ -33,6 +33,7 @@
 #include <new>
 
 #include "internal.h"
+#include "runtime.h"
 
 namespace lx {
 
@@ -1092,56 +1093,36 @@ int cuda_err(cudaError_t e)
 
 using namespace lx;
 
-struct lx_ctx {
-    int device = 0;
-    int num_sms = 0;
-    void *scratch = nullptr;
-    size_t scratch_bytes = 0;
-    Result *h_res = nullptr;   // pinned
-    uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;
-    std::vector<std::pair<uint64_t, int>> occupancy;   // (form << 32 | shared bytes) -> CTAs per SM
-    // lx_lex_batch: device scratch, pinned staging (descriptors up, records
-    // down), the capture stream and the cached graph with its shape key
-    void *b_dev = nullptr;
-    size_t b_dev_bytes = 0;
-    void *b_host = nullptr;
-    size_t b_host_bytes = 0;
-    cudaStream_t b_stream = nullptr;
-    cudaGraphExec_t b_exec = nullptr;
-    std::vector<uint64_t> b_key;
-    // device buffers of lx_lex_host
-    void *d_in = nullptr;
-    size_t d_in_bytes = 0;
-    void *d_out = nullptr;
-    size_t d_out_bytes = 0;
-    // optional kernel timing
-    bool timing = false;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-};
-
-static int ensure_device_tables(const lx_tokenset *cts, int device, void **out_blobs)
+int lx::ensure_device_tables(const lx_tokenset *cts, int device, void **out_blobs, void **out_scan)
 {
     lx_tokenset *ts = const_cast<lx_tokenset *>(cts);
     std::lock_guard<std::mutex> g(ts->mu);
     for (auto &d : ts->dev)
         if (d.device == device) {
             for (int m = 0; m < 3; m++) out_blobs[m] = d.d_blob[m];
+            if (out_scan) *out_scan = d.d_scan;
             return LX_OK;
         }
     DeviceTables dt;
     dt.device = device;
-    for (int m = 0; m < 3; m++) {
-        const HostTable &h = ts->tab[m];
-        if (h.status != LX_OK) continue;
-        int rc = cuda_err(cudaMalloc(&dt.d_blob[m], h.blob.size()));
-        if (rc == LX_OK) rc = cuda_err(cudaMemcpy(dt.d_blob[m], h.blob.data(), h.blob.size(), cudaMemcpyHostToDevice));
-        if (rc != LX_OK) {
-            for (int k = 0; k <= m; k++) cudaFree(dt.d_blob[k]);
-            return rc;
-        }
+    auto upload = [](const std::vector<uint8_t> &blob, void **dst) {
+        int rc = cuda_err(cudaMalloc(dst, blob.size()));
+        if (rc == LX_OK) rc = cuda_err(cudaMemcpy(*dst, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+        return rc;
+    };
+    int rc = LX_OK;
+    for (int m = 0; m < 3 && rc == LX_OK; m++)
+        if (ts->tab[m].status == LX_OK) rc = upload(ts->tab[m].blob, &dt.d_blob[m]);
+    if (rc == LX_OK && ts->scan.status == LX_OK) rc = upload(ts->scan.blob, &dt.d_scan);
+    if (rc != LX_OK) {
+        for (int m = 0; m < 3; m++)
+            if (dt.d_blob[m]) cudaFree(dt.d_blob[m]);
+        if (dt.d_scan) cudaFree(dt.d_scan);
+        return rc;
     }
     ts->dev.push_back(dt);
     for (int m = 0; m < 3; m++) out_blobs[m] = dt.d_blob[m];
+    if (out_scan) *out_scan = dt.d_scan;
     return LX_OK;
 }
 
@@ -1154,6 +1135,7 @@ extern "C" void lx_tokenset_free(lx_tokenset *ts)
         cudaSetDevice(d.device);
         for (int m = 0; m < 3; m++)
             if (d.d_blob[m]) cudaFree(d.d_blob[m]);
+        if (d.d_scan) cudaFree(d.d_scan);
     }
     if (cur >= 0 && !ts->dev.empty()) cudaSetDevice(cur);
     delete ts;
@@ -1173,7 +1155,7 @@ extern "C" int lx_ctx_create(lx_ctx **out)
     if (!c) return LX_E_NOMEM;
     c->device = dev;
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void **>(&c->h_res), sizeof(Result)) != cudaSuccess) {
+        cudaMallocHost(&c->h_res, sizeof(Result)) != cudaSuccess) {
         delete c;
         return LX_E_CUDA;
     }
@@ -1189,6 +1171,7 @@ extern "C" void lx_ctx_free(lx_ctx *c)
     if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
     if (c->b_stream) cudaStreamDestroy(c->b_stream);
     if (c->b_dev) cudaFree(c->b_dev);
+    if (c->e_dev) cudaFree(c->e_dev);
     if (c->b_host) cudaFreeHost(c->b_host);
     if (c->d_in) cudaFree(c->d_in);
     if (c->d_out) cudaFree(c->d_out);
@@ -1221,7 +1204,7 @@ extern "C" int lx_ctx_set_timeout_ms(lx_ctx *c, uint32_t ms)
     return LX_OK;
 }
 
-static int grow(void **p, size_t *have, size_t need)
+int lx::grow(void **p, size_t *have, size_t need)
 {
     if (*have >= need) return LX_OK;
     if (*p) cudaFree(*p);
@@ -1296,7 +1279,7 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
     void *blobs[3];
-    int rc = ensure_device_tables(ts, dev, blobs);
+    int rc = ensure_device_tables(ts, dev, blobs, nullptr);
     if (rc != LX_OK) return rc;
 
     const uint64_t n_tiles64 = (n + TILE - 1) / TILE;
@@ -1349,7 +1332,7 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     rc = cuda_err(cudaMemcpyAsync(c->h_res, P.res, sizeof(Result), cudaMemcpyDeviceToHost, st));
     if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(st));
     if (rc != LX_OK) return rc;
-    const Result r = *c->h_res;
+    const Result r = *static_cast<const Result *>(c->h_res);
     if (r.error & ERR_TIMEOUT) return LX_E_TIMEOUT;
     if (r.error & ERR_SMEM) return LX_E_TOOBIG;
     uint64_t tokens = r.total, con = n;
@@ -1452,7 +1435,10 @@ BatchLayout batch_layout(uint32_t G, uint32_t D, uint64_t TT, uint32_t grid)
     return B;
 }
 
-int grow_host(void **p, size_t *have, size_t need)
+
+}  // namespace
+
+int lx::grow_host(void **p, size_t *have, size_t need)
 {
     if (*have >= need) return LX_OK;
     if (*p) cudaFreeHost(*p);
@@ -1462,8 +1448,6 @@ int grow_host(void **p, size_t *have, size_t need)
     *have = need;
     return LX_OK;
 }
-
-}  // namespace
 
 extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, const lx_doc *docs,
                             uint32_t n_docs, int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity,
@@ -1516,7 +1500,7 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
     for (uint32_t k = 0; k < G; k++) {
         const lx_tokenset *ts = sets[groups[k].set];
         void *blobs[3];
-        int rc = ensure_device_tables(ts, dev, blobs);
+        int rc = ensure_device_tables(ts, dev, blobs, nullptr);
         if (rc != LX_OK) return rc;
         blob[k] = blobs[mode];
         const HostTable &h = ts->tab[mode];

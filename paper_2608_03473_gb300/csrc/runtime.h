@@ -1,0 +1,58 @@
+// runtime.h -- host-side runtime shared by the CUDA translation units: the
+// context (scratch, pinned staging, graph cache, timing events) and the
+// helpers that size its buffers and upload token-set tables.  Not part of the
+// C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+struct lx_ctx {
+    int device = 0;
+    int num_sms = 0;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    void *h_res = nullptr;   // pinned: the launch record read back by lx_lex
+    uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;
+    std::vector<std::pair<uint64_t, int>> occupancy;   // (form << 32 | shared bytes) -> CTAs per SM
+    // lx_lex_batch: device scratch, pinned staging (descriptors up, records
+    // down), the capture stream and the cached graph with its shape key
+    void *b_dev = nullptr;
+    size_t b_dev_bytes = 0;
+    void *b_host = nullptr;
+    size_t b_host_bytes = 0;
+    cudaStream_t b_stream = nullptr;
+    cudaGraphExec_t b_exec = nullptr;
+    std::vector<uint64_t> b_key;
+    // lx_lex_enumerative: device scratch
+    void *e_dev = nullptr;
+    size_t e_dev_bytes = 0;
+    // device buffers of lx_lex_host
+    void *d_in = nullptr;
+    size_t d_in_bytes = 0;
+    void *d_out = nullptr;
+    size_t d_out_bytes = 0;
+    // optional kernel timing
+    bool timing = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace lx {
+
+// LX_OK, LX_E_NOMEM for an allocation failure, LX_E_CUDA otherwise.
+int cuda_err(cudaError_t e);
+// Grow a device (grow) or pinned host (grow_host) buffer to at least `need`
+// bytes; contents are not kept.
+int grow(void **p, size_t *have, size_t need);
+int grow_host(void **p, size_t *have, size_t need);
+// The token set's tables on `device` (uploaded on first use): the walk-table
+// blob of each mode and the plain scan table (nullptr where a table does not
+// exist for this token set).
+int ensure_device_tables(const lx_tokenset *ts, int device, void **out_blobs, void **out_scan);
+
+}  // namespace lx

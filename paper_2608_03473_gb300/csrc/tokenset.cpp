@@ -11,6 +11,7 @@
 namespace {
 
 using lx::HostTable;
+using lx::ScanTable;
 
 // Predecessor index over the stored (class-compressed) table: one entry per
 // defined (state, class) edge, grouped by target (Section 6.1 builds it once
@@ -260,6 +261,69 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
     }
 }
 
+void build_scan_table(const lx_tokenset &t, ScanTable &st)
+{
+    const uint32_t S = t.n_states, C = t.n_classes;
+    st.S = S;
+    st.C = C;
+    st.q0 = t.q0;
+    st.cand_count.assign(256, 1);
+    if (S >= 0xFFFEu) {
+        st.status = LX_E_TOOBIG;
+        return;
+    }
+    const auto &live = t.live;
+    std::vector<std::vector<uint16_t>> cand(256);
+    for (uint32_t b = 0; b < 256; b++) {
+        const uint32_t c = t.byte_class[b];
+        std::vector<uint8_t> seen(S, 0);
+        for (uint32_t q = 0; q < S; q++) {
+            if (!live[q]) continue;
+            const uint32_t d = t.next[(size_t)c * S + q];
+            if (d != LX_NONE && live[d] && !seen[d]) {
+                seen[d] = 1;
+                cand[b].push_back((uint16_t)d);
+            }
+        }
+        std::sort(cand[b].begin(), cand[b].end());
+        st.max_cand = std::max<uint32_t>(st.max_cand, (uint32_t)cand[b].size());
+        st.cand_count[b] = (uint8_t)std::min<size_t>(255, cand[b].size() + 1);
+    }
+    auto al = [](uint32_t x) { return (x + 15u) & ~15u; };
+    st.next_off = 256;
+    st.acc_off = al(st.next_off + 2 * C * S);
+    st.cbeg_off = al(st.acc_off + 2 * S);
+    st.cand_off = al(st.cbeg_off + 2 * 257);
+    uint32_t total = 0;
+    for (auto &v : cand) total += (uint32_t)v.size();
+    const uint32_t bytes = al(st.cand_off + 2 * total);
+    if (bytes > lx::MAX_TABLE_BYTES || total > 0xFFFFu) {
+        st.status = LX_E_TOOBIG;
+        return;
+    }
+    st.blob.assign(bytes, 0);
+    std::memcpy(st.blob.data(), t.byte_class.data(), 256);
+    uint16_t *nx = reinterpret_cast<uint16_t *>(st.blob.data() + st.next_off);
+    for (uint32_t c = 0; c < C; c++)
+        for (uint32_t q = 0; q < S; q++) {
+            const uint32_t d = t.next[(size_t)c * S + q];
+            nx[(size_t)c * S + q] = (d != LX_NONE && live[d]) ? (uint16_t)d : lx::SCAN_NONE;
+        }
+    uint16_t *acc = reinterpret_cast<uint16_t *>(st.blob.data() + st.acc_off);
+    for (uint32_t q = 0; q < S; q++) {
+        const uint32_t k = t.accept[q];
+        acc[q] = k == LX_NO_KIND ? (uint16_t)lx::KIND_NONE : (uint16_t)(k | (t.discard[k] ? 0u : lx::KIND_KEEP));
+    }
+    uint16_t *cb = reinterpret_cast<uint16_t *>(st.blob.data() + st.cbeg_off);
+    uint16_t *cv = reinterpret_cast<uint16_t *>(st.blob.data() + st.cand_off);
+    uint32_t o = 0;
+    for (uint32_t b = 0; b < 256; b++) {
+        cb[b] = (uint16_t)o;
+        for (uint16_t v : cand[b]) cv[o++] = v;
+    }
+    cb[256] = (uint16_t)o;
+}
+
 }  // namespace
 
 extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
@@ -295,6 +359,7 @@ extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
         for (uint32_t k = 0; k < n_discarded; k++) t->discard[discarded[k]] = 1;
         derive_certificates(*t);
         for (int m = 0; m < 3; m++) build_table(*t, m, t->tab[m]);
+        build_scan_table(*t, t->scan);
     } catch (const std::bad_alloc &) {
         delete t;
         return LX_E_NOMEM;
@@ -334,4 +399,16 @@ extern "C" int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uin
                             h.cert_off, h.p_pre};
     if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 12));
     return h.status;
+}
+
+extern "C" int lx_tokenset_scan_table(const lx_tokenset *ts, void *out, uint32_t cap, uint32_t *meta,
+                                      uint32_t meta_len)
+{
+    if (!ts) return LX_E_INVAL;
+    const lx::ScanTable &st = ts->scan;
+    if (out && cap) std::memcpy(out, st.blob.data(), std::min<size_t>(cap, st.blob.size()));
+    const uint32_t m[9] = {(uint32_t)st.blob.size(), st.S, st.C, st.q0, st.next_off, st.acc_off,
+                           st.cbeg_off, st.cand_off, st.max_cand};
+    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 9));
+    return st.status;
 }
