@@ -121,12 +121,12 @@ __host__ __device__ inline Layout make_layout(uint32_t blob_bytes)
     L.slots = L.buf + BUF;
     L.stage = L.slots + KS * NT * 4;
     L.misc = L.stage + STAGE_CAP * 4;
-    L.total = L.misc + 256;
+    L.total = L.misc + 256 + 12 * NW;
     return L;
 }
 
 // misc region offsets
-constexpr uint32_t M_WARP = 0;      // u64[8] warp totals -> exclusive offsets
+constexpr uint32_t M_WARP = 256;    // u64[NW] warp totals -> exclusive offsets
 constexpr uint32_t M_MBAR = 64;     // u64
 constexpr uint32_t M_TILE = 80;     // u32: next tile id
 constexpr uint32_t M_X = 84;        // u32: first cut at or past the tile end (relative)
@@ -134,7 +134,7 @@ constexpr uint32_t M_G = 96;        // u64: resolved output offset
 constexpr uint32_t M_TOT = 104;     // u64: this tile's kept total
 constexpr uint32_t M_FPOS = 112;    // u64: this tile's first failure offset (NOPOS = none)
 constexpr uint32_t M_FIDX = 120;    // u64: kept tokens before it, within the tile
-constexpr uint32_t M_WMIN = 128;    // u32[8]: per-warp minimum chunk start
+constexpr uint32_t M_WMIN = 256 + 8 * NW;   // u32[NW]: per-warp minimum chunk start
 constexpr uint32_t M_PTILE = 160;   // u32: pending tile (NONE32 = none)
 constexpr uint32_t M_PTOT = 168;    // u64: pending tile's kept total
 constexpr uint32_t M_PFPOS = 176;   // u64: pending tile's failure offset
