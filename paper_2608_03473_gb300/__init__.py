@@ -49,6 +49,7 @@ EXPORTED = (
     "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_scan_table",
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
+    "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune",
     "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative",
     "lx_strerror",
 )
@@ -104,6 +105,9 @@ def load_library(path: Optional[str] = None):
             "lx_ctx_set_timeout_ms": (i32, [vp, u32]),
             "lx_ctx_enable_timing": (i32, [vp, i32]),
             "lx_ctx_last_kernel_ms": (i32, [vp, vp]),
+            "lx_ctx_set_config": (i32, [vp, vp, i32, u32, u32]),
+            "lx_ctx_get_config": (i32, [vp, vp, i32, vp, vp, vp]),
+            "lx_autotune": (i32, [vp, vp, i32, vp, u64, vp, vp, u64, vp]),
             "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_host": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_noalloc": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
@@ -356,3 +360,27 @@ def lx_tokenset_scan_table(ts: Tokenset):
     rc = lib.lx_tokenset_scan_table(ts.handle, blob.ctypes.data, meta[0], meta, 9)
     keys = ("bytes", "S", "C", "q0", "next_off", "acc_off", "cbeg_off", "cand_off", "max_cand")
     return rc, blob[:meta[0]], dict(zip(keys, list(meta)))
+
+
+LX_KS_MIN, LX_KS_MAX = 16, 96
+
+
+def lx_ctx_set_config(ctx: Ctx, ts: Tokenset, mode: int, ks: int, ctas_per_sm: int = 0) -> int:
+    return load_library().lx_ctx_set_config(ctx.handle, ts.handle, int(mode), int(ks), int(ctas_per_sm))
+
+
+def lx_ctx_get_config(ctx: Ctx, ts: Tokenset, mode: int):
+    """(ks, ctas_per_sm, ms) in force for (ts, mode)."""
+    ks, ctas, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
+    load_library().lx_ctx_get_config(ctx.handle, ts.handle, int(mode), ctypes.byref(ks), ctypes.byref(ctas),
+                                     ctypes.byref(ms))
+    return ks.value, ctas.value, ms.value
+
+
+def lx_autotune(ctx: Ctx, ts: Tokenset, mode: int, d_sample, d_kinds, d_lens, n: Optional[int] = None,
+                capacity: Optional[int] = None, stream=None) -> int:
+    """Time the launch configurations on a device sample and keep the fastest."""
+    n = d_sample.numel() if n is None else int(n)
+    cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
+    return load_library().lx_autotune(ctx.handle, ts.handle, int(mode), d_sample.data_ptr(), n,
+                                      d_kinds.data_ptr(), d_lens.data_ptr(), cap, _stream_handle(stream))

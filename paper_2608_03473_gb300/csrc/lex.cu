@@ -43,7 +43,8 @@ constexpr int SEG = 68;                 // bytes per thread target (17 words: od
 constexpr int TILE = NT * SEG;          // 17408 input bytes per tile
 constexpr int HALO = 1024;              // extra staged bytes for ranges that run past the tile
 constexpr int BUF = TILE + HALO;        // 18432, a multiple of 16
-constexpr int KS = 40;                  // token-end records per thread
+constexpr uint32_t KS_DEFAULT = 40;     // token-end records per thread (the column height), unless tuned
+constexpr uint32_t KS_MIN = LX_KS_MIN;  // make_room needs half a column of at least 8 words
 constexpr int STAGE_CAP = 4096;         // kept tokens per tile that take the deferred coalesced path
 constexpr int SPILL_WORDS = 8192;       // global spill region per CTA (kept tokens of long ranges)
 constexpr uint64_t NOPOS = ~0ull;
@@ -103,6 +104,7 @@ struct Params {
     uint64_t timeout_ns;
     uint32_t *spill;       // per-CTA spill regions for long ranges' kept tokens
     uint32_t spill_cap;    // words per CTA (0: no spilling)
+    uint32_t ks;           // record column height (words per thread)
 };
 
 // ---- shared-memory layout (bytes from the dynamic shared base) ----
@@ -114,12 +116,12 @@ struct Layout {
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) & ~(a - 1); }
 
-__host__ __device__ inline Layout make_layout(uint32_t blob_bytes)
+__host__ __device__ inline Layout make_layout(uint32_t blob_bytes, uint32_t ks)
 {
     Layout L;                                    // blob first: + up to 511 bytes to 512-align the table
     L.buf = align_up(512 + blob_bytes, 128);
     L.slots = L.buf + BUF;
-    L.stage = L.slots + KS * NT * 4;
+    L.stage = L.slots + ks * NT * 4;
     L.misc = L.stage + STAGE_CAP * 4;
     L.total = L.misc + 256 + 12 * NW;
     return L;
@@ -244,6 +246,7 @@ struct Env {
     uint32_t tbase, kind_s, cmap_s, cert_s, kcol2;
     uint32_t *spill;            // this CTA's spill region (global)
     uint32_t spill_cap;         // its size in words
+    uint32_t ks;                // record column height
     unsigned *spill_used;       // shared allocation counter, reset per tile
 };
 
@@ -477,7 +480,7 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
                                              uint32_t &fail, uint32_t &sp_first, uint32_t &spilled)
 {
     const uint32_t P_flag = E.P_flag, P_slow = E.P_slow;
-    const uint32_t col_end = col + (uint32_t)KS * NT * 4;
+    const uint32_t col_end = col + E.ks * NT * 4;
     const uint32_t lim = eoi ? end : end + 1;             // bytes [start, lim) are stepped
     const uint32_t mlim = eoi ? (lim & ~3u) : lim;        // whole words while p < mlim
     uint32_t p = start & ~3u;
@@ -524,7 +527,7 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
         raw0 = sp = sp_lo = wr;
         tok_base = prev_pos;   // the token in progress began at the last end
         if (big) return false;
-        if (sp > col + (uint32_t)(KS / 2) * NT * 4) {   // move the kept tokens out
+        if (sp > col + (E.ks / 2) * NT * 4) {   // move the kept tokens out
             const uint32_t off = atomicAdd(E.spill_used, ncomp + 2);
             if (off + ncomp + 2 > E.spill_cap) return false;
             uint32_t *blk = E.spill + off;
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const Layout L = make_layout(P.blob_bytes);
+    const Layout L = make_layout(P.blob_bytes, P.ks);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t tbase = align_up(sbase, 512);
     uint8_t *misc = smem + L.misc;
@@ -765,6 +768,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     E.buf = buf;
     E.spill = P.spill + (size_t)blockIdx.x * P.spill_cap;
     E.spill_cap = P.spill_cap;
+    E.ks = P.ks;
     E.spill_used = reinterpret_cast<unsigned *>(misc + M_SPILL);
 
     volatile uint32_t *s_tile = reinterpret_cast<volatile uint32_t *>(misc + M_TILE);
@@ -1264,10 +1268,38 @@ static void launch_tiles(int form, uint32_t grid, uint32_t smem, cudaStream_t st
     else lex_tiles<FORM_CLASS><<<grid, NT, smem, st>>>(P);
 }
 
+struct LaunchCfg {
+    uint32_t ks = KS_DEFAULT;
+    uint32_t ctas = 0;   // CTAs per SM; 0 = as many as fit
+};
+
+static LaunchCfg config_for(const lx_ctx *c, const lx_tokenset *ts, int mode)
+{
+    LaunchCfg g;
+    for (const lx_tuned &t : c->tuned)
+        if (t.ts == ts && t.mode == mode) {
+            g.ks = t.ks;
+            g.ctas = t.ctas;
+        }
+    return g;
+}
+
+// Grid of the tile kernel for a configuration: CTAs per SM as asked, never
+// above what fits (shared memory, registers).
+static int grid_for(lx_ctx *c, int form, uint32_t smem, const LaunchCfg &g, uint64_t n_tiles, uint32_t *grid)
+{
+    int occ = 0;
+    int rc = occupancy_for(c, form, smem, &occ);
+    if (rc != LX_OK) return rc;
+    const uint64_t per_sm = g.ctas ? std::min<uint64_t>(g.ctas, (uint64_t)occ) : (uint64_t)occ;
+    *grid = (uint32_t)std::min<uint64_t>(n_tiles, per_sm * c->num_sms);
+    return LX_OK;
+}
+
 // Launch the tile kernel and read back its result record.
 static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
                       uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
-                      uint64_t *consumed, cudaStream_t st)
+                      uint64_t *consumed, cudaStream_t st, const LaunchCfg *force = nullptr)
 {
     const HostTable &h = ts->tab[mode];
     if (h.status != LX_OK) return h.status;
@@ -1304,13 +1336,14 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     P.cap = capacity;
     P.n_tiles = n_tiles;
     P.timeout_ns = c->timeout_ns;
+    const LaunchCfg g = force ? *force : config_for(c, ts, mode);
+    P.ks = g.ks;
 
-    const Layout L = make_layout(P.blob_bytes);
+    const Layout L = make_layout(P.blob_bytes, P.ks);
     const int form = h.form;
-    int occ = 0;
-    rc = occupancy_for(c, form, L.total, &occ);
+    uint32_t grid = 0;
+    rc = grid_for(c, form, L.total, g, n_tiles, &grid);
     if (rc != LX_OK) return rc;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(n_tiles, (uint64_t)occ * c->num_sms);
 
     // scratch: result record, tile counter, status words, then the spill regions
     rc = grow(&c->scratch, &c->scratch_bytes, spill_off + sizeof(uint32_t) * (size_t)SPILL_WORDS * grid);
@@ -1496,6 +1529,7 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
     // tables, occupancy and grid per group
     std::vector<void *> blob(G);
     std::vector<uint32_t> grid(G), smem(G);
+    std::vector<LaunchCfg> cfg(G);
     uint32_t grid_max = 0;
     for (uint32_t k = 0; k < G; k++) {
         const lx_tokenset *ts = sets[groups[k].set];
@@ -1504,11 +1538,10 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
         if (rc != LX_OK) return rc;
         blob[k] = blobs[mode];
         const HostTable &h = ts->tab[mode];
-        smem[k] = make_layout((uint32_t)h.blob.size()).total;
-        int occ = 0;
-        rc = occupancy_for(c, h.form, smem[k], &occ);
+        cfg[k] = config_for(c, ts, mode);
+        smem[k] = make_layout((uint32_t)h.blob.size(), cfg[k].ks).total;
+        rc = grid_for(c, h.form, smem[k], cfg[k], groups[k].n_tiles, &grid[k]);
         if (rc != LX_OK) return rc;
-        grid[k] = (uint32_t)std::min<uint64_t>(groups[k].n_tiles, (uint64_t)occ * c->num_sms);
         grid_max = std::max(grid_max, grid[k]);
     }
     const BatchLayout B = batch_layout(G, D, TT, grid_max);
@@ -1545,6 +1578,7 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
         key.push_back(groups[k].doc_begin);
         key.push_back(groups[k].n_tiles);
         key.push_back(grid[k]);
+        key.push_back(cfg[k].ks);
     }
     if (moved || key != c->b_key || !c->b_exec) {
         if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
@@ -1578,6 +1612,7 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
             P.spill = reinterpret_cast<uint32_t *>(dv + B.spill);
             P.spill_cap = SPILL_WORDS;
             P.timeout_ns = c->timeout_ns;
+            P.ks = cfg[k].ks;
             launch_tiles(h.form, grid[k], smem[k], cs, P);
         }
         cudaMemcpyAsync(hs + B.down, dv, B.zero_end - 8 * TT, cudaMemcpyDeviceToHost, cs);
@@ -1623,6 +1658,117 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
     }
     *n_total = total;
     return total > capacity ? LX_E_CAPACITY : LX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch configuration: set by hand or measured
+// ---------------------------------------------------------------------------
+static void store_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t ks, uint32_t ctas, float ms)
+{
+    for (lx_tuned &t : c->tuned)
+        if (t.ts == ts && t.mode == mode) {
+            t.ks = ks;
+            t.ctas = ctas;
+            t.ms = ms;
+            return;
+        }
+    c->tuned.push_back(lx_tuned{ts, mode, ks, ctas, ms});
+    if (c->b_exec) {   // a cached batch graph may hold the old configuration
+        cudaGraphExecDestroy(c->b_exec);
+        c->b_exec = nullptr;
+        c->b_key.clear();
+    }
+}
+
+extern "C" int lx_ctx_set_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t ks, uint32_t ctas_per_sm)
+{
+    if (!c || !ts) return LX_E_INVAL;
+    if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
+    if (ks < KS_MIN || ks > LX_KS_MAX) return LX_E_INVAL;
+    if (make_layout((uint32_t)ts->tab[mode].blob.size(), ks).total > 200u * 1024u) return LX_E_TOOBIG;
+    store_config(c, ts, mode, ks, ctas_per_sm, 0.0f);
+    return LX_OK;
+}
+
+extern "C" int lx_ctx_get_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t *ks, uint32_t *ctas_per_sm,
+                                 float *ms)
+{
+    if (!c || !ts) return LX_E_INVAL;
+    LaunchCfg g = config_for(c, ts, mode);
+    float t = 0.0f;
+    for (const lx_tuned &x : c->tuned)
+        if (x.ts == ts && x.mode == mode) t = x.ms;
+    if (ks) *ks = g.ks;
+    if (ctas_per_sm) *ctas_per_sm = g.ctas;
+    if (ms) *ms = t;
+    return LX_OK;
+}
+
+extern "C" int lx_autotune(lx_ctx *c, const lx_tokenset *ts, int mode, const uint8_t *d_sample, uint64_t n,
+                           uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, void *stream)
+{
+    uint64_t unused_t = 0, unused_c = 0;
+    int rc = check_args(c, ts, d_sample, n, mode, d_kinds, d_lens, capacity, &unused_t, &unused_c);
+    if (rc != LX_OK || n == 0) return rc == LX_OK ? LX_E_INVAL : rc;
+    const HostTable &h = ts->tab[mode];
+    if (h.status != LX_OK) return h.status;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return LX_E_CUDA;
+    }
+    const bool timing = c->timing;
+    c->timing = false;
+    float best = 1e30f;
+    LaunchCfg best_g;
+    uint64_t ref_tokens = ~0ull, ref_con = ~0ull;
+    static const uint32_t ks_list[] = {24, 32, 40, 48, 56, 64};
+    for (uint32_t ks : ks_list) {
+        const uint32_t smem = make_layout((uint32_t)h.blob.size(), ks).total;
+        if (smem > 200u * 1024u) continue;
+        int occ = 0;
+        rc = occupancy_for(c, h.form, smem, &occ);
+        if (rc != LX_OK) break;
+        for (uint32_t ctas : {(uint32_t)occ, 1u}) {
+            if (ctas == 1 && occ == 1) continue;
+            LaunchCfg g;
+            g.ks = ks;
+            g.ctas = ctas;
+            uint64_t nt = 0, con = 0;
+            float total = 0.0f;
+            for (int rep = 0; rep < 4 && rc == LX_OK; rep++) {
+                cudaEventRecord(e0, st);
+                rc = lex_device(c, ts, d_sample, n, mode, d_kinds, d_lens, capacity, &nt, &con, st, &g);
+                cudaEventRecord(e1, st);
+                if (rc == LX_E_CAPACITY) rc = LX_OK;
+                if (rc != LX_OK) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep) total += ms;   // the first run warms up
+            }
+            if (rc != LX_OK) break;
+            if (ref_tokens == ~0ull) {
+                ref_tokens = nt;
+                ref_con = con;
+            } else if (nt != ref_tokens || con != ref_con) {
+                rc = LX_E_CUDA;   // every configuration must give the same result
+                break;
+            }
+            if (total / 3 < best) {
+                best = total / 3;
+                best_g = g;
+            }
+        }
+        if (rc != LX_OK) break;
+    }
+    c->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LX_OK) return rc;
+    store_config(c, ts, mode, best_g.ks, best_g.ctas, best);
+    return LX_OK;
 }
 
 extern "C" const char *lx_strerror(int code)
@@ -1748,10 +1894,11 @@ extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64
     P.status = reinterpret_cast<unsigned long long *>(scr + NA_STATUS);
     P.spill = nullptr;   // no spill region: long ranges take the generic walker
     P.spill_cap = 0;
+    P.ks = KS_DEFAULT;
     P.n_tiles = n_tiles;
     P.timeout_ns = 20ull * 1000 * 1000 * 1000;
 
-    const Layout L = make_layout(P.blob_bytes);
+    const Layout L = make_layout(P.blob_bytes, P.ks);
     int occ = 0;
     cudaError_t e = h.form == FORM_BYTE
                         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lex_tiles<FORM_BYTE>, NT, L.total)

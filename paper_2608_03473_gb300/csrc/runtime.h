@@ -12,6 +12,15 @@
 
 #include "internal.h"
 
+// A launch configuration of the tile kernel for one token set and mode:
+// the record column height and the CTAs per SM (capped by occupancy).
+struct lx_tuned {
+    const lx_tokenset *ts;
+    int mode;
+    uint32_t ks, ctas;
+    float ms;   // measured by lx_autotune (0 when set by hand)
+};
+
 struct lx_ctx {
     int device = 0;
     int num_sms = 0;
@@ -20,6 +29,7 @@ struct lx_ctx {
     void *h_res = nullptr;   // pinned: the launch record read back by lx_lex
     uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;
     std::vector<std::pair<uint64_t, int>> occupancy;   // (form << 32 | shared bytes) -> CTAs per SM
+    std::vector<lx_tuned> tuned;                       // per (token set, mode); default otherwise
     // lx_lex_batch: device scratch, pinned staging (descriptors up, records
     // down), the capture stream and the cached graph with its shape key
     void *b_dev = nullptr;
