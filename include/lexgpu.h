@@ -249,6 +249,72 @@ int lx_lex_enumerative(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, 
                        uint64_t *consumed, void *stream);
 
 /*
+ * lx_chunk_contexts -- the chunk starts lx_lex_enumerative plans for `d_in`
+ * and the true entry context of each (0..states-1: inside a token in that
+ * DFA state; 0xFFFE: at a token boundary), resolved by enumeration.  One
+ * entry per 4096-byte target into d_starts / d_ctx (device, cap entries;
+ * offset ~0 and context 0xFFFF where a target has no start, or after a
+ * lexing error); *count = number of targets (LX_E_CAPACITY if cap < count).
+ * These are the labels the entry-context model is trained on.
+ */
+int lx_chunk_contexts(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, uint64_t *d_starts,
+                      uint16_t *d_ctx, uint64_t cap, uint64_t *count, void *stream);
+
+/*
+ * Entry-context model (opaque, lives on the device that created it): a small
+ * MLP over the 64 bytes around a chunk start (32 before, 32 after; a padding
+ * value outside the input) scoring n_contexts = states + 1 classes
+ * (class states = BOUNDARY): byte embedding (257 x 8), hidden layer of
+ * `hidden` ReLU units, linear output.  FP32 master parameters trained with
+ * Adam on mean softmax cross-entropy; predictions use a BF16 copy and take
+ * the argmax over the candidate contexts of the byte before the start.
+ * Parameters are exchanged as one FP32 array in the order: embedding
+ * [257][8], W1 [512][hidden], b1 [hidden], W2 [hidden][n_contexts],
+ * b2 [n_contexts].  Windows are u16 arrays of 64 byte values (256 = pad),
+ * labels u16 class indices.
+ */
+typedef struct lx_model lx_model;
+int lx_model_create(uint32_t n_contexts, uint32_t hidden, uint64_t seed, lx_model **out);
+void lx_model_free(lx_model *m);
+int lx_model_info(const lx_model *m, uint32_t *n_contexts, uint32_t *hidden, uint32_t *window, uint32_t *embed,
+                  uint64_t *n_params);
+int lx_model_get_params(const lx_model *m, float *host, uint64_t count);
+int lx_model_set_params(lx_model *m, const float *host, uint64_t count);
+/* windows around the offsets d_pos[0..count) of d_in (all device buffers) */
+int lx_model_windows(const uint8_t *d_in, uint64_t n, const uint64_t *d_pos, uint32_t count, uint16_t *d_windows,
+                     void *stream);
+/* FP32 logits [batch][n_contexts] (device) */
+int lx_model_forward(lx_model *m, const uint16_t *d_windows, uint32_t batch, float *d_logits, void *stream);
+/* gradient of the mean loss w.r.t. the parameters (host, parameter order) and the loss */
+int lx_model_gradient(lx_model *m, const uint16_t *d_windows, const uint16_t *d_labels, uint32_t batch,
+                      float *host_grad, uint64_t count, float *loss, void *stream);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on a batch; returns its loss before the step */
+int lx_model_train_step(lx_model *m, const uint16_t *d_windows, const uint16_t *d_labels, uint32_t batch,
+                        float lr, float *loss, void *stream);
+
+/*
+ * lx_lex_speculative -- lx_lex_enumerative with one scan per chunk: chunks
+ * start where lx_lex_enumerative puts them, each is scanned from a predicted
+ * entry context (the model's, or BOUNDARY with model == NULL), then rounds of
+ * fix-up give every chunk its predecessor's exit context and rescan the
+ * chunks whose entry changed, until the chain from offset 0 is consistent:
+ * the result is exact whatever the predictions.  Same output and errors as
+ * lx_lex_enumerative; LX_E_INVAL when the model does not score states + 1
+ * contexts of this token set.  stats (optional): chunk targets, rounds (scans
+ * of the dirty chunks, the first included), chunks scanned again after the
+ * first round.
+ */
+typedef struct {
+    uint64_t chunks;
+    uint32_t rounds;
+    uint32_t rescanned;
+    uint64_t mispredicted_first;   /* reserved, 0 */
+} lx_spec_stats;
+int lx_lex_speculative(lx_ctx *ctx, const lx_tokenset *ts, lx_model *model, const uint8_t *d_in, uint64_t n,
+                       int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
+                       uint64_t *consumed, lx_spec_stats *stats, void *stream);
+
+/*
  * lx_lex_batch -- lex many documents, each with its own token set, in one
  * graph launch (the batched form of lx_lex; the paper lexes one input, this
  * applies its method per document).

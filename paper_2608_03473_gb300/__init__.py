@@ -50,7 +50,9 @@ EXPORTED = (
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
     "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune",
-    "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative",
+    "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative", "lx_chunk_contexts",
+    "lx_lex_speculative", "lx_model_create", "lx_model_free", "lx_model_info", "lx_model_get_params",
+    "lx_model_set_params", "lx_model_windows", "lx_model_forward", "lx_model_gradient", "lx_model_train_step",
     "lx_strerror",
 )
 
@@ -113,6 +115,17 @@ def load_library(path: Optional[str] = None):
             "lx_lex_noalloc": (i32, [vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_batch": (i32, [vp, vp, u32, vp, u32, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_enumerative": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
+            "lx_chunk_contexts": (i32, [vp, vp, vp, u64, vp, vp, u64, vp, vp]),
+            "lx_lex_speculative": (i32, [vp, vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp, vp]),
+            "lx_model_create": (i32, [u32, u32, u64, vp]),
+            "lx_model_free": (None, [vp]),
+            "lx_model_info": (i32, [vp, vp, vp, vp, vp, vp]),
+            "lx_model_get_params": (i32, [vp, vp, u64]),
+            "lx_model_set_params": (i32, [vp, vp, u64]),
+            "lx_model_windows": (i32, [vp, u64, vp, u32, vp, vp]),
+            "lx_model_forward": (i32, [vp, vp, u32, vp, vp]),
+            "lx_model_gradient": (i32, [vp, vp, vp, u32, vp, u64, vp, vp]),
+            "lx_model_train_step": (i32, [vp, vp, vp, u32, ctypes.c_float, vp, vp]),
             "lx_strerror": (ctypes.c_char_p, [i32]),
         }
         for name, (res, args) in sig.items():
@@ -384,3 +397,157 @@ def lx_autotune(ctx: Ctx, ts: Tokenset, mode: int, d_sample, d_kinds, d_lens, n:
     cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
     return load_library().lx_autotune(ctx.handle, ts.handle, int(mode), d_sample.data_ptr(), n,
                                       d_kinds.data_ptr(), d_lens.data_ptr(), cap, _stream_handle(stream))
+
+
+CTX_BOUNDARY = 0xFFFE
+CTX_NONE = 0xFFFF
+
+
+def lx_chunk_contexts(ctx: Ctx, ts: Tokenset, d_in, n: Optional[int] = None, stream=None):
+    """(status, starts uint64 device tensor, contexts uint16 device tensor) per
+    4096-byte chunk target: the true entry context at every chunk start."""
+    import torch
+    lib = load_library()
+    n = d_in.numel() if n is None else int(n)
+    count = ctypes.c_uint64()
+    lib.lx_chunk_contexts(ctx.handle, ts.handle, d_in.data_ptr(), n, None, None, 0, ctypes.byref(count),
+                          _stream_handle(stream))
+    m = max(count.value, 1)
+    starts = torch.empty(m, dtype=torch.int64, device=d_in.device)
+    cx = torch.empty(m, dtype=torch.int16, device=d_in.device)
+    rc = lib.lx_chunk_contexts(ctx.handle, ts.handle, d_in.data_ptr(), n, starts.data_ptr(), cx.data_ptr(), m,
+                               ctypes.byref(count), _stream_handle(stream))
+    return rc, starts[:count.value], cx[:count.value]
+
+
+class _SpecStats(ctypes.Structure):
+    _fields_ = [("chunks", ctypes.c_uint64), ("rounds", ctypes.c_uint32), ("rescanned", ctypes.c_uint32),
+                ("mispredicted_first", ctypes.c_uint64)]
+
+
+class Model:
+    """Owning handle of an ``lx_model`` (the entry-context predictor)."""
+
+    def __init__(self, n_contexts: int, hidden: int = 64, seed: int = 1):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        rc = lib.lx_model_create(int(n_contexts), int(hidden), int(seed), ctypes.byref(h))
+        if rc != 0:
+            raise LexError(rc, "lx_model_create")
+        self.handle = h.value
+        c, hd, w, e, n = (ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(),
+                          ctypes.c_uint64())
+        lib.lx_model_info(self.handle, ctypes.byref(c), ctypes.byref(hd), ctypes.byref(w), ctypes.byref(e),
+                          ctypes.byref(n))
+        self.n_contexts, self.hidden, self.window, self.embed, self.n_params = c.value, hd.value, w.value, \
+            e.value, n.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.lx_model_free(self.handle)
+            self.handle = None
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        rc = load_library().lx_model_get_params(self.handle, out.ctypes.data, self.n_params)
+        if rc != 0:
+            raise LexError(rc, "lx_model_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, np.float32)
+        rc = load_library().lx_model_set_params(self.handle, p.ctypes.data, p.size)
+        if rc != 0:
+            raise LexError(rc, "lx_model_set_params")
+
+    def windows(self, d_in, d_pos, stream=None):
+        import torch
+        cnt = d_pos.numel()
+        win = torch.empty((max(cnt, 1), self.window), dtype=torch.int16, device=d_in.device)
+        rc = load_library().lx_model_windows(d_in.data_ptr(), d_in.numel(), d_pos.data_ptr(), cnt,
+                                             win.data_ptr(), _stream_handle(stream))
+        if rc != 0:
+            raise LexError(rc, "lx_model_windows")
+        return win[:cnt]
+
+    def forward(self, d_windows, stream=None):
+        import torch
+        b = d_windows.shape[0]
+        logits = torch.empty((b, self.n_contexts), dtype=torch.float32, device=d_windows.device)
+        rc = load_library().lx_model_forward(self.handle, d_windows.data_ptr(), b, logits.data_ptr(),
+                                             _stream_handle(stream))
+        if rc != 0:
+            raise LexError(rc, "lx_model_forward")
+        return logits
+
+    def gradient(self, d_windows, d_labels, stream=None):
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_float()
+        rc = load_library().lx_model_gradient(self.handle, d_windows.data_ptr(), d_labels.data_ptr(),
+                                              d_windows.shape[0], g.ctypes.data, self.n_params,
+                                              ctypes.byref(loss), _stream_handle(stream))
+        if rc != 0:
+            raise LexError(rc, "lx_model_gradient")
+        return g, loss.value
+
+    def train_step(self, d_windows, d_labels, lr: float, stream=None) -> float:
+        loss = ctypes.c_float()
+        rc = load_library().lx_model_train_step(self.handle, d_windows.data_ptr(), d_labels.data_ptr(),
+                                                d_windows.shape[0], ctypes.c_float(lr), ctypes.byref(loss),
+                                                _stream_handle(stream))
+        if rc != 0:
+            raise LexError(rc, "lx_model_train_step")
+        return loss.value
+
+
+def lx_lex_speculative(ctx: Ctx, ts: Tokenset, model: Optional[Model], d_in, mode: int, d_kinds, d_lens,
+                       n: Optional[int] = None, capacity: Optional[int] = None, stream=None):
+    """Speculative lexing of a token set with no certified byte.  Returns
+    (status, n_tokens, consumed, stats dict)."""
+    lib = load_library()
+    n = d_in.numel() if n is None else int(n)
+    cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
+    nt, con = ctypes.c_uint64(), ctypes.c_uint64()
+    st = _SpecStats()
+    rc = lib.lx_lex_speculative(ctx.handle, ts.handle, model.handle if model is not None else None,
+                                d_in.data_ptr(), n, int(mode), d_kinds.data_ptr(), d_lens.data_ptr(), cap,
+                                ctypes.byref(nt), ctypes.byref(con), ctypes.byref(st), _stream_handle(stream))
+    return rc, nt.value, con.value, {"chunks": st.chunks, "rounds": st.rounds, "rescanned": st.rescanned}
+
+
+def context_training_set(ctx: Ctx, ts: Tokenset, model: Model, d_in, stream=None):
+    """(windows, labels) on the device for every chunk start of d_in, the
+    labels being the entry contexts resolved by lx_chunk_contexts (class
+    index: a DFA state, or n_contexts - 1 for BOUNDARY)."""
+    import torch
+    rc, starts, cx = lx_chunk_contexts(ctx, ts, d_in, stream=stream)
+    if rc != 0:
+        raise LexError(rc, "lx_chunk_contexts")
+    keep = (starts >= 0) & (starts > 0)   # targets with a start, chunk 0 excluded (always BOUNDARY)
+    starts, cx = starts[keep].contiguous(), cx[keep].contiguous()
+    lab = cx.to(torch.int32) & 0xFFFF
+    lab = torch.where(lab == CTX_BOUNDARY, torch.full_like(lab, model.n_contexts - 1), lab)
+    return model.windows(d_in, starts, stream=stream), lab.to(torch.int16).contiguous()
+
+
+def train_context_model(ctx: Ctx, ts: Tokenset, samples, hidden: int = 64, epochs: int = 4, batch: int = 512,
+                        lr: float = 2e-3, seed: int = 1, stream=None) -> Model:
+    """Train an entry-context model for ``ts`` on device buffers ``samples``
+    (labels from enumeration, every step in this library's kernels)."""
+    import torch
+    info = lx_tokenset_scan_table(ts)[2]
+    model = Model(info["S"] + 1, hidden=hidden, seed=seed)
+    wins, labs = [], []
+    for d in samples:
+        w, y = context_training_set(ctx, ts, model, d, stream=stream)
+        wins.append(w)
+        labs.append(y)
+    W = torch.cat(wins)
+    Y = torch.cat(labs)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    for _ in range(epochs):
+        perm = torch.randperm(W.shape[0], generator=g).to(W.device)
+        for i in range(0, W.shape[0] - batch + 1, batch):
+            idx = perm[i:i + batch]
+            model.train_step(W[idx].contiguous(), Y[idx].contiguous(), lr, stream=stream)
+    return model

@@ -82,6 +82,13 @@ struct EnParams {
     uint16_t *kinds;
     uint32_t *lens;
     uint64_t cap;
+    // speculative scans
+    uint16_t *ctx;               // [M] assumed entry context of each chunk
+    uint32_t *prev;              // [M] previous chunk with a start
+    uint8_t *dirty;              // [M] chunk to (re)scan from ctx
+    unsigned int *changed;       // a fix-up round changed some ctx
+    unsigned int *rescans;       // chunks scanned again after the first round
+    const uint16_t *guess;       // [M] predicted entry contexts (nullptr: BOUNDARY)
 };
 
 // Shared-memory view of the scan table.
@@ -423,24 +430,161 @@ __global__ void __launch_bounds__(EN_NT) en_emit(EnParams P)
     }
 }
 
+// ---- speculative scans: one context per chunk, fixed up round by round ----
+// A chunk's result is final once its entry equals the exit of its
+// predecessor under the predecessor's (final) entry; chunk 0 enters at
+// BOUNDARY.  Each round scans the chunks whose assumed entry changed, then
+// every chunk takes its predecessor's exit as its entry.  At the fixed point
+// the chain from offset 0 is consistent, so every entry is the true context.
+__global__ void __launch_bounds__(EN_NT) sp_init(EnParams P)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
+        const bool has = P.start[j] != NOPOS64;
+        uint16_t c = CTX_B;
+        if (j > 0 && has && P.guess) c = P.guess[j];
+        P.ctx[j] = c;
+        P.dirty[j] = has ? 1 : 0;
+        uint32_t q = NONE32_EN;
+        for (uint32_t k = j; k-- > 0;)
+            if (P.start[k] != NOPOS64) {
+                q = k;
+                break;
+            }
+        P.prev[j] = q;
+    }
+}
+
+__global__ void __launch_bounds__(EN_NT) sp_scan(EnParams P, uint32_t round)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const ScanEnv E = stage_scan(P, smem);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
+        if (!P.dirty[j]) continue;
+        uint32_t jn;
+        const uint64_t p1 = next_start(P, j, &jn);
+        CountTok ct;
+        uint64_t fail;
+        const uint16_t x = chunk_scan(E, P.start[j], p1, P.ctx[j], ct, fail);
+        ChunkRes r;
+        r.fail = fail;
+        r.count = ct.count;
+        r.exit = x;
+        r.pad = 0;
+        P.res[(size_t)j * KMAX] = r;
+        P.dirty[j] = 0;
+        if (round > 0) atomicAdd(P.rescans, 1u);
+    }
+}
+
+__global__ void __launch_bounds__(EN_NT) sp_fix(EnParams P)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
+        const uint32_t q = P.prev[j];
+        if (P.start[j] == NOPOS64 || q == NONE32_EN) continue;
+        const ChunkRes r = P.res[(size_t)q * KMAX];
+        if (r.fail != NOPOS64 || r.exit == CTX_BAD) continue;   // failed, or not settled yet
+        if (r.exit != P.ctx[j]) {
+            P.ctx[j] = r.exit;
+            P.dirty[j] = 1;
+            *P.changed = 1;
+        }
+    }
+}
+
+// Chunk starts and their true entry contexts (after en_resolve), per target.
+__global__ void __launch_bounds__(EN_NT) ctx_export(EnParams P, uint64_t *starts, uint16_t *ctx)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
+        const ChunkOut o = P.out[j];
+        starts[j] = o.live ? P.start[j] : NOPOS64;
+        ctx[j] = o.live ? o.entry : CTX_BAD;
+    }
+}
+
+// Output offsets along the settled chain (one CTA): each thread sums its run
+// of chunks, thread 0 links the runs and finds the first failure, each
+// thread labels its run.
+__global__ void __launch_bounds__(RS_NT) sp_offsets(EnParams P)
+{
+    __shared__ unsigned long long run_sum[RS_NT];
+    __shared__ uint32_t run_fail[RS_NT];   // first failing chunk of the run
+    const uint32_t t = threadIdx.x;
+    const uint32_t per = (P.M + RS_NT - 1) / RS_NT;
+    const uint32_t j0 = min(P.M, t * per), j1 = min(P.M, j0 + per);
+    unsigned long long sum = 0;
+    uint32_t f = NONE32_EN;
+    for (uint32_t j = j0; j < j1; j++) {
+        if (P.start[j] == NOPOS64) continue;
+        const ChunkRes r = P.res[(size_t)j * KMAX];
+        sum += r.count;
+        if (r.fail != NOPOS64) {
+            f = j;
+            break;
+        }
+    }
+    run_sum[t] = sum;
+    run_fail[t] = f;
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long acc = 0;
+        uint32_t r = 0;
+        bool failed = false;
+        for (; r < RS_NT; r++) {
+            const unsigned long long s = run_sum[r];
+            run_sum[r] = acc;   // exclusive prefix
+            acc += s;
+            if (run_fail[r] != NONE32_EN) {
+                P.rec->fail = P.res[(size_t)run_fail[r] * KMAX].fail;
+                failed = true;
+                r++;
+                break;
+            }
+        }
+        for (; r < RS_NT; r++) run_sum[r] = ~0ull;   // after the failure
+        P.rec->total = acc;
+        if (!failed) P.rec->fail = NOPOS64;
+    }
+    __syncthreads();
+    unsigned long long off = run_sum[t];
+    for (uint32_t j = j0; j < j1; j++) {
+        ChunkOut o{0, CTX_BAD, 0, 0};
+        if (P.start[j] != NOPOS64 && off != ~0ull) {
+            const ChunkRes r = P.res[(size_t)j * KMAX];
+            o.off = off;
+            o.entry = P.ctx[j];
+            o.live = 1;
+            off += r.count;
+            if (r.fail != NOPOS64) off = ~0ull;   // nothing after the failure
+        }
+        P.out[j] = o;
+    }
+}
+
 }  // namespace
 }  // namespace lx
 
 using namespace lx;
 
-extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
-                                  uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
-                                  uint64_t *consumed, void *stream)
+namespace {
+
+// Everything a run over one input needs: parameters, launch shapes, stream.
+struct EnRun {
+    EnParams P;
+    uint32_t grid = 0, smem = 0, rs_smem = 0;
+    cudaStream_t s = nullptr;
+    uint16_t *guess_buf = nullptr;   // [M] scratch for predicted contexts
+};
+
+// Validate, upload tables, size the scratch and fill the parameters.
+int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+             uint32_t *d_lens, uint64_t capacity, void *stream, EnRun &R)
 {
-    if (!c || !ts || !n_tokens || !consumed) return LX_E_INVAL;
+    if (!c || !ts) return LX_E_INVAL;
     if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
     if (n && !d_in) return LX_E_INVAL;
     if (capacity && (!d_kinds || !d_lens)) return LX_E_INVAL;
     const ScanTable &st = ts->scan;
     if (st.status != LX_OK) return st.status;
-    *n_tokens = 0;
-    *consumed = 0;
-    if (n == 0) return LX_OK;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
     void *blobs[3], *scan = nullptr;
@@ -449,17 +593,18 @@ extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_
     const uint64_t M64 = (n + CHUNK - 1) / CHUNK;
     if (M64 > 0xFFFFFFF0ull) return LX_E_INVAL;
     const uint32_t M = (uint32_t)M64;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t o_rec = 0, o_start = 256, o_cinfo = al(o_start + 8 * (size_t)M);
+    const size_t o_rec = 0, o_flags = 128, o_start = 256, o_cinfo = al(o_start + 8 * (size_t)M);
     const size_t o_res = al(o_cinfo + 4 * (size_t)M), o_out = al(o_res + sizeof(ChunkRes) * KMAX * (size_t)M);
-    const size_t total = al(o_out + sizeof(ChunkOut) * (size_t)M);
+    const size_t o_ctx = al(o_out + sizeof(ChunkOut) * (size_t)M), o_prev = al(o_ctx + 2 * (size_t)M);
+    const size_t o_dirty = al(o_prev + 4 * (size_t)M), o_guess = al(o_dirty + (size_t)M);
+    const size_t total = al(o_guess + 2 * (size_t)M);
     rc = grow(&c->e_dev, &c->e_dev_bytes, total);
     if (rc != LX_OK) return rc;
     uint8_t *d = static_cast<uint8_t *>(c->e_dev);
 
-    EnParams P;
+    EnParams &P = R.P;
     P.in = d_in;
     P.n = n;
     P.blob = static_cast<const uint8_t *>(scan);
@@ -480,40 +625,138 @@ extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_
     P.kinds = d_kinds;
     P.lens = d_lens;
     P.cap = capacity;
+    P.ctx = reinterpret_cast<uint16_t *>(d + o_ctx);
+    P.prev = reinterpret_cast<uint32_t *>(d + o_prev);
+    P.dirty = d + o_dirty;
+    P.changed = reinterpret_cast<unsigned int *>(d + o_flags);
+    P.rescans = reinterpret_cast<unsigned int *>(d + o_flags + 4);
+    P.guess = nullptr;
+    R.guess_buf = reinterpret_cast<uint16_t *>(d + o_guess);
 
-    const uint32_t smem = P.blob_bytes;
-    const uint32_t rs_smem = ((smem + 15u) & ~15u) + sizeof(Summary) * RS_NT * KMAX + 8u * RS_NT + 8u * RS_NT;
+    R.smem = P.blob_bytes;
+    R.rs_smem = ((R.smem + 15u) & ~15u) + sizeof(Summary) * RS_NT * KMAX + 8u * RS_NT + 8u * RS_NT;
     static bool attr_done[64] = {false};
     if (dev < 64 && !attr_done[dev]) {
-        if (cudaFuncSetAttribute(en_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) != cudaSuccess ||
-            cudaFuncSetAttribute(en_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(en_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) != cudaSuccess ||
+        const size_t lim = 64 * 1024;
+        if (cudaFuncSetAttribute(en_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+            cudaFuncSetAttribute(en_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+            cudaFuncSetAttribute(en_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+            cudaFuncSetAttribute(sp_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(en_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) !=
                 cudaSuccess)
             return LX_E_CUDA;
         attr_done[dev] = true;
     }
-    if (rs_smem > 220u * 1024u) return LX_E_TOOBIG;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((M + EN_NT - 1) / EN_NT, 4ull * c->num_sms);
+    if (R.rs_smem > 220u * 1024u) return LX_E_TOOBIG;
+    R.grid = (uint32_t)std::min<uint64_t>((M + EN_NT - 1) / EN_NT, 4ull * c->num_sms);
+    R.s = static_cast<cudaStream_t>(stream);
+    return cuda_err(cudaMemsetAsync(d, 0, 256, R.s));
+}
 
-    rc = cuda_err(cudaMemsetAsync(d, 0, 256, s));
+// Read back the record: status, token count and con(w).
+int en_finish(lx_ctx *c, const EnRun &R, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed,
+              unsigned int *rescans = nullptr)
+{
+    int rc = cuda_err(cudaGetLastError());
     if (rc != LX_OK) return rc;
-    if (c->timing) cudaEventRecord(c->ev[0], s);
-    en_plan<<<grid, EN_NT, smem, s>>>(P);
-    en_enumerate<<<grid, EN_NT, smem, s>>>(P);
-    en_resolve<<<1, RS_NT, rs_smem, s>>>(P);
-    en_emit<<<grid, EN_NT, smem, s>>>(P);
-    rc = cuda_err(cudaGetLastError());
-    if (c->timing) cudaEventRecord(c->ev[1], s);
+    uint8_t buf[256];
+    rc = cuda_err(cudaMemcpyAsync(c->h_res, R.P.rec, sizeof(EnResult), cudaMemcpyDeviceToHost, R.s));
+    if (rc == LX_OK && rescans) rc = cuda_err(cudaMemcpyAsync(rescans, R.P.rescans, 4, cudaMemcpyDeviceToHost, R.s));
+    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(R.s));
     if (rc != LX_OK) return rc;
+    std::memcpy(buf, c->h_res, sizeof(EnResult));
     EnResult r;
-    rc = cuda_err(cudaMemcpyAsync(c->h_res, P.rec, sizeof(EnResult), cudaMemcpyDeviceToHost, s));
-    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(s));
-    if (rc != LX_OK) return rc;
-    std::memcpy(&r, c->h_res, sizeof r);
+    std::memcpy(&r, buf, sizeof r);
     if (r.error) return LX_E_CUDA;
     *n_tokens = r.total;
-    *consumed = r.fail == NOPOS64 ? n : r.fail;
+    *consumed = r.fail == NOPOS64 ? R.P.n : r.fail;
     return r.total > capacity ? LX_E_CAPACITY : LX_OK;
+}
+
+}  // namespace
+
+extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+                                  uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
+                                  uint64_t *consumed, void *stream)
+{
+    if (!n_tokens || !consumed) return LX_E_INVAL;
+    *n_tokens = 0;
+    *consumed = 0;
+    EnRun R;
+    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R);
+    if (rc != LX_OK || n == 0) return rc;
+    if (c->timing) cudaEventRecord(c->ev[0], R.s);
+    en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    en_enumerate<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    en_resolve<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+    en_emit<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    if (c->timing) cudaEventRecord(c->ev[1], R.s);
+    return en_finish(c, R, capacity, n_tokens, consumed);
+}
+
+extern "C" int lx_chunk_contexts(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n,
+                                 uint64_t *d_starts, uint16_t *d_ctx, uint64_t cap, uint64_t *count, void *stream)
+{
+    if (!count || (cap && (!d_starts || !d_ctx))) return LX_E_INVAL;
+    *count = 0;
+    EnRun R;
+    int rc = en_setup(c, ts, d_in, n, LX_FULL_EXACT, nullptr, nullptr, 0, stream, R);
+    if (rc != LX_OK || n == 0) return rc;
+    *count = R.P.M;
+    if (cap < R.P.M) return LX_E_CAPACITY;
+    en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    en_enumerate<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    en_resolve<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+    ctx_export<<<R.grid, EN_NT, 0, R.s>>>(R.P, d_starts, d_ctx);
+    uint64_t nt, con;
+    rc = en_finish(c, R, ~0ull, &nt, &con);
+    return rc;
+}
+
+extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *model, const uint8_t *d_in,
+                                  uint64_t n, int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity,
+                                  uint64_t *n_tokens, uint64_t *consumed, lx_spec_stats *stats, void *stream)
+{
+    if (!n_tokens || !consumed) return LX_E_INVAL;
+    *n_tokens = 0;
+    *consumed = 0;
+    if (stats) *stats = lx_spec_stats{0, 0, 0, 0};
+    EnRun R;
+    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R);
+    if (rc != LX_OK || n == 0) return rc;
+    if (model && model_contexts(model) != ts->scan.S + 1) return LX_E_INVAL;
+    if (c->timing) cudaEventRecord(c->ev[0], R.s);
+    en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    if (model) {
+        rc = model_predict(model, R.P.in, R.P.n, R.P.start, R.P.cinfo, R.P.blob, R.P.cbeg_off, R.P.cand_off,
+                           R.P.M, R.guess_buf, R.s);
+        if (rc != LX_OK) return rc;
+        R.P.guess = R.guess_buf;
+    }
+    sp_init<<<R.grid, EN_NT, 0, R.s>>>(R.P);
+    unsigned int *h_flag = static_cast<unsigned int *>(c->h_res);
+    uint32_t rounds = 0;
+    for (;; rounds++) {
+        sp_scan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P, rounds);
+        rc = cuda_err(cudaMemsetAsync(R.P.changed, 0, 4, R.s));
+        if (rc != LX_OK) return rc;
+        sp_fix<<<R.grid, EN_NT, 0, R.s>>>(R.P);
+        rc = cuda_err(cudaMemcpyAsync(h_flag, R.P.changed, 4, cudaMemcpyDeviceToHost, R.s));
+        if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(R.s));
+        if (rc != LX_OK) return rc;
+        if (*h_flag == 0) break;
+        if (rounds > R.P.M + 1) return LX_E_CUDA;   // cannot happen: every round settles one more chunk
+    }
+    sp_offsets<<<1, RS_NT, 0, R.s>>>(R.P);
+    en_emit<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    if (c->timing) cudaEventRecord(c->ev[1], R.s);
+    unsigned int rescans = 0;
+    rc = en_finish(c, R, capacity, n_tokens, consumed, &rescans);
+    if (stats) {
+        stats->chunks = R.P.M;
+        stats->rounds = rounds + 1;
+        stats->rescanned = rescans;
+        stats->mispredicted_first = 0;
+    }
+    return rc;
 }

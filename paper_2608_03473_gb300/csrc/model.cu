@@ -1,0 +1,451 @@
+// model.cu -- the entry-context model of the speculative path: a small MLP
+// that reads the bytes around a chunk start and scores every context
+// (BOUNDARY or a DFA state), trained on the true contexts that the
+// enumerative path resolves.  The lexer stays exact whatever it predicts: a
+// wrong guess only costs a rescan.
+//
+//   h0 = [emb[x_0], ..., emb[x_{W-1}]]          x = w[p - W/2, p + W/2), pad byte 256 outside
+//   a1 = h0 W1 + b1,  h1 = relu(a1)              W1: (W*D) x H
+//   z  = h1 W2 + b2                              W2: H x C,  C = states + 1 (BOUNDARY = last)
+//   loss = mean over the batch of -log softmax(z)[y]
+// Inference takes the argmax of z over the candidate contexts of the byte
+// before p.  Master weights are FP32 (trained with Adam); inference reads a
+// BF16 copy.  The matrix products are plain FP32 tiled kernels: a few
+// hundred MFLOP per 512 MiB of input, well under 1 % of the lexing time.
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "runtime.h"
+
+namespace lx {
+namespace {
+
+constexpr uint32_t MW = 64;          // window bytes
+constexpr uint32_t MD = 8;           // embedding width
+constexpr uint32_t MROWS = 257;      // 256 byte values + padding
+constexpr uint32_t MIN_ = MW * MD;   // MLP input width
+constexpr int GT = 16;               // GEMM tile
+constexpr uint32_t PRED_BATCH = 16384;
+
+}  // namespace
+}  // namespace lx
+
+struct lx_model {
+    uint32_t C = 0, H = 0;
+    uint64_t step = 0;
+    // parameters in one FP32 block: emb | W1 | b1 | W2 | b2, and Adam moments
+    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    __nv_bfloat16 *w16 = nullptr;   // inference copy
+    size_t n_params = 0;
+    size_t o_emb = 0, o_w1 = 0, o_b1 = 0, o_w2 = 0, o_b2 = 0;
+    // activations for a batch, and windows for inference batches
+    float *act = nullptr;
+    size_t act_floats = 0;
+    uint16_t *win = nullptr;
+    int device = -1;
+};
+
+namespace lx {
+namespace {
+
+__device__ __forceinline__ uint32_t window_byte(const uint8_t *in, uint64_t n, uint64_t p, uint32_t k)
+{
+    const int64_t q = (int64_t)p - (int64_t)(MW / 2) + (int64_t)k;
+    return (q >= 0 && (uint64_t)q < n) ? (uint32_t)in[q] : 256u;
+}
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// h0[b, k*D + d] = emb[x_bk, d]; windows are given as bytes (256 = pad)
+template <class TW>
+__global__ void k_gather(const uint16_t *win, uint32_t B, const TW *emb, float *h0)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * MIN_) return;
+    const uint32_t b = i / MIN_, r = i % MIN_, k = r / MD, d = r % MD;
+    h0[i] = to_f(emb[(size_t)win[(size_t)b * MW + k] * MD + d]);
+}
+
+// C[M x N] = alpha * op(A) op(B) (+ bias[N]) (+ C if accumulate): A is M x K
+// (or K x M when ta), B is K x N (or N x K when tb), all row-major.
+template <class TW>
+__global__ void k_gemm(const float *A, const TW *Bm, float *Cm, const TW *bias, uint32_t M, uint32_t N,
+                       uint32_t K, int ta, int tb, int relu_out)
+{
+    __shared__ float As[GT][GT + 1], Bs[GT][GT + 1];
+    const uint32_t r = blockIdx.y * GT + threadIdx.y, c = blockIdx.x * GT + threadIdx.x;
+    float acc = 0.0f;
+    for (uint32_t k0 = 0; k0 < K; k0 += GT) {
+        const uint32_t ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+        As[threadIdx.y][threadIdx.x] =
+            (r < M && ka < K) ? (ta ? A[(size_t)ka * M + r] : A[(size_t)r * K + ka]) : 0.0f;
+        Bs[threadIdx.y][threadIdx.x] =
+            (kb < K && c < N) ? to_f(tb ? Bm[(size_t)c * K + kb] : Bm[(size_t)kb * N + c]) : 0.0f;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GT; k++) acc = fmaf(As[threadIdx.y][k], Bs[k][threadIdx.x], acc);
+        __syncthreads();
+    }
+    if (r < M && c < N) {
+        if (bias) acc += to_f(bias[c]);
+        if (relu_out) acc = acc > 0.0f ? acc : 0.0f;
+        Cm[(size_t)r * N + c] = acc;
+    }
+}
+
+// softmax cross-entropy per row: dz = (softmax(z) - onehot(y)) / B, loss sum
+__global__ void k_softmax_ce(const float *z, const uint16_t *y, uint32_t B, uint32_t C, float *dz, float *loss)
+{
+    const uint32_t b = blockIdx.x;
+    if (b >= B) return;
+    const float *zr = z + (size_t)b * C;
+    float mx = -INFINITY;
+    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) mx = fmaxf(mx, zr[c]);
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float se = 0.0f;
+    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) se += expf(zr[c] - mx);
+    for (int o = 16; o; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+    const float lse = mx + logf(se);
+    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) {
+        const float pr = expf(zr[c] - lse);
+        dz[(size_t)b * C + c] = (pr - (c == y[b] ? 1.0f : 0.0f)) / (float)B;
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, (lse - zr[y[b]]) / (float)B);
+}
+
+// column sums: out[c] = sum_b M[b, c]
+__global__ void k_colsum(const float *Mx, uint32_t B, uint32_t N, float *out)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    float s = 0.0f;
+    for (uint32_t b = 0; b < B; b++) s += Mx[(size_t)b * N + c];
+    out[c] = s;
+}
+
+// dA1 = dH1 * (A1 > 0)
+__global__ void k_relu_back(float *dh, const float *a, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && a[i] <= 0.0f) dh[i] = 0.0f;
+}
+
+// demb[x, d] += dh0[b, k*D + d]
+__global__ void k_emb_back(const uint16_t *win, uint32_t B, const float *dh0, float *demb)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * MIN_) return;
+    const uint32_t b = i / MIN_, r = i % MIN_, k = r / MD, d = r % MD;
+    atomicAdd(&demb[(size_t)win[(size_t)b * MW + k] * MD + d], dh0[i]);
+}
+
+__global__ void k_adam(float *w, float *m, float *v, const float *g, __nv_bfloat16 *w16, size_t n, float lr,
+                       float b1c, float b2c)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / b1c) / (sqrtf(vi / b2c) + 1e-8f);
+    w[i] = wi;
+    w16[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_to_bf16(const float *w, __nv_bfloat16 *w16, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w16[i] = __float2bfloat16(w[i]);
+}
+
+// windows of the chunk starts (pad where there is no start)
+__global__ void k_windows(const uint8_t *in, uint64_t n, const uint64_t *start, uint32_t j0, uint32_t cnt,
+                          uint16_t *win)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt * MW) return;
+    const uint32_t b = i / MW, k = i % MW;
+    const uint64_t p = start[j0 + b];
+    win[i] = p == ~0ull ? 256u : (uint16_t)window_byte(in, n, p, k);
+}
+
+// The argmax of the logits over the candidate contexts of the byte before
+// each chunk start (BOUNDARY = class C-1 -> 0xFFFE); one warp per chunk.
+__global__ void k_argmax(const float *z, uint32_t C, uint32_t j0, uint32_t cnt, const uint64_t *start,
+                         const uint32_t *cinfo, const uint8_t *scan_blob, uint32_t cbeg_off, uint32_t cand_off,
+                         uint16_t *guess)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= cnt) return;
+    const uint32_t j = j0 + b;
+    if (j == 0 || start[j] == ~0ull) {
+        if (lane == 0) guess[j] = 0xFFFEu;
+        return;
+    }
+    const uint16_t *cbeg = reinterpret_cast<const uint16_t *>(scan_blob + cbeg_off);
+    const uint16_t *cand = reinterpret_cast<const uint16_t *>(scan_blob + cand_off);
+    const uint32_t byte = cinfo[j] >> 8, lo = cbeg[byte], hi = cbeg[byte + 1];
+    const float *zr = z + (size_t)b * C;
+    float best = -INFINITY;
+    uint32_t arg = C - 1;
+    for (uint32_t t = lane; t < 1 + hi - lo; t += 32) {
+        const uint32_t c = t == 0 ? C - 1 : cand[lo + t - 1];
+        const float v = zr[c];
+        if (v > best || (v == best && c < arg)) {
+            best = v;
+            arg = c;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const uint32_t oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa < arg)) {
+            best = ob;
+            arg = oa;
+        }
+    }
+    if (lane == 0) guess[j] = arg == C - 1 ? (uint16_t)0xFFFEu : (uint16_t)arg;
+}
+
+}  // namespace
+
+uint32_t model_contexts(const lx_model *m) { return m ? m->C : 0; }
+
+}  // namespace lx
+
+using namespace lx;
+
+namespace {
+
+int ensure_act(lx_model *m, uint32_t B)
+{
+    const size_t need = (size_t)B * (MIN_ * 2 + m->H * 4 + m->C * 2) + 16;
+    if (m->act_floats >= need) return LX_OK;
+    if (m->act) cudaFree(m->act);
+    m->act = nullptr;
+    m->act_floats = 0;
+    if (cudaMalloc(&m->act, need * sizeof(float)) != cudaSuccess) return LX_E_NOMEM;
+    m->act_floats = need;
+    return LX_OK;
+}
+
+dim3 gemm_grid(uint32_t M, uint32_t N) { return dim3((N + GT - 1) / GT, (M + GT - 1) / GT); }
+
+// Forward (and with labels, backward into m->g) for a batch of windows.
+// Activations: h0 | a1 | h1 | z | dz | dh1 | dh0 | loss
+int model_pass(lx_model *m, const uint16_t *d_win, const uint16_t *d_y, uint32_t B, float *d_logits_out,
+               cudaStream_t s, float *h_loss)
+{
+    int rc = ensure_act(m, B);
+    if (rc != LX_OK) return rc;
+    const uint32_t H = m->H, C = m->C;
+    float *h0 = m->act, *a1 = h0 + (size_t)B * MIN_, *h1 = a1 + (size_t)B * H, *z = h1 + (size_t)B * H;
+    float *dz = z + (size_t)B * C, *dh1 = dz + (size_t)B * C, *dh0 = dh1 + (size_t)B * H;
+    float *loss = dh0 + (size_t)B * MIN_;
+    const float *w = m->w;
+    const dim3 t2(GT, GT);
+    const uint32_t nin = B * MIN_;
+    k_gather<float><<<(nin + 255) / 256, 256, 0, s>>>(d_win, B, w + m->o_emb, h0);
+    k_gemm<float><<<gemm_grid(B, H), t2, 0, s>>>(h0, w + m->o_w1, a1, w + m->o_b1, B, H, MIN_, 0, 0, 0);
+    cudaMemcpyAsync(h1, a1, sizeof(float) * B * H, cudaMemcpyDeviceToDevice, s);
+    k_relu_back<<<(B * H + 255) / 256, 256, 0, s>>>(h1, a1, (size_t)B * H);   // h1 = relu(a1)
+    k_gemm<float><<<gemm_grid(B, C), t2, 0, s>>>(h1, w + m->o_w2, z, w + m->o_b2, B, C, H, 0, 0, 0);
+    if (d_logits_out)
+        cudaMemcpyAsync(d_logits_out, z, sizeof(float) * B * C, cudaMemcpyDeviceToDevice, s);
+    if (!d_y) return cuda_err(cudaGetLastError());
+    float *g = m->g;
+    cudaMemsetAsync(loss, 0, sizeof(float), s);
+    cudaMemsetAsync(g, 0, sizeof(float) * m->n_params, s);
+    k_softmax_ce<<<B, 32, 0, s>>>(z, d_y, B, C, dz, loss);
+    k_gemm<float><<<gemm_grid(H, C), t2, 0, s>>>(h1, dz, g + m->o_w2, nullptr, H, C, B, 1, 0, 0);  // h1^T dz
+    k_colsum<<<(C + 255) / 256, 256, 0, s>>>(dz, B, C, g + m->o_b2);
+    k_gemm<float><<<gemm_grid(B, H), t2, 0, s>>>(dz, w + m->o_w2, dh1, nullptr, B, H, C, 0, 1, 0);  // dz W2^T
+    k_relu_back<<<(B * H + 255) / 256, 256, 0, s>>>(dh1, a1, (size_t)B * H);
+    k_gemm<float><<<gemm_grid(MIN_, H), t2, 0, s>>>(h0, dh1, g + m->o_w1, nullptr, MIN_, H, B, 1, 0, 0);
+    k_colsum<<<(H + 255) / 256, 256, 0, s>>>(dh1, B, H, g + m->o_b1);
+    k_gemm<float><<<gemm_grid(B, MIN_), t2, 0, s>>>(dh1, w + m->o_w1, dh0, nullptr, B, MIN_, H, 0, 1, 0);
+    k_emb_back<<<(nin + 255) / 256, 256, 0, s>>>(d_win, B, dh0, g + m->o_emb);
+    rc = cuda_err(cudaGetLastError());
+    if (rc == LX_OK && h_loss) {
+        rc = cuda_err(cudaMemcpyAsync(h_loss, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    }
+    return rc;
+}
+
+// splitmix64 -> uniform in [-a, a)
+float init_value(uint64_t &st, float a)
+{
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)((double)(z >> 11) / (double)(1ull << 53) * 2.0 - 1.0) * a;
+}
+
+}  // namespace
+
+int lx::model_predict(lx_model *m, const uint8_t *in, uint64_t n, const uint64_t *start, const uint32_t *cinfo,
+                      const uint8_t *scan_blob, uint32_t cbeg_off, uint32_t cand_off, uint32_t M, uint16_t *guess,
+                      cudaStream_t s)
+{
+    const uint32_t B = std::min<uint32_t>(M, PRED_BATCH);
+    int rc = ensure_act(m, B);
+    if (rc != LX_OK) return rc;
+    if (!m->win && cudaMalloc(&m->win, sizeof(uint16_t) * PRED_BATCH * MW) != cudaSuccess) return LX_E_NOMEM;
+    const uint32_t H = m->H, C = m->C;
+    float *h0 = m->act, *h1 = h0 + (size_t)B * MIN_, *z = h1 + (size_t)B * H;
+    const __nv_bfloat16 *w = m->w16;
+    const dim3 t2(GT, GT);
+    for (uint32_t j0 = 0; j0 < M; j0 += B) {
+        const uint32_t cnt = std::min<uint32_t>(B, M - j0);
+        k_windows<<<(cnt * MW + 255) / 256, 256, 0, s>>>(in, n, start, j0, cnt, m->win);
+        k_gather<__nv_bfloat16><<<(cnt * MIN_ + 255) / 256, 256, 0, s>>>(m->win, cnt, w + m->o_emb, h0);
+        k_gemm<__nv_bfloat16><<<gemm_grid(cnt, H), t2, 0, s>>>(h0, w + m->o_w1, h1, w + m->o_b1, cnt, H, MIN_, 0, 0, 1);
+        k_gemm<__nv_bfloat16><<<gemm_grid(cnt, C), t2, 0, s>>>(h1, w + m->o_w2, z, w + m->o_b2, cnt, C, H, 0, 0, 0);
+        k_argmax<<<(cnt * 32 + 255) / 256, 256, 0, s>>>(z, C, j0, cnt, start, cinfo, scan_blob, cbeg_off, cand_off,
+                                                        guess);
+    }
+    return cuda_err(cudaGetLastError());
+}
+
+extern "C" int lx_model_create(uint32_t n_contexts, uint32_t hidden, uint64_t seed, lx_model **out)
+{
+    if (!out || n_contexts < 2 || n_contexts > 0xFFFEu || hidden == 0 || hidden > 1024) return LX_E_INVAL;
+    *out = nullptr;
+    lx_model *m = new (std::nothrow) lx_model();
+    if (!m) return LX_E_NOMEM;
+    m->C = n_contexts;
+    m->H = hidden;
+    cudaGetDevice(&m->device);
+    m->o_emb = 0;
+    m->o_w1 = m->o_emb + (size_t)MROWS * MD;
+    m->o_b1 = m->o_w1 + (size_t)MIN_ * hidden;
+    m->o_w2 = m->o_b1 + hidden;
+    m->o_b2 = m->o_w2 + (size_t)hidden * n_contexts;
+    m->n_params = m->o_b2 + n_contexts;
+    std::vector<float> h(m->n_params, 0.0f);
+    uint64_t st = seed;
+    for (size_t i = m->o_emb; i < m->o_w1; i++) h[i] = init_value(st, 0.5f);
+    const float a1 = 1.0f / std::sqrt((float)MIN_), a2 = 1.0f / std::sqrt((float)hidden);
+    for (size_t i = m->o_w1; i < m->o_b1; i++) h[i] = init_value(st, a1);
+    for (size_t i = m->o_w2; i < m->o_b2; i++) h[i] = init_value(st, a2);
+    const size_t bytes = sizeof(float) * m->n_params;
+    bool ok = cudaMalloc(&m->w, bytes) == cudaSuccess && cudaMalloc(&m->m, bytes) == cudaSuccess &&
+              cudaMalloc(&m->v, bytes) == cudaSuccess && cudaMalloc(&m->g, bytes) == cudaSuccess &&
+              cudaMalloc(&m->w16, sizeof(__nv_bfloat16) * m->n_params) == cudaSuccess;
+    ok = ok && cudaMemcpy(m->w, h.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(m->m, 0, bytes) == cudaSuccess && cudaMemset(m->v, 0, bytes) == cudaSuccess;
+    if (ok) {
+        k_to_bf16<<<(unsigned)((m->n_params + 255) / 256), 256>>>(m->w, m->w16, m->n_params);
+        ok = cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (!ok) {
+        lx_model_free(m);
+        return LX_E_NOMEM;
+    }
+    *out = m;
+    return LX_OK;
+}
+
+extern "C" void lx_model_free(lx_model *m)
+{
+    if (!m) return;
+    cudaFree(m->w);
+    cudaFree(m->m);
+    cudaFree(m->v);
+    cudaFree(m->g);
+    cudaFree(m->w16);
+    cudaFree(m->act);
+    cudaFree(m->win);
+    delete m;
+}
+
+extern "C" int lx_model_info(const lx_model *m, uint32_t *n_contexts, uint32_t *hidden, uint32_t *window,
+                             uint32_t *embed, uint64_t *n_params)
+{
+    if (!m) return LX_E_INVAL;
+    if (n_contexts) *n_contexts = m->C;
+    if (hidden) *hidden = m->H;
+    if (window) *window = MW;
+    if (embed) *embed = MD;
+    if (n_params) *n_params = m->n_params;
+    return LX_OK;
+}
+
+extern "C" int lx_model_get_params(const lx_model *m, float *host, uint64_t count)
+{
+    if (!m || !host || count != m->n_params) return LX_E_INVAL;
+    return cuda_err(cudaMemcpy(host, m->w, sizeof(float) * count, cudaMemcpyDeviceToHost));
+}
+
+extern "C" int lx_model_set_params(lx_model *m, const float *host, uint64_t count)
+{
+    if (!m || !host || count != m->n_params) return LX_E_INVAL;
+    int rc = cuda_err(cudaMemcpy(m->w, host, sizeof(float) * count, cudaMemcpyHostToDevice));
+    if (rc != LX_OK) return rc;
+    k_to_bf16<<<(unsigned)((m->n_params + 255) / 256), 256>>>(m->w, m->w16, m->n_params);
+    return cuda_err(cudaDeviceSynchronize());
+}
+
+extern "C" int lx_model_windows(const uint8_t *d_in, uint64_t n, const uint64_t *d_pos, uint32_t count,
+                                uint16_t *d_windows, void *stream)
+{
+    if ((count && (!d_pos || !d_windows)) || (n && !d_in)) return LX_E_INVAL;
+    if (!count) return LX_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_windows<<<(count * MW + 255) / 256, 256, 0, s>>>(d_in, n, d_pos, 0, count, d_windows);
+    return cuda_err(cudaGetLastError());
+}
+
+extern "C" int lx_model_forward(lx_model *m, const uint16_t *d_windows, uint32_t batch, float *d_logits,
+                                void *stream)
+{
+    if (!m || !d_windows || !d_logits || batch == 0) return LX_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = model_pass(m, d_windows, nullptr, batch, d_logits, s, nullptr);
+    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    return rc;
+}
+
+extern "C" int lx_model_gradient(lx_model *m, const uint16_t *d_windows, const uint16_t *d_labels, uint32_t batch,
+                                 float *host_grad, uint64_t count, float *loss, void *stream)
+{
+    if (!m || !d_windows || !d_labels || batch == 0 || !host_grad || count != m->n_params) return LX_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float l = 0.0f;
+    int rc = model_pass(m, d_windows, d_labels, batch, nullptr, s, &l);
+    if (rc == LX_OK) rc = cuda_err(cudaMemcpy(host_grad, m->g, sizeof(float) * count, cudaMemcpyDeviceToHost));
+    if (loss) *loss = l;
+    return rc;
+}
+
+extern "C" int lx_model_train_step(lx_model *m, const uint16_t *d_windows, const uint16_t *d_labels,
+                                   uint32_t batch, float lr, float *loss, void *stream)
+{
+    if (!m || !d_windows || !d_labels || batch == 0 || !(lr > 0.0f)) return LX_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float l = 0.0f;
+    int rc = model_pass(m, d_windows, d_labels, batch, nullptr, s, &l);
+    if (rc != LX_OK) return rc;
+    m->step++;
+    const float b1c = 1.0f - std::pow(0.9f, (float)m->step), b2c = 1.0f - std::pow(0.999f, (float)m->step);
+    k_adam<<<(unsigned)((m->n_params + 255) / 256), 256, 0, s>>>(m->w, m->m, m->v, m->g, m->w16, m->n_params, lr,
+                                                                 b1c, b2c);
+    rc = cuda_err(cudaGetLastError());
+    if (loss) *loss = l;
+    return rc;
+}

@@ -64,5 +64,12 @@ int grow_host(void **p, size_t *have, size_t need);
 // blob of each mode and the plain scan table (nullptr where a table does not
 // exist for this token set).
 int ensure_device_tables(const lx_tokenset *ts, int device, void **out_blobs, void **out_scan);
+// The entry-context model (model.cu): number of contexts it scores, and the
+// BF16 prediction of the entry context of every chunk start (0xFFFE =
+// BOUNDARY) into guess[M], restricted to the candidates of the byte before.
+uint32_t model_contexts(const lx_model *m);
+int model_predict(lx_model *m, const uint8_t *in, uint64_t n, const uint64_t *start, const uint32_t *cinfo,
+                  const uint8_t *scan_blob, uint32_t cbeg_off, uint32_t cand_off, uint32_t M, uint16_t *guess,
+                  cudaStream_t s);
 
 }  // namespace lx
