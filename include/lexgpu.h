@@ -133,7 +133,8 @@ void lx_tokenset_free(lx_tokenset *ts);
  * tests): up to `cap` bytes into `out`, and meta[0..8] = {bytes, states,
  * classes, q0, next offset, accept offset, candidate-begin offset, candidate
  * offset, longest candidate list}.  Layout: class u8[256]; next u16[C*S]
- * (0xFFFF = undefined or leaving Q+); accept u16[S] (kind | 0x8000 when not
+ * (0xFFFF = undefined or leaving Q+; else the target state, | 0x8000 when it
+ * accepts); accept u16[S] (kind | 0x8000 when not
  * discarded, 0x7FFF = not accepting); cand_begin u16[257]; cand u16[...]:
  * for byte b the ascending states delta+(q, b), q in Q+, at
  * [cand_begin[b], cand_begin[b+1]).  Returns LX_E_TOOBIG when no such table

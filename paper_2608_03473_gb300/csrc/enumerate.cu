@@ -120,7 +120,13 @@ __device__ __forceinline__ ScanEnv stage_scan(const EnParams &P, uint8_t *smem)
     return E;
 }
 
-__device__ __forceinline__ uint32_t byte_at(const ScanEnv &E, uint64_t p) { return __ldg(E.in + p); }
+// A thread's view of the input: byte loads through the read-only path (a
+// chunk's consecutive bytes share L1 lines; holding 16-byte blocks in
+// registers measured slower).
+struct Bytes {
+    const uint8_t *in;
+    __device__ __forceinline__ uint32_t operator()(uint64_t p) { return __ldg(in + p); }
+};
 
 __device__ __forceinline__ uint32_t delta(const ScanEnv &E, uint32_t q, uint32_t b)
 {
@@ -129,26 +135,28 @@ __device__ __forceinline__ uint32_t delta(const ScanEnv &E, uint32_t q, uint32_t
 
 // The DFA run from state q before byte j while transitions are defined: the
 // last accepting end (> j) and its accept word, or NOPOS64.
-__device__ __forceinline__ uint64_t run_last_accept(const ScanEnv &E, uint32_t q, uint64_t j, uint32_t &acc)
+__device__ __forceinline__ uint64_t run_last_accept(const ScanEnv &E, Bytes &by, uint32_t q, uint64_t j,
+                                                    uint32_t &acc)
 {
     uint64_t last = NOPOS64;
+    uint32_t lq = 0;
     while (j < E.n) {
-        const uint32_t t = delta(E, q, byte_at(E, j));
+        const uint32_t t = delta(E, q, by(j));
         if (t == SCAN_NONE) break;
-        q = t;
+        q = t & ~(uint32_t)SCAN_ACCEPT;
         j++;
-        const uint32_t a = E.acc[q];
-        if ((a & 0x7FFFu) != KIND_NONE) {
+        if (t & SCAN_ACCEPT) {
             last = j;
-            acc = a;
+            lq = q;
         }
     }
+    if (last != NOPOS64) acc = E.acc[lq];
     return last;
 }
 
-__device__ __forceinline__ uint32_t state_after(const ScanEnv &E, uint32_t q, uint64_t lo, uint64_t hi)
+__device__ __forceinline__ uint32_t state_after(const ScanEnv &E, Bytes &by, uint32_t q, uint64_t lo, uint64_t hi)
 {
-    for (uint64_t j = lo; j < hi; j++) q = delta(E, q, byte_at(E, j));
+    for (uint64_t j = lo; j < hi; j++) q = delta(E, q, by(j)) & ~(uint32_t)SCAN_ACCEPT;
     return q;
 }
 
@@ -184,20 +192,21 @@ __device__ uint16_t chunk_scan(const ScanEnv &E, uint64_t p0, uint64_t p1, uint1
     fail = NOPOS64;
     uint64_t pos = p0;
     uint32_t acc = 0;
+    Bytes by{E.in};
     if (ctx != CTX_B) {
-        const uint64_t e = run_last_accept(E, ctx, p0, acc);
+        const uint64_t e = run_last_accept(E, by, ctx, p0, acc);
         if (e == NOPOS64) return CTX_BAD;
-        if (e >= p1) return e == p1 ? CTX_B : (uint16_t)state_after(E, ctx, p0, p1);
+        if (e >= p1) return e == p1 ? CTX_B : (uint16_t)state_after(E, by, ctx, p0, p1);
         pos = e;
     }
     while (pos < p1) {
-        const uint64_t e = run_last_accept(E, E.q0, pos, acc);
+        const uint64_t e = run_last_accept(E, by, E.q0, pos, acc);
         if (e == NOPOS64) {
             fail = pos;
             return CTX_BAD;
         }
         if (E.keep_all || (acc & KIND_KEEP)) emit(acc & 0x7FFFu, e - pos);
-        if (e >= p1) return e == p1 ? CTX_B : (uint16_t)state_after(E, E.q0, pos, p1);
+        if (e >= p1) return e == p1 ? CTX_B : (uint16_t)state_after(E, by, E.q0, pos, p1);
         pos = e;
     }
     return CTX_B;
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(EN_NT) en_plan(EnParams P)
         uint64_t best = NOPOS64;
         uint32_t bk = KMAX + 1, bb = 0;
         for (uint64_t p = lo; p < hi; p++) {
-            const uint32_t b = byte_at(E, p - 1);
+            const uint32_t b = __ldg(E.in + p - 1);
             const uint32_t k = n_cand(E, b);
             if (k < bk) {
                 bk = k;

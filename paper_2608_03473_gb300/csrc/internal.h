@@ -65,7 +65,8 @@ struct HostTable {
 // Plain DFA tables for scans entered in a context (splitting an input whose
 // token set certifies no byte): the class map, the next state per (class,
 // state) with targets outside Q+ made undefined (no accepting state is
-// reachable from them, so the longest match is unchanged), an accept word per
+// reachable from them, so the longest match is unchanged) and bit 15 set when
+// the target accepts (a scan tests acceptance without a lookup), an accept word per
 // state (bits 0..14 kind or KIND_NONE, bit 15 kept modulo I), and for every
 // byte b the ascending list of states delta+(q, b), q in Q+ -- the mid-token
 // contexts possible right after b.
@@ -79,6 +80,7 @@ struct ScanTable {
     std::vector<uint8_t> blob;
 };
 constexpr uint16_t SCAN_NONE = 0xFFFFu;
+constexpr uint16_t SCAN_ACCEPT = 0x8000u;   // next-state flag: the target state accepts
 
 struct DeviceTables {
     int device = -1;

@@ -268,7 +268,7 @@ void build_scan_table(const lx_tokenset &t, ScanTable &st)
     st.C = C;
     st.q0 = t.q0;
     st.cand_count.assign(256, 1);
-    if (S >= 0xFFFEu) {
+    if (S >= lx::SCAN_ACCEPT) {   // state numbers and the accept flag share 16 bits
         st.status = LX_E_TOOBIG;
         return;
     }
@@ -307,7 +307,9 @@ void build_scan_table(const lx_tokenset &t, ScanTable &st)
     for (uint32_t c = 0; c < C; c++)
         for (uint32_t q = 0; q < S; q++) {
             const uint32_t d = t.next[(size_t)c * S + q];
-            nx[(size_t)c * S + q] = (d != LX_NONE && live[d]) ? (uint16_t)d : lx::SCAN_NONE;
+            nx[(size_t)c * S + q] = (d != LX_NONE && live[d])
+                                        ? (uint16_t)(d | (t.accept[d] != LX_NO_KIND ? lx::SCAN_ACCEPT : 0u))
+                                        : lx::SCAN_NONE;
         }
     uint16_t *acc = reinterpret_cast<uint16_t *>(st.blob.data() + st.acc_off);
     for (uint32_t q = 0; q < S; q++) {

@@ -32,7 +32,7 @@ def _check(lg, dfa, discarded):
             continue
         for b in range(256):
             d = int(a.delta[q, b])
-            want = d if (d >= 0 and live[d]) else 0xFFFF
+            want = (d | (0x8000 if a.tau[d] >= 0 else 0)) if (d >= 0 and live[d]) else 0xFFFF
             assert int(nxt[cls[b], q]) == want, (q, b)
     acc = _u16(blob, m["acc_off"], S)
     for q in range(S):
