@@ -101,6 +101,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """The largest of x over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -280,11 +291,7 @@ def run_batch(args, rank, world, local):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1))
     value = world * total * args.steps / (total_ms / 1e3) / 1e9
     g_ms = statistics.mean(graph_ms)
     alg = total + 6 * n_tok
@@ -448,11 +455,7 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1))
     ms_per_step = total_ms / args.steps
     value = world * n * args.steps / (total_ms / 1e3) / 1e9
     tokens_per_s = world * nt * args.steps / (total_ms / 1e3)
@@ -489,11 +492,7 @@ def main():
         assert rc == 0 and nt3 == nt and con3 == con
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps)
     e2e_value = world * n / (e2e_ms / 1e3) / 1e9
 
     if rank == 0:

@@ -161,6 +161,16 @@ int lx_ctx_set_timeout_ms(lx_ctx *ctx, uint32_t ms);
 /* Kernel timing: when enabled, lx_lex records a CUDA event pair on its stream
  * around the tile-kernel launch; lx_ctx_last_kernel_ms returns the elapsed
  * time of the most recent launch (milliseconds, host out).  Off by default. */
+/*
+ * lx_ctx_debug_withhold -- failure-detection test hook.  In later lx_lex
+ * calls on this context, the CTA that processes tile `tile` (17 408-byte
+ * tiles) never publishes its look-back aggregate, so the bounded look-back
+ * waits of its successors run out: the call returns LX_E_TIMEOUT after about
+ * the context's timeout (lx_ctx_set_timeout_ms), every CTA stops claiming
+ * tiles once one wait has given up, and the context stays usable.
+ * 0xFFFFFFFF turns it off (the default).  No GPU fault is involved.
+ */
+int lx_ctx_debug_withhold(lx_ctx *ctx, uint32_t tile);
 int lx_ctx_enable_timing(lx_ctx *ctx, int on);
 int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
 

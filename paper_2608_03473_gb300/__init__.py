@@ -49,7 +49,7 @@ EXPORTED = (
     "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_scan_table",
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
-    "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune",
+    "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold",
     "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative", "lx_chunk_contexts",
     "lx_lex_speculative", "lx_model_create", "lx_model_free", "lx_model_info", "lx_model_get_params",
     "lx_model_set_params", "lx_model_windows", "lx_model_forward", "lx_model_gradient", "lx_model_train_step",
@@ -108,6 +108,7 @@ def load_library(path: Optional[str] = None):
             "lx_ctx_enable_timing": (i32, [vp, i32]),
             "lx_ctx_last_kernel_ms": (i32, [vp, vp]),
             "lx_ctx_set_config": (i32, [vp, vp, i32, u32, u32]),
+            "lx_ctx_debug_withhold": (i32, [vp, u32]),
             "lx_ctx_get_config": (i32, [vp, vp, i32, vp, vp, vp]),
             "lx_autotune": (i32, [vp, vp, i32, vp, u64, vp, vp, u64, vp]),
             "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
@@ -551,3 +552,9 @@ def train_context_model(ctx: Ctx, ts: Tokenset, samples, hidden: int = 64, epoch
             idx = perm[i:i + batch]
             model.train_step(W[idx].contiguous(), Y[idx].contiguous(), lr, stream=stream)
     return model
+
+
+def lx_ctx_debug_withhold(ctx: Ctx, tile: int) -> int:
+    """Failure-detection test hook: tile ``tile`` never publishes its
+    look-back aggregate (0xFFFFFFFF: off)."""
+    return load_library().lx_ctx_debug_withhold(ctx.handle, int(tile) & 0xFFFFFFFF)

@@ -105,6 +105,7 @@ struct Params {
     uint32_t *spill;       // per-CTA spill regions for long ranges' kept tokens
     uint32_t spill_cap;    // words per CTA (0: no spilling)
     uint32_t ks;           // record column height (words per thread)
+    uint32_t withhold;     // failure-detection tests: this tile never publishes (NONE32: off)
 };
 
 // ---- shared-memory layout (bytes from the dynamic shared base) ----
@@ -676,7 +677,9 @@ __device__ uint64_t resolve_prefix(const Params &P, uint32_t tile, uint64_t agg,
         const unsigned upto = incl ? (incl & (0u - incl)) : 0u;            // lowest lane holding one
         const unsigned lanes = incl ? ((upto - 1u) | upto) : 0xffffffffu;  // lanes to sum
         if (zero & lanes) {
-            if ((++spins & 15) == 0 && globaltimer() - t0 > P.timeout_ns) {
+            // bounded: the time budget, or another CTA already gave up
+            if ((++spins & 15) == 0 &&
+                (globaltimer() - t0 > P.timeout_ns || *(volatile unsigned int *)&P.res->error != 0)) {
                 timed_out = true;
                 break;
             }
@@ -689,7 +692,7 @@ __device__ uint64_t resolve_prefix(const Params &P, uint32_t tile, uint64_t agg,
         if (incl) break;
         base -= 32 * LB_PER_LANE;
     }
-    if (lane == 0) st_status(&P.status[tile], ST_INCL | (G + agg));
+    if (lane == 0 && tile != P.withhold) st_status(&P.status[tile], ST_INCL | (G + agg));
     return G;
 }
 
@@ -816,7 +819,8 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
     TileRef *s_tref = reinterpret_cast<TileRef *>(misc + M_TREF);
     // one thread: claim the next tile, note where it lies, start its copy
     auto claim = [&]() {
-        const uint32_t t = atomicAdd(P.tile_counter, 1u);
+        uint32_t t = atomicAdd(P.tile_counter, 1u);
+        if (*(volatile unsigned int *)&P.res->error != 0) t = P.n_tiles;   // a wait gave up: stop
         s_tile[0] = t;
         if (t >= P.n_tiles) return;
         const TileRef R = tile_ref(P, t);
@@ -995,7 +999,7 @@ __global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
             *s_tot = run;
             *s_flags = (any_big || run > (unsigned long long)STAGE_CAP) ? 1u : 0u;
             // publish this tile's aggregate at once
-            publish_aggregate(P, tile, run);
+            if (tile != P.withhold) publish_aggregate(P, tile, run);
             if (run) {
                 atomicAdd(&rec(T.doc)->total, run);
                 if (P.dres) atomicAdd(&P.res->total, run);
@@ -1201,6 +1205,13 @@ extern "C" int lx_ctx_last_kernel_ms(lx_ctx *c, float *ms)
     return cuda_err(cudaEventElapsedTime(ms, c->ev[0], c->ev[1]));
 }
 
+extern "C" int lx_ctx_debug_withhold(lx_ctx *c, uint32_t tile)
+{
+    if (!c) return LX_E_INVAL;
+    c->withhold = tile;
+    return LX_OK;
+}
+
 extern "C" int lx_ctx_set_timeout_ms(lx_ctx *c, uint32_t ms)
 {
     if (!c || ms == 0) return LX_E_INVAL;
@@ -1338,6 +1349,7 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     P.timeout_ns = c->timeout_ns;
     const LaunchCfg g = force ? *force : config_for(c, ts, mode);
     P.ks = g.ks;
+    P.withhold = c->withhold;
 
     const Layout L = make_layout(P.blob_bytes, P.ks);
     const int form = h.form;
@@ -1613,6 +1625,7 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
             P.spill_cap = SPILL_WORDS;
             P.timeout_ns = c->timeout_ns;
             P.ks = cfg[k].ks;
+            P.withhold = NONE32;
             launch_tiles(h.form, grid[k], smem[k], cs, P);
         }
         cudaMemcpyAsync(hs + B.down, dv, B.zero_end - 8 * TT, cudaMemcpyDeviceToHost, cs);
@@ -1895,6 +1908,7 @@ extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64
     P.spill = nullptr;   // no spill region: long ranges take the generic walker
     P.spill_cap = 0;
     P.ks = KS_DEFAULT;
+    P.withhold = NONE32;
     P.n_tiles = n_tiles;
     P.timeout_ns = 20ull * 1000 * 1000 * 1000;
 

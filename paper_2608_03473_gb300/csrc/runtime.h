@@ -28,6 +28,7 @@ struct lx_ctx {
     size_t scratch_bytes = 0;
     void *h_res = nullptr;   // pinned: the launch record read back by lx_lex
     uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;
+    uint32_t withhold = 0xFFFFFFFFu;   // failure-detection tests (lx_ctx_debug_withhold)
     std::vector<std::pair<uint64_t, int>> occupancy;   // (form << 32 | shared bytes) -> CTAs per SM
     std::vector<lx_tuned> tuned;                       // per (token set, mode); default otherwise
     // lx_lex_batch: device scratch, pinned staging (descriptors up, records
