@@ -452,8 +452,8 @@ __device__ __forceinline__ void walk_word(const Env &E, uint32_t &e, uint32_t &s
 // ---- lockstep walker (staged bytes only, 32-bit offsets) ----
 enum { LS_WALK = 0, LS_SLOW = 1, LS_END = 2, LS_TAIL = 3, LS_FULL = 4, LS_DONE = 5, LS_FAIL = 6, LS_OVF = 7 };
 
-// All lanes of a warp walk their ranges in lockstep, four bytes of one
-// aligned shared-memory word per lane per iteration, with no per-byte
+// All lanes of a warp walk their ranges in lockstep, two aligned
+// shared-memory words (eight bytes) per lane per iteration, with no per-byte
 // predicate: a lane whose chunk starts inside a word begins at the word in
 // the PRE row (the bytes between the word start and the chunk start are not
 // certified, PRE absorbs them), and a lane runs over the word holding its
@@ -547,13 +547,20 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
     for (;;) {
         while (__any_sync(0xffffffffu, st == LS_WALK)) {
             if (st == LS_WALK) {
-                if (sp + 4 * NT * 4 > col_end) {
+                if (sp + 8 * NT * 4 > col_end) {
                     st = LS_FULL;
                 } else {
-                    walk_word<FORM>(E, e, sp, lds_u32(E.buf + p), p);
+                    const uint32_t w0 = lds_u32(E.buf + p), w1 = lds_u32(E.buf + p + 4);
+                    walk_word<FORM>(E, e, sp, w0, p);
                     p += 4;
                     if (p >= mlim) st = eoi ? (e == P_slow ? LS_SLOW : LS_TAIL) : LS_END;
                     else if (e == P_slow) st = LS_SLOW;
+                    else {
+                        walk_word<FORM>(E, e, sp, w1, p);
+                        p += 4;
+                        if (p >= mlim) st = eoi ? (e == P_slow ? LS_SLOW : LS_TAIL) : LS_END;
+                        else if (e == P_slow) st = LS_SLOW;
+                    }
                 }
             }
         }
@@ -1888,17 +1895,7 @@ extern "C" int lx_lex_noalloc(const lx_tokenset *ts, const uint8_t *d_in, uint64
     P.dres = nullptr;
     P.prev = nullptr;
     P.n_prev = 0;
-    P.blob = scr;
-    P.blob_bytes = (uint32_t)h.blob.size();
-    P.table_bytes = h.table_bytes;
-    P.kind_off = h.kind_off;
-    P.cmap_off = h.cmap_off;
-    P.cert_off = h.cert_off;
-    P.ncols = h.ncols;
-    P.p_start = h.p_start;
-    P.p_flag = h.p_flag;
-    P.p_slow = h.p_slow;
-    P.p_pre = h.p_pre;
+    set_table_params(P, h, scr);
     P.out_kinds = d_kinds;
     P.out_lens = d_lens;
     P.cap = capacity;
