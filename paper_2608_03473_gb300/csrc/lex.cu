@@ -1189,6 +1189,11 @@ extern "C" void lx_ctx_free(lx_ctx *c)
     if (c->e_dev) cudaFree(c->e_dev);
     if (c->b_host) cudaFreeHost(c->b_host);
     if (c->d_in) cudaFree(c->d_in);
+    if (c->h_scratch) cudaFreeHost(c->h_scratch);
+    if (c->s_in) cudaStreamDestroy(c->s_in);
+    if (c->s_out) cudaStreamDestroy(c->s_out);
+    for (auto e : c->ev_in) cudaEventDestroy(e);
+    for (auto e : c->ev_lex) cudaEventDestroy(e);
     if (c->d_out) cudaFree(c->d_out);
     if (c->h_res) cudaFreeHost(c->h_res);
     for (auto &e : c->ev)
@@ -1417,33 +1422,170 @@ extern "C" int lx_lex(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
                       static_cast<cudaStream_t>(stream));
 }
 
+// lx_lex_host splits inputs of at least 2 * HOST_PIECE bytes into up to
+// HOST_PIECES pieces at certified bytes (the planner of Section 6 on the
+// host: each equal-division target slides forward to the next byte of the
+// mode's cut set, within HOST_SLIDE bytes), so that the copy of one piece in,
+// the lexing of another and the copy of a third's tokens out overlap.  Each
+// piece is lexed by its own launch, in order on the caller's stream, its
+// output placed after the previous pieces' tokens (device-side totals).
+constexpr uint64_t HOST_PIECE = 32ull << 20;
+constexpr uint32_t HOST_PIECES = 8;
+constexpr uint64_t HOST_SLIDE = 4ull << 20;
+
+static std::vector<uint64_t> host_pieces(const HostTable &h, const uint8_t *in, uint64_t n)
+{
+    std::vector<uint64_t> b{0};
+    const uint8_t *cert = h.blob.data() + h.cert_off;
+    uint32_t k = (uint32_t)std::min<uint64_t>(HOST_PIECES, n / HOST_PIECE);
+    bool any = false;
+    for (uint32_t x = 0; x < 256; x++) any |= cert[x] != 0;
+    if (!any || k < 2) k = 1;
+    for (uint32_t i = 1; i < k; i++) {
+        uint64_t t = n / k * i;
+        const uint64_t lim = std::min(n, t + HOST_SLIDE);
+        while (t < lim && !cert[in[t]]) t++;
+        if (t < lim && t > b.back()) b.push_back(t);
+    }
+    b.push_back(n);
+    return b;
+}
+
 extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in, uint64_t n, int mode,
                            uint16_t *h_kinds, uint32_t *h_lens, uint64_t capacity, uint64_t *n_tokens,
                            uint64_t *consumed, void *stream)
 {
     int rc = check_args(c, ts, h_in, n, mode, h_kinds, h_lens, capacity, n_tokens, consumed);
     if (rc != LX_OK) return rc;
+    const HostTable &h = ts->tab[mode];
+    if (h.status != LX_OK) return h.status;
+    *n_tokens = 0;
+    *consumed = 0;
+    if (n == 0) return LX_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
+    void *blobs[3];
+    rc = ensure_device_tables(ts, dev, blobs, nullptr);
+    if (rc != LX_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    rc = grow(&c->d_in, &c->d_in_bytes, n ? n : 1);
+    rc = grow(&c->d_in, &c->d_in_bytes, n);
     if (rc == LX_OK) rc = grow(&c->d_out, &c->d_out_bytes, capacity ? capacity * 6 + 16 : 16);
     if (rc != LX_OK) return rc;
     uint32_t *d_lens = static_cast<uint32_t *>(c->d_out);
     uint16_t *d_kinds = reinterpret_cast<uint16_t *>(d_lens + capacity);
-    if (n) {
-        rc = cuda_err(cudaMemcpyAsync(c->d_in, h_in, n, cudaMemcpyHostToDevice, st));
+    const uint8_t *d_in = static_cast<const uint8_t *>(c->d_in);
+
+    const std::vector<uint64_t> b = host_pieces(h, h_in, n);
+    const uint32_t K = (uint32_t)b.size() - 1;
+    if (!c->s_in && (cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking) != cudaSuccess))
+        return LX_E_CUDA;
+    while (c->ev_in.size() < K) {
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess)
+            return LX_E_CUDA;
+        c->ev_in.push_back(e1);
+        c->ev_lex.push_back(e2);
+    }
+
+    // scratch: one record + tile counter per piece, status words, spill regions
+    const Layout L = make_layout((uint32_t)h.blob.size(), config_for(c, ts, mode).ks);
+    const LaunchCfg g = config_for(c, ts, mode);
+    uint32_t grid_max = 0;
+    std::vector<uint32_t> tiles(K), grid(K);
+    uint64_t tiles_total = 0;
+    for (uint32_t i = 0; i < K; i++) {
+        tiles[i] = (uint32_t)((b[i + 1] - b[i] + TILE - 1) / TILE);
+        rc = grid_for(c, h.form, L.total, g, tiles[i], &grid[i]);
+        if (rc != LX_OK) return rc;
+        grid_max = std::max(grid_max, grid[i]);
+        tiles_total += tiles[i];
+    }
+    const size_t o_cnt = (sizeof(Result) * K + 63) & ~(size_t)63, o_status = o_cnt + 64 * (size_t)K;
+    const size_t zero = o_status + 8 * tiles_total;
+    const size_t o_spill = (zero + 255) & ~(size_t)255;
+    rc = grow(&c->scratch, &c->scratch_bytes, o_spill + sizeof(uint32_t) * (size_t)SPILL_WORDS * grid_max);
+    if (rc == LX_OK) rc = grow_host(&c->h_scratch, &c->h_scratch_bytes, sizeof(Result) * (size_t)K);
+    if (rc != LX_OK) return rc;
+    uint8_t *scr = static_cast<uint8_t *>(c->scratch);
+    Result *res = reinterpret_cast<Result *>(scr);   // one record per piece
+    Result *h_res = static_cast<Result *>(c->h_scratch);
+    uint8_t *d_in_w = static_cast<uint8_t *>(c->d_in);
+    rc = cuda_err(cudaMemsetAsync(scr, 0, zero, st));
+    if (rc != LX_OK) return rc;
+    // the pieces in, each on its own event
+    for (uint32_t i = 0; i < K; i++) {
+        rc = cuda_err(cudaMemcpyAsync(d_in_w + b[i], h_in + b[i], b[i + 1] - b[i], cudaMemcpyHostToDevice, c->s_in));
+        if (rc == LX_OK) rc = cuda_err(cudaEventRecord(c->ev_in[i], c->s_in));
         if (rc != LX_OK) return rc;
     }
-    rc = lex_device(c, ts, static_cast<const uint8_t *>(c->d_in), n, mode, d_kinds, d_lens, capacity,
-                    n_tokens, consumed, st);
-    if (rc != LX_OK && rc != LX_E_CAPACITY) return rc;
-    uint64_t m = std::min(*n_tokens, capacity);
-    if (m) {
-        int r2 = cuda_err(cudaMemcpyAsync(h_kinds, d_kinds, m * 2, cudaMemcpyDeviceToHost, st));
-        if (r2 == LX_OK) r2 = cuda_err(cudaMemcpyAsync(h_lens, d_lens, m * 4, cudaMemcpyDeviceToHost, st));
-        if (r2 == LX_OK) r2 = cuda_err(cudaStreamSynchronize(st));
-        if (r2 != LX_OK) return r2;
+    // the launches, in order on the caller's stream
+    if (c->timing) cudaEventRecord(c->ev[0], st);
+    uint64_t tile_off = 0;
+    for (uint32_t i = 0; i < K; i++) {
+        Params P;
+        P.one = DocDesc{d_in + b[i], b[i + 1] - b[i], 0,
+                        ((reinterpret_cast<uintptr_t>(d_in + b[i]) & 15u) == 0) ? 1u : 0u};
+        P.docs = nullptr;
+        P.tile_doc = nullptr;
+        P.dres = nullptr;
+        P.prev = res;
+        P.n_prev = i;
+        set_table_params(P, h, blobs[mode]);
+        P.out_kinds = d_kinds;
+        P.out_lens = d_lens;
+        P.cap = capacity;
+        P.n_tiles = tiles[i];
+        P.timeout_ns = c->timeout_ns;
+        P.ks = g.ks;
+        P.withhold = NONE32;
+        P.res = res + i;
+        P.tile_counter = reinterpret_cast<unsigned int *>(scr + o_cnt + 64 * (size_t)i);
+        P.status = reinterpret_cast<unsigned long long *>(scr + o_status) + tile_off;
+        P.spill = reinterpret_cast<uint32_t *>(scr + o_spill);
+        P.spill_cap = SPILL_WORDS;
+        tile_off += tiles[i];
+        rc = cuda_err(cudaStreamWaitEvent(st, c->ev_in[i], 0));
+        if (rc != LX_OK) return rc;
+        launch_tiles(h.form, grid[i], L.total, st, P);
+        rc = cuda_err(cudaMemcpyAsync(h_res + i, P.res, sizeof(Result), cudaMemcpyDeviceToHost, st));
+        if (rc == LX_OK) rc = cuda_err(cudaEventRecord(c->ev_lex[i], st));
+        if (rc != LX_OK) return rc;
     }
-    return rc;
+    if (c->timing) cudaEventRecord(c->ev[1], st);
+    // each piece's tokens out as soon as it is lexed
+    uint64_t out = 0, con = n;
+    bool failed = false;
+    for (uint32_t i = 0; i < K && !failed && rc == LX_OK; i++) {
+        rc = cuda_err(cudaEventSynchronize(c->ev_lex[i]));
+        if (rc != LX_OK) break;
+        const Result r = h_res[i];
+        if (r.error & ERR_TIMEOUT) rc = LX_E_TIMEOUT;
+        if (r.error & ERR_SMEM) rc = LX_E_TOOBIG;
+        if (rc != LX_OK) break;
+        uint64_t end = out + r.total;
+        if (r.inv_fail_pos) {   // Corollary 1: the first failing piece ends the stream
+            end = ~r.inv_fail_tok;
+            con = b[i] + ~r.inv_fail_pos;
+            failed = true;
+        }
+        const uint64_t lo = std::min(out, capacity), hi = std::min(end, capacity);
+        if (hi > lo) {
+            rc = cuda_err(cudaMemcpyAsync(h_kinds + lo, d_kinds + lo, (hi - lo) * 2, cudaMemcpyDeviceToHost, c->s_out));
+            if (rc == LX_OK)
+                rc = cuda_err(cudaMemcpyAsync(h_lens + lo, d_lens + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost, c->s_out));
+        }
+        out = end;
+    }
+    int r2 = cuda_err(cudaStreamSynchronize(c->s_out));
+    if (rc == LX_OK) rc = r2;
+    r2 = cuda_err(cudaStreamSynchronize(st));
+    if (rc == LX_OK) rc = r2;
+    if (rc != LX_OK) return rc;
+    *n_tokens = out;
+    *consumed = con;
+    return out > capacity ? LX_E_CAPACITY : LX_OK;
 }
 
 

@@ -43,11 +43,16 @@ struct lx_ctx {
     // lx_lex_enumerative: device scratch
     void *e_dev = nullptr;
     size_t e_dev_bytes = 0;
-    // device buffers of lx_lex_host
+    // device buffers of lx_lex_host, its copy streams, per-piece events and
+    // pinned per-piece records
     void *d_in = nullptr;
     size_t d_in_bytes = 0;
     void *d_out = nullptr;
     size_t d_out_bytes = 0;
+    void *h_scratch = nullptr;   // pinned
+    size_t h_scratch_bytes = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_lex;
     // optional kernel timing
     bool timing = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};

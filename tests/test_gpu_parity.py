@@ -232,3 +232,38 @@ def test_long_ranges_noalloc(gpu):
     assert rc == 0 and con == econ and nt == ek.size
     assert np.array_equal(k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), ek)
     assert np.array_equal(l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), el)
+
+
+@pytest.mark.parametrize("name,size", [("json", 96 << 20), ("clike", 130 << 20)])
+def test_lex_host_pieces(gpu, name, size):
+    """Inputs of 64 MiB and more go through lx_lex_host in pieces split at
+    certified bytes on the host (copies overlapping the lexing): the stream
+    must be the same, including a failure inside a later piece and the
+    capacity protocol."""
+    import torch
+    lg, ctx = gpu
+    ts = tokenset(lg, name)
+    w = corpus.generate(name, size, seed=14)
+    hk = torch.zeros(size // 2, dtype=torch.int16).pin_memory()
+    hl = torch.zeros(size // 2, dtype=torch.int32).pin_memory()
+    h_in = torch.from_numpy(w.copy()).pin_memory()
+    ek, el, econ = expected(name, w, 2)
+    rc, nt, con = lg.lx_lex_host(ctx, ts, h_in, 2, hk, hl)
+    assert rc == 0 and nt == ek.size and con == econ
+    assert np.array_equal(hk[:nt].numpy().view(np.uint16).astype(np.int64), ek)
+    assert np.array_equal(hl[:nt].numpy().view(np.uint32).astype(np.int64), el)
+    # a lexing error two thirds in
+    bad = w.copy()
+    bad[size * 2 // 3 + 12345] = 0x01
+    fk, fl, fcon = expected(name, bad, 2)
+    assert fcon < size
+    h_bad = torch.from_numpy(bad).pin_memory()
+    rc, nt, con = lg.lx_lex_host(ctx, ts, h_bad, 2, hk, hl)
+    assert rc == 0 and con == fcon and nt == fk.size
+    assert np.array_equal(hk[:nt].numpy().view(np.uint16).astype(np.int64), fk)
+    assert np.array_equal(hl[:nt].numpy().view(np.uint32).astype(np.int64), fl)
+    # capacity: the first `cap` tokens and the required count
+    cap = ek.size // 3
+    rc, nt, con = lg.lx_lex_host(ctx, ts, h_in, 2, hk, hl, capacity=cap)
+    assert rc == lg.LX_E_CAPACITY and nt == ek.size and con == econ
+    assert np.array_equal(hk[:cap].numpy().view(np.uint16).astype(np.int64), ek[:cap])
