@@ -220,22 +220,28 @@ int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_
  *   ks          -- token-end records per thread held in shared memory before
  *                  compaction / spilling (LX_KS_MIN .. LX_KS_MAX; default 40);
  *   ctas_per_sm -- resident CTAs per SM (0 = as many as fit; capped by what
- *                  fits).
+ *                  fits);
+ *   class_table -- 1: walk the class-indexed table even where the
+ *                  byte-indexed one fits (one more lookup per byte, a far
+ *                  smaller table, so more CTAs per SM).
+ * Without a configuration the context takes the byte-indexed table and ks 40
+ * unless the class-indexed table with some ks >= 32 fits more CTAs per SM.
  * Every configuration gives the same tokens; only speed differs.
  * lx_ctx_set_config sets one (LX_E_TOOBIG if its shared memory exceeds the
  * kernel's budget); lx_ctx_get_config reads the one in force (ms = the time
  * lx_autotune measured for it, 0 if set by hand or default).
- * lx_autotune times every ks in {24, 32, 40, 48, 56, 64} with the largest
- * and the smallest CTA count on `d_sample` (a device buffer representative
+ * lx_autotune times every ks in {24, 32, 36, 40, 48, 56, 64} on each table form,
+ * with the largest and the smallest CTA count, on `d_sample` (a device buffer representative
  * of the inputs to come, n bytes; outputs go to d_kinds / d_lens), checks that
  * all give the same result, and keeps the fastest.  Synchronizes `stream`.
  * The configuration also applies to lx_lex_batch groups of that token set.
  */
 #define LX_KS_MIN 16u
 #define LX_KS_MAX 96u
-int lx_ctx_set_config(lx_ctx *ctx, const lx_tokenset *ts, int mode, uint32_t ks, uint32_t ctas_per_sm);
+int lx_ctx_set_config(lx_ctx *ctx, const lx_tokenset *ts, int mode, uint32_t ks, uint32_t ctas_per_sm,
+                      uint32_t class_table);
 int lx_ctx_get_config(lx_ctx *ctx, const lx_tokenset *ts, int mode, uint32_t *ks, uint32_t *ctas_per_sm,
-                      float *ms);
+                      uint32_t *class_table, float *ms);
 int lx_autotune(lx_ctx *ctx, const lx_tokenset *ts, int mode, const uint8_t *d_sample, uint64_t n,
                 uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, void *stream);
 

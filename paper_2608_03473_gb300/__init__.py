@@ -107,9 +107,9 @@ def load_library(path: Optional[str] = None):
             "lx_ctx_set_timeout_ms": (i32, [vp, u32]),
             "lx_ctx_enable_timing": (i32, [vp, i32]),
             "lx_ctx_last_kernel_ms": (i32, [vp, vp]),
-            "lx_ctx_set_config": (i32, [vp, vp, i32, u32, u32]),
+            "lx_ctx_set_config": (i32, [vp, vp, i32, u32, u32, u32]),
             "lx_ctx_debug_withhold": (i32, [vp, u32]),
-            "lx_ctx_get_config": (i32, [vp, vp, i32, vp, vp, vp]),
+            "lx_ctx_get_config": (i32, [vp, vp, i32, vp, vp, vp, vp]),
             "lx_autotune": (i32, [vp, vp, i32, vp, u64, vp, vp, u64, vp]),
             "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
             "lx_lex_host": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
@@ -379,16 +379,18 @@ def lx_tokenset_scan_table(ts: Tokenset):
 LX_KS_MIN, LX_KS_MAX = 16, 96
 
 
-def lx_ctx_set_config(ctx: Ctx, ts: Tokenset, mode: int, ks: int, ctas_per_sm: int = 0) -> int:
-    return load_library().lx_ctx_set_config(ctx.handle, ts.handle, int(mode), int(ks), int(ctas_per_sm))
+def lx_ctx_set_config(ctx: Ctx, ts: Tokenset, mode: int, ks: int, ctas_per_sm: int = 0,
+                      class_table: int = 0) -> int:
+    return load_library().lx_ctx_set_config(ctx.handle, ts.handle, int(mode), int(ks), int(ctas_per_sm),
+                                            int(class_table))
 
 
 def lx_ctx_get_config(ctx: Ctx, ts: Tokenset, mode: int):
-    """(ks, ctas_per_sm, ms) in force for (ts, mode)."""
-    ks, ctas, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
+    """(ks, ctas_per_sm, class_table, ms) in force for (ts, mode)."""
+    ks, ctas, cls, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
     load_library().lx_ctx_get_config(ctx.handle, ts.handle, int(mode), ctypes.byref(ks), ctypes.byref(ctas),
-                                     ctypes.byref(ms))
-    return ks.value, ctas.value, ms.value
+                                     ctypes.byref(cls), ctypes.byref(ms))
+    return ks.value, ctas.value, cls.value, ms.value
 
 
 def lx_autotune(ctx: Ctx, ts: Tokenset, mode: int, d_sample, d_kinds, d_lens, n: Optional[int] = None,

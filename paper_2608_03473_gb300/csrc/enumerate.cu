@@ -596,9 +596,10 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     if (st.status != LX_OK) return st.status;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
-    void *blobs[3], *scan = nullptr;
-    int rc = ensure_device_tables(ts, dev, blobs, &scan);
+    DeviceTables dt;
+    int rc = ensure_device_tables(ts, dev, &dt);
     if (rc != LX_OK) return rc;
+    void *scan = dt.d_scan;
     const uint64_t M64 = (n + CHUNK - 1) / CHUNK;
     if (M64 > 0xFFFFFFF0ull) return LX_E_INVAL;
     const uint32_t M = (uint32_t)M64;

@@ -85,6 +85,7 @@ constexpr uint16_t SCAN_ACCEPT = 0x8000u;   // next-state flag: the target state
 struct DeviceTables {
     int device = -1;
     void *d_blob[3] = {nullptr, nullptr, nullptr};
+    void *d_blob_cls[3] = {nullptr, nullptr, nullptr};
     void *d_scan = nullptr;
 };
 
@@ -99,7 +100,8 @@ struct lx_tokenset {
     std::vector<uint8_t> live;        // [q], Q+
     bool reentrant = false;
     uint32_t exact[8] = {0}, modulo[8] = {0};
-    lx::HostTable tab[3];
+    lx::HostTable tab[3];       // per mode: byte-indexed when it fits, else class-indexed
+    lx::HostTable tab_cls[3];   // per mode: class-indexed (only when tab[m] is byte-indexed)
     lx::ScanTable scan;
     std::mutex mu;
     std::vector<lx::DeviceTables> dev;

@@ -738,7 +738,7 @@ __device__ __forceinline__ uint32_t cut_mask4(const Env &E, uint32_t w)
 }
 
 template <int FORM>
-__global__ void __launch_bounds__(NT, 2) lex_tiles(Params P)
+__global__ void __launch_bounds__(NT, 3) lex_tiles(Params P)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1108,14 +1108,13 @@ int cuda_err(cudaError_t e)
 
 using namespace lx;
 
-int lx::ensure_device_tables(const lx_tokenset *cts, int device, void **out_blobs, void **out_scan)
+int lx::ensure_device_tables(const lx_tokenset *cts, int device, DeviceTables *out)
 {
     lx_tokenset *ts = const_cast<lx_tokenset *>(cts);
     std::lock_guard<std::mutex> g(ts->mu);
     for (auto &d : ts->dev)
         if (d.device == device) {
-            for (int m = 0; m < 3; m++) out_blobs[m] = d.d_blob[m];
-            if (out_scan) *out_scan = d.d_scan;
+            *out = d;
             return LX_OK;
         }
     DeviceTables dt;
@@ -1126,18 +1125,22 @@ int lx::ensure_device_tables(const lx_tokenset *cts, int device, void **out_blob
         return rc;
     };
     int rc = LX_OK;
-    for (int m = 0; m < 3 && rc == LX_OK; m++)
+    for (int m = 0; m < 3 && rc == LX_OK; m++) {
         if (ts->tab[m].status == LX_OK) rc = upload(ts->tab[m].blob, &dt.d_blob[m]);
+        if (rc == LX_OK && ts->tab_cls[m].status == LX_OK && !ts->tab_cls[m].blob.empty())
+            rc = upload(ts->tab_cls[m].blob, &dt.d_blob_cls[m]);
+    }
     if (rc == LX_OK && ts->scan.status == LX_OK) rc = upload(ts->scan.blob, &dt.d_scan);
     if (rc != LX_OK) {
-        for (int m = 0; m < 3; m++)
+        for (int m = 0; m < 3; m++) {
             if (dt.d_blob[m]) cudaFree(dt.d_blob[m]);
+            if (dt.d_blob_cls[m]) cudaFree(dt.d_blob_cls[m]);
+        }
         if (dt.d_scan) cudaFree(dt.d_scan);
         return rc;
     }
     ts->dev.push_back(dt);
-    for (int m = 0; m < 3; m++) out_blobs[m] = dt.d_blob[m];
-    if (out_scan) *out_scan = dt.d_scan;
+    *out = dt;
     return LX_OK;
 }
 
@@ -1148,8 +1151,10 @@ extern "C" void lx_tokenset_free(lx_tokenset *ts)
     cudaGetDevice(&cur);
     for (auto &d : ts->dev) {
         cudaSetDevice(d.device);
-        for (int m = 0; m < 3; m++)
+        for (int m = 0; m < 3; m++) {
             if (d.d_blob[m]) cudaFree(d.d_blob[m]);
+            if (d.d_blob_cls[m]) cudaFree(d.d_blob_cls[m]);
+        }
         if (d.d_scan) cudaFree(d.d_scan);
     }
     if (cur >= 0 && !ts->dev.empty()) cudaSetDevice(cur);
@@ -1294,16 +1299,46 @@ static void launch_tiles(int form, uint32_t grid, uint32_t smem, cudaStream_t st
 struct LaunchCfg {
     uint32_t ks = KS_DEFAULT;
     uint32_t ctas = 0;   // CTAs per SM; 0 = as many as fit
+    uint32_t cls = 0;    // 1: the class-indexed table (when the default is byte-indexed)
 };
 
-static LaunchCfg config_for(const lx_ctx *c, const lx_tokenset *ts, int mode)
+static bool has_class_table(const lx_tokenset *ts, int mode)
+{
+    return ts->tab_cls[mode].status == LX_OK && !ts->tab_cls[mode].blob.empty();
+}
+
+static const HostTable &table_for(const lx_tokenset *ts, int mode, const LaunchCfg &g)
+{
+    return g.cls && has_class_table(ts, mode) ? ts->tab_cls[mode] : ts->tab[mode];
+}
+
+static LaunchCfg config_for(lx_ctx *c, const lx_tokenset *ts, int mode)
 {
     LaunchCfg g;
     for (const lx_tuned &t : c->tuned)
         if (t.ts == ts && t.mode == mode) {
             g.ks = t.ks;
             g.ctas = t.ctas;
+            g.cls = t.cls;
+            return g;
         }
+    // default: the byte-indexed table (one LOP3 per step) unless the smaller
+    // class-indexed one lets more CTAs share an SM with a column of >= 32
+    if (!has_class_table(ts, mode)) return g;
+    int occ_b = 0, occ_c = 0;
+    if (occupancy_for(c, ts->tab[mode].form, make_layout((uint32_t)ts->tab[mode].blob.size(), KS_DEFAULT).total,
+                      &occ_b) != LX_OK)
+        return g;
+    for (uint32_t ks = KS_DEFAULT; ks >= 32; ks -= 2) {
+        if (occupancy_for(c, FORM_CLASS, make_layout((uint32_t)ts->tab_cls[mode].blob.size(), ks).total, &occ_c) !=
+            LX_OK)
+            return g;
+        if (occ_c > occ_b) {
+            g.ks = ks;
+            g.cls = 1;
+            return g;
+        }
+    }
     return g;
 }
 
@@ -1324,8 +1359,9 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
                       uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
                       uint64_t *consumed, cudaStream_t st, const LaunchCfg *force = nullptr)
 {
-    const HostTable &h = ts->tab[mode];
-    if (h.status != LX_OK) return h.status;
+    if (ts->tab[mode].status != LX_OK) return ts->tab[mode].status;
+    const LaunchCfg g = force ? *force : config_for(c, ts, mode);
+    const HostTable &h = table_for(ts, mode, g);
     if (n == 0) {
         *n_tokens = 0;
         *consumed = 0;
@@ -1333,9 +1369,10 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
-    void *blobs[3];
-    int rc = ensure_device_tables(ts, dev, blobs, nullptr);
+    DeviceTables dt;
+    int rc = ensure_device_tables(ts, dev, &dt);
     if (rc != LX_OK) return rc;
+    void *blob = &h == &ts->tab_cls[mode] ? dt.d_blob_cls[mode] : dt.d_blob[mode];
 
     const uint64_t n_tiles64 = (n + TILE - 1) / TILE;
     if (n_tiles64 > 0xFFFFFFF0ull) return LX_E_INVAL;
@@ -1353,13 +1390,12 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     P.dres = nullptr;
     P.prev = nullptr;
     P.n_prev = 0;
-    set_table_params(P, h, blobs[mode]);
+    set_table_params(P, h, blob);
     P.out_kinds = d_kinds;
     P.out_lens = d_lens;
     P.cap = capacity;
     P.n_tiles = n_tiles;
     P.timeout_ns = c->timeout_ns;
-    const LaunchCfg g = force ? *force : config_for(c, ts, mode);
     P.ks = g.ks;
     P.withhold = c->withhold;
 
@@ -1457,16 +1493,18 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
 {
     int rc = check_args(c, ts, h_in, n, mode, h_kinds, h_lens, capacity, n_tokens, consumed);
     if (rc != LX_OK) return rc;
-    const HostTable &h = ts->tab[mode];
-    if (h.status != LX_OK) return h.status;
+    if (ts->tab[mode].status != LX_OK) return ts->tab[mode].status;
+    const LaunchCfg g = config_for(c, ts, mode);
+    const HostTable &h = table_for(ts, mode, g);
     *n_tokens = 0;
     *consumed = 0;
     if (n == 0) return LX_OK;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
-    void *blobs[3];
-    rc = ensure_device_tables(ts, dev, blobs, nullptr);
+    DeviceTables dt;
+    rc = ensure_device_tables(ts, dev, &dt);
     if (rc != LX_OK) return rc;
+    void *blob = &h == &ts->tab_cls[mode] ? dt.d_blob_cls[mode] : dt.d_blob[mode];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = grow(&c->d_in, &c->d_in_bytes, n);
     if (rc == LX_OK) rc = grow(&c->d_out, &c->d_out_bytes, capacity ? capacity * 6 + 16 : 16);
@@ -1490,8 +1528,7 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
     }
 
     // scratch: one record + tile counter per piece, status words, spill regions
-    const Layout L = make_layout((uint32_t)h.blob.size(), config_for(c, ts, mode).ks);
-    const LaunchCfg g = config_for(c, ts, mode);
+    const Layout L = make_layout((uint32_t)h.blob.size(), g.ks);
     uint32_t grid_max = 0;
     std::vector<uint32_t> tiles(K), grid(K);
     uint64_t tiles_total = 0;
@@ -1532,7 +1569,7 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
         P.dres = nullptr;
         P.prev = res;
         P.n_prev = i;
-        set_table_params(P, h, blobs[mode]);
+        set_table_params(P, h, blob);
         P.out_kinds = d_kinds;
         P.out_lens = d_lens;
         P.cap = capacity;
@@ -1694,12 +1731,12 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
     uint32_t grid_max = 0;
     for (uint32_t k = 0; k < G; k++) {
         const lx_tokenset *ts = sets[groups[k].set];
-        void *blobs[3];
-        int rc = ensure_device_tables(ts, dev, blobs, nullptr);
+        DeviceTables dt;
+        int rc = ensure_device_tables(ts, dev, &dt);
         if (rc != LX_OK) return rc;
-        blob[k] = blobs[mode];
-        const HostTable &h = ts->tab[mode];
         cfg[k] = config_for(c, ts, mode);
+        const HostTable &h = table_for(ts, mode, cfg[k]);
+        blob[k] = &h == &ts->tab_cls[mode] ? dt.d_blob_cls[mode] : dt.d_blob[mode];
         smem[k] = make_layout((uint32_t)h.blob.size(), cfg[k].ks).total;
         rc = grid_for(c, h.form, smem[k], cfg[k], groups[k].n_tiles, &grid[k]);
         if (rc != LX_OK) return rc;
@@ -1754,7 +1791,7 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
         Result *res = reinterpret_cast<Result *>(dv + B.res);
         for (uint32_t k = 0; k < G; k++) {
             const BatchGroup &g = groups[k];
-            const HostTable &h = sets[g.set]->tab[mode];
+            const HostTable &h = table_for(sets[g.set], mode, cfg[k]);
             Params P;
             P.one = DocDesc{nullptr, 0, 0, 0};
             P.docs = reinterpret_cast<const DocDesc *>(dv + B.docs) + g.doc_begin;
@@ -1825,16 +1862,18 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
 // ---------------------------------------------------------------------------
 // launch configuration: set by hand or measured
 // ---------------------------------------------------------------------------
-static void store_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t ks, uint32_t ctas, float ms)
+static void store_config(lx_ctx *c, const lx_tokenset *ts, int mode, const LaunchCfg &g, float ms)
 {
+    bool found = false;
     for (lx_tuned &t : c->tuned)
         if (t.ts == ts && t.mode == mode) {
-            t.ks = ks;
-            t.ctas = ctas;
+            t.ks = g.ks;
+            t.ctas = g.ctas;
+            t.cls = g.cls;
             t.ms = ms;
-            return;
+            found = true;
         }
-    c->tuned.push_back(lx_tuned{ts, mode, ks, ctas, ms});
+    if (!found) c->tuned.push_back(lx_tuned{ts, mode, g.ks, g.ctas, g.cls, ms});
     if (c->b_exec) {   // a cached batch graph may hold the old configuration
         cudaGraphExecDestroy(c->b_exec);
         c->b_exec = nullptr;
@@ -1842,26 +1881,33 @@ static void store_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t ks
     }
 }
 
-extern "C" int lx_ctx_set_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t ks, uint32_t ctas_per_sm)
+extern "C" int lx_ctx_set_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t ks, uint32_t ctas_per_sm,
+                                 uint32_t class_table)
 {
     if (!c || !ts) return LX_E_INVAL;
     if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
-    if (ks < KS_MIN || ks > LX_KS_MAX) return LX_E_INVAL;
-    if (make_layout((uint32_t)ts->tab[mode].blob.size(), ks).total > 200u * 1024u) return LX_E_TOOBIG;
-    store_config(c, ts, mode, ks, ctas_per_sm, 0.0f);
+    if (ks < KS_MIN || ks > LX_KS_MAX || class_table > 1) return LX_E_INVAL;
+    LaunchCfg g;
+    g.ks = ks;
+    g.ctas = ctas_per_sm;
+    g.cls = class_table && has_class_table(ts, mode) ? 1u : 0u;
+    if (make_layout((uint32_t)table_for(ts, mode, g).blob.size(), ks).total > 200u * 1024u) return LX_E_TOOBIG;
+    store_config(c, ts, mode, g, 0.0f);
     return LX_OK;
 }
 
 extern "C" int lx_ctx_get_config(lx_ctx *c, const lx_tokenset *ts, int mode, uint32_t *ks, uint32_t *ctas_per_sm,
-                                 float *ms)
+                                 uint32_t *class_table, float *ms)
 {
     if (!c || !ts) return LX_E_INVAL;
-    LaunchCfg g = config_for(c, ts, mode);
+    if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
+    const LaunchCfg g = config_for(c, ts, mode);
     float t = 0.0f;
     for (const lx_tuned &x : c->tuned)
         if (x.ts == ts && x.mode == mode) t = x.ms;
     if (ks) *ks = g.ks;
     if (ctas_per_sm) *ctas_per_sm = g.ctas;
+    if (class_table) *class_table = table_for(ts, mode, g).form == FORM_CLASS ? 1u : 0u;
     if (ms) *ms = t;
     return LX_OK;
 }
@@ -1872,8 +1918,7 @@ extern "C" int lx_autotune(lx_ctx *c, const lx_tokenset *ts, int mode, const uin
     uint64_t unused_t = 0, unused_c = 0;
     int rc = check_args(c, ts, d_sample, n, mode, d_kinds, d_lens, capacity, &unused_t, &unused_c);
     if (rc != LX_OK || n == 0) return rc == LX_OK ? LX_E_INVAL : rc;
-    const HostTable &h = ts->tab[mode];
-    if (h.status != LX_OK) return h.status;
+    if (ts->tab[mode].status != LX_OK) return ts->tab[mode].status;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1885,51 +1930,56 @@ extern "C" int lx_autotune(lx_ctx *c, const lx_tokenset *ts, int mode, const uin
     float best = 1e30f;
     LaunchCfg best_g;
     uint64_t ref_tokens = ~0ull, ref_con = ~0ull;
-    static const uint32_t ks_list[] = {24, 32, 40, 48, 56, 64};
-    for (uint32_t ks : ks_list) {
-        const uint32_t smem = make_layout((uint32_t)h.blob.size(), ks).total;
-        if (smem > 200u * 1024u) continue;
-        int occ = 0;
-        rc = occupancy_for(c, h.form, smem, &occ);
-        if (rc != LX_OK) break;
-        for (uint32_t ctas : {(uint32_t)occ, 1u}) {
-            if (ctas == 1 && occ == 1) continue;
-            LaunchCfg g;
-            g.ks = ks;
-            g.ctas = ctas;
-            uint64_t nt = 0, con = 0;
-            float total = 0.0f;
-            for (int rep = 0; rep < 4 && rc == LX_OK; rep++) {
-                cudaEventRecord(e0, st);
-                rc = lex_device(c, ts, d_sample, n, mode, d_kinds, d_lens, capacity, &nt, &con, st, &g);
-                cudaEventRecord(e1, st);
-                if (rc == LX_E_CAPACITY) rc = LX_OK;
+    static const uint32_t ks_list[] = {24, 32, 36, 40, 48, 56, 64};
+    for (uint32_t cls = 0; cls < (has_class_table(ts, mode) ? 2u : 1u) && rc == LX_OK; cls++) {
+        for (uint32_t ks : ks_list) {
+            LaunchCfg g0;
+            g0.ks = ks;
+            g0.cls = cls;
+            const HostTable &h = table_for(ts, mode, g0);
+            const uint32_t smem = make_layout((uint32_t)h.blob.size(), ks).total;
+            if (smem > 200u * 1024u) continue;
+            int occ = 0;
+            rc = occupancy_for(c, h.form, smem, &occ);
+            if (rc != LX_OK) break;
+            for (uint32_t ctas : {(uint32_t)occ, 1u}) {
+                if (ctas == 1 && occ == 1) continue;
+                LaunchCfg g = g0;
+                g.ctas = ctas;
+                uint64_t nt = 0, con = 0;
+                float total = 0.0f;
+                for (int rep = 0; rep < 4 && rc == LX_OK; rep++) {
+                    cudaEventRecord(e0, st);
+                    rc = lex_device(c, ts, d_sample, n, mode, d_kinds, d_lens, capacity, &nt, &con, st, &g);
+                    cudaEventRecord(e1, st);
+                    if (rc == LX_E_CAPACITY) rc = LX_OK;
+                    if (rc != LX_OK) break;
+                    cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep) total += ms;   // the first run warms up
+                }
                 if (rc != LX_OK) break;
-                cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep) total += ms;   // the first run warms up
+                if (ref_tokens == ~0ull) {
+                    ref_tokens = nt;
+                    ref_con = con;
+                } else if (nt != ref_tokens || con != ref_con) {
+                    rc = LX_E_CUDA;   // every configuration must give the same result
+                    break;
+                }
+                if (total / 3 < best) {
+                    best = total / 3;
+                    best_g = g;
+                }
             }
             if (rc != LX_OK) break;
-            if (ref_tokens == ~0ull) {
-                ref_tokens = nt;
-                ref_con = con;
-            } else if (nt != ref_tokens || con != ref_con) {
-                rc = LX_E_CUDA;   // every configuration must give the same result
-                break;
-            }
-            if (total / 3 < best) {
-                best = total / 3;
-                best_g = g;
-            }
         }
-        if (rc != LX_OK) break;
     }
     c->timing = timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LX_OK) return rc;
-    store_config(c, ts, mode, best_g.ks, best_g.ctas, best);
+    store_config(c, ts, mode, best_g, best);
     return LX_OK;
 }
 

@@ -17,7 +17,7 @@
 struct lx_tuned {
     const lx_tokenset *ts;
     int mode;
-    uint32_t ks, ctas;
+    uint32_t ks, ctas, cls;   // cls: class-indexed table
     float ms;   // measured by lx_autotune (0 when set by hand)
 };
 
@@ -67,9 +67,9 @@ int cuda_err(cudaError_t e);
 int grow(void **p, size_t *have, size_t need);
 int grow_host(void **p, size_t *have, size_t need);
 // The token set's tables on `device` (uploaded on first use): the walk-table
-// blob of each mode and the plain scan table (nullptr where a table does not
-// exist for this token set).
-int ensure_device_tables(const lx_tokenset *ts, int device, void **out_blobs, void **out_scan);
+// blobs of each mode (both forms where both exist) and the plain scan table
+// (nullptr where a table does not exist for this token set).
+int ensure_device_tables(const lx_tokenset *ts, int device, DeviceTables *out);
 // The entry-context model (model.cu): number of contexts it scores, and the
 // BF16 prediction of the entry context of every chunk start (0xFFFE =
 // BOUNDARY) into guess[M], restricted to the candidates of the byte before.

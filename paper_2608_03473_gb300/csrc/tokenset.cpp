@@ -143,7 +143,7 @@ void derive_certificates(lx_tokenset &t)
 inline bool bit(const uint32_t m[8], uint32_t b) { return (m[b >> 5] >> (b & 31)) & 1u; }
 
 // Walk rows (see internal.h).  target(row, class) -> row.
-void build_table(const lx_tokenset &t, int mode, HostTable &ht)
+void build_table(const lx_tokenset &t, int mode, HostTable &ht, bool class_form)
 {
     const uint32_t S = t.n_states, C = t.n_classes, q0 = t.q0;
     auto nx = [&](uint32_t c, uint32_t q) { return t.next[(size_t)c * S + q]; };
@@ -203,7 +203,7 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht)
 
     ht = HostTable();
     ht.n_rows = R;
-    bool byte_form = (uint64_t)R * 512 <= lx::MAX_BYTE_FORM_BYTES;
+    bool byte_form = !class_form && (uint64_t)R * 512 <= lx::MAX_BYTE_FORM_BYTES;
     std::vector<uint32_t> P(R);
     if (byte_form) {
         ht.form = lx::FORM_BYTE;
@@ -360,7 +360,12 @@ extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
         t->discard.assign(dfa->n_kinds, 0);
         for (uint32_t k = 0; k < n_discarded; k++) t->discard[discarded[k]] = 1;
         derive_certificates(*t);
-        for (int m = 0; m < 3; m++) build_table(*t, m, t->tab[m]);
+        for (int m = 0; m < 3; m++) {
+            build_table(*t, m, t->tab[m], false);
+            // the class-indexed form as well when the default is byte-indexed:
+            // far smaller, so more CTAs fit per SM
+            if (t->tab[m].form == lx::FORM_BYTE) build_table(*t, m, t->tab_cls[m], true);
+        }
         build_scan_table(*t, t->scan);
     } catch (const std::bad_alloc &) {
         delete t;

@@ -46,13 +46,16 @@ def test_every_config_is_exact(gpu, name):
     w = corpus.generate(name, 2 << 20, seed=41)
     ek, el, econ = _expected(name, w, 2)
     d = torch.from_numpy(w.copy()).cuda()
-    for ks in (16, 24, 40, 64, 96):
-        for ctas in (0, 1):
-            assert lg.lx_ctx_set_config(ctx, ts, 2, ks, ctas) == 0
-            assert lg.lx_ctx_get_config(ctx, ts, 2)[:2] == (ks, ctas)
-            rc, k, l, con = _lex(lg, ctx, ts, d, 2, w.size)
-            assert rc == 0 and con == econ, (ks, ctas)
-            assert np.array_equal(k.astype(np.int64), ek) and np.array_equal(l.astype(np.int64), el), (ks, ctas)
+    for cls in (0, 1):
+        for ks in (16, 24, 36, 40, 64, 96):
+            for ctas in (0, 1):
+                assert lg.lx_ctx_set_config(ctx, ts, 2, ks, ctas, cls) == 0
+                got = lg.lx_ctx_get_config(ctx, ts, 2)
+                assert got[:2] == (ks, ctas) and (got[2] == 1 if cls else True)
+                rc, k, l, con = _lex(lg, ctx, ts, d, 2, w.size)
+                assert rc == 0 and con == econ, (cls, ks, ctas)
+                assert np.array_equal(k.astype(np.int64), ek), (cls, ks, ctas)
+                assert np.array_equal(l.astype(np.int64), el), (cls, ks, ctas)
 
 
 def test_invalid_config(gpu):
@@ -60,6 +63,7 @@ def test_invalid_config(gpu):
     ts = lg.lx_compile_tokenset(T.tokenset("json"), T.discarded_kinds("json"))
     assert lg.lx_ctx_set_config(ctx, ts, 2, 8, 0) == lg.LX_E_INVAL
     assert lg.lx_ctx_set_config(ctx, ts, 2, 200, 0) == lg.LX_E_INVAL
+    assert lg.lx_ctx_set_config(ctx, ts, 2, 40, 0, 2) == lg.LX_E_INVAL
     assert lg.lx_ctx_set_config(ctx, ts, 9, 40, 0) == lg.LX_E_MODE
 
 
@@ -73,8 +77,8 @@ def test_autotune_then_lex(gpu):
     k = torch.zeros(w.size, dtype=torch.int16, device="cuda")
     l = torch.zeros(w.size, dtype=torch.int32, device="cuda")
     assert lg.lx_autotune(ctx, ts, 2, d, k, l) == 0
-    ks, ctas, ms = lg.lx_ctx_get_config(ctx, ts, 2)
-    assert ks in (24, 32, 40, 48, 56, 64) and ms > 0
+    ks, ctas, cls, ms = lg.lx_ctx_get_config(ctx, ts, 2)
+    assert ks in (24, 32, 36, 40, 48, 56, 64) and ms > 0
     ek, el, econ = _expected("json", w, 2)
     rc, kk, ll, con = _lex(lg, ctx, ts, d, 2, w.size)
     assert rc == 0 and con == econ
@@ -95,9 +99,9 @@ def test_batch_uses_config(gpu):
     k = torch.zeros(total + 64, dtype=torch.int16, device="cuda")
     l = torch.zeros(total + 64, dtype=torch.int32, device="cuda")
     docs = [((d.data_ptr() + o, s), names.index(nm)) for (nm, s, _), o in zip(spec, offs)]
-    for ks in (40, 16):
+    for ks, cls in ((40, 0), (16, 1)):
         for ts in sets:
-            assert lg.lx_ctx_set_config(ctx, ts, 2, ks, 0) == 0
+            assert lg.lx_ctx_set_config(ctx, ts, 2, ks, 0, cls) == 0
         rc, n_total, res = lg.lx_lex_batch(ctx, sets, docs, 2, k, l)
         assert rc == 0
         kk = k[:n_total].cpu().numpy().view(np.uint16)
@@ -107,3 +111,15 @@ def test_batch_uses_config(gpu):
             assert con == econ and nt == ek.size
             assert np.array_equal(kk[off:off + nt].astype(np.int64), ek)
             assert np.array_equal(ll[off:off + nt].astype(np.int64), el)
+
+
+def test_default_config_prefers_occupancy(gpu):
+    """JSON's byte-indexed table is 18 KB; its class-indexed one fits three
+    CTAs per SM, which the default configuration takes."""
+    lg, _ = gpu
+    ctx = lg.lx_ctx_create()
+    ts = lg.lx_compile_tokenset(T.tokenset("json"), T.discarded_kinds("json"))
+    ks, ctas, cls, ms = lg.lx_ctx_get_config(ctx, ts, 2)
+    assert cls == 1 and 32 <= ks <= 40 and ms == 0
+    tc = lg.lx_compile_tokenset(T.tokenset("clike"), T.discarded_kinds("clike"))
+    assert lg.lx_ctx_get_config(ctx, tc, 2)[:3] == (40, 0, 1)   # class-indexed anyway
