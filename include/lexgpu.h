@@ -123,6 +123,10 @@ int lx_tokenset_info(const lx_tokenset *ts, int mode, uint32_t *n_states, uint32
  */
 int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
                       uint32_t meta_len);
+/* The same for the class-indexed table of `mode` (the default table when
+ * that is class-indexed already). */
+int lx_tokenset_class_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
+                            uint32_t meta_len);
 
 /* Release a token set (NULL is a no-op).  Frees its device tables. */
 void lx_tokenset_free(lx_tokenset *ts);

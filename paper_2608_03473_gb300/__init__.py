@@ -46,7 +46,8 @@ LX_FILTERED_MODULO = 2
 
 # every function declared in include/lexgpu.h
 EXPORTED = (
-    "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_scan_table",
+    "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_class_table",
+    "lx_tokenset_scan_table",
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
     "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold",
@@ -100,6 +101,7 @@ def load_library(path: Optional[str] = None):
             "lx_certificates": (i32, [vp, vp, vp]),
             "lx_tokenset_info": (i32, [vp, i32, vp, vp, vp, vp, vp]),
             "lx_tokenset_table": (i32, [vp, i32, vp, u32, vp, u32]),
+            "lx_tokenset_class_table": (i32, [vp, i32, vp, u32, vp, u32]),
             "lx_tokenset_scan_table": (i32, [vp, vp, u32, vp, u32]),
             "lx_tokenset_free": (None, [vp]),
             "lx_ctx_create": (i32, [vp]),
@@ -215,13 +217,15 @@ def lx_tokenset_info(ts: Tokenset, mode: int = LX_FULL_EXACT) -> dict:
             "table_form": tf.value, "table_rows": tr.value}
 
 
-def lx_tokenset_table(ts: Tokenset, mode: int) -> Tuple[int, np.ndarray, dict]:
-    """(status, blob bytes, layout) of the packed walk table for ``mode``."""
+def lx_tokenset_table(ts: Tokenset, mode: int, class_table: bool = False) -> Tuple[int, np.ndarray, dict]:
+    """(status, blob bytes, layout) of the packed walk table for ``mode`` (the
+    class-indexed one with ``class_table``)."""
     lib = load_library()
+    fn = lib.lx_tokenset_class_table if class_table else lib.lx_tokenset_table
     meta = (ctypes.c_uint32 * 11)()
-    rc = lib.lx_tokenset_table(ts.handle, int(mode), None, 0, meta, 11)
+    rc = fn(ts.handle, int(mode), None, 0, meta, 11)
     blob = np.zeros(max(meta[0], 1), dtype=np.uint8)
-    lib.lx_tokenset_table(ts.handle, int(mode), blob.ctypes.data, int(meta[0]), None, 0)
+    fn(ts.handle, int(mode), blob.ctypes.data, int(meta[0]), None, 0)
     keys = ("blob_bytes", "form", "n_rows", "ncols", "row_bytes", "table_bytes", "p_start", "p_flag", "p_slow")
     info = {k: int(meta[i]) for i, k in enumerate(keys)}
     info["kind_off"] = int(meta[9]) & 0xFFFF

@@ -395,11 +395,25 @@ extern "C" int lx_tokenset_info(const lx_tokenset *ts, int mode, uint32_t *n_sta
     return ts->tab[mode].status;
 }
 
+static int table_out(const HostTable &h, void *out, uint32_t cap, uint32_t *meta, uint32_t meta_len);
+
 extern "C" int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
                                  uint32_t meta_len)
 {
     if (!ts || mode < 0 || mode > 2) return LX_E_INVAL;
-    const HostTable &h = ts->tab[mode];
+    return table_out(ts->tab[mode], out, cap, meta, meta_len);
+}
+
+extern "C" int lx_tokenset_class_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
+                                       uint32_t meta_len)
+{
+    if (!ts || mode < 0 || mode > 2) return LX_E_INVAL;
+    const bool own = ts->tab_cls[mode].status == LX_OK && !ts->tab_cls[mode].blob.empty();
+    return table_out(own ? ts->tab_cls[mode] : ts->tab[mode], out, cap, meta, meta_len);
+}
+
+static int table_out(const HostTable &h, void *out, uint32_t cap, uint32_t *meta, uint32_t meta_len)
+{
     if (out && cap) std::memcpy(out, h.blob.data(), std::min<size_t>(cap, h.blob.size()));
     const uint32_t m[12] = {(uint32_t)h.blob.size(), (uint32_t)h.form, h.n_rows, h.ncols, h.row_bytes,
                             h.table_bytes, h.p_start, h.p_flag, h.p_slow, h.kind_off | (h.cmap_off << 16),

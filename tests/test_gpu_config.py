@@ -123,3 +123,26 @@ def test_default_config_prefers_occupancy(gpu):
     assert cls == 1 and 32 <= ks <= 40 and ms == 0
     tc = lg.lx_compile_tokenset(T.tokenset("clike"), T.discarded_kinds("clike"))
     assert lg.lx_ctx_get_config(ctx, tc, 2)[:3] == (40, 0, 1)   # class-indexed anyway
+
+
+def test_wide_class_form_on_gpu(gpu):
+    """More than 128 byte classes, both table forms."""
+    import random
+    import torch
+    from test_walk_table_model import wide_class_dfa
+    lg, _ = gpu
+    ctx = lg.lx_ctx_create()
+    dfa, alpha = wide_class_dfa()
+    ts = lg.lx_compile_tokenset(dfa, [1])
+    rng = random.Random(8)
+    w = np.frombuffer(bytes(rng.choice(alpha) for _ in range(300000)), np.uint8)
+    d = torch.from_numpy(w.copy()).cuda()
+    for mode in (0, 1):
+        k, l, con = oracle.lex(dfa, w)
+        if mode:
+            k, l = oracle.discard(k, l, [1], dfa.n_kinds)
+        for cls in (0, 1):
+            assert lg.lx_ctx_set_config(ctx, ts, mode, 40, 0, cls) == 0
+            rc, kk, ll, c2 = _lex(lg, ctx, ts, d, mode, w.size)
+            assert rc == 0 and c2 == con, (mode, cls)
+            assert np.array_equal(kk.astype(np.int64), k) and np.array_equal(ll.astype(np.int64), l)

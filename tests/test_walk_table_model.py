@@ -23,8 +23,8 @@ NOPOS = None
 
 
 class TableModel:
-    def __init__(self, lg, ts, mode):
-        rc, blob, info = lg.lx_tokenset_table(ts, mode)
+    def __init__(self, lg, ts, mode, class_table=False):
+        rc, blob, info = lg.lx_tokenset_table(ts, mode, class_table)
         assert rc == 0
         self.b = blob
         self.i = info
@@ -117,9 +117,10 @@ def _expected(dfa, w, mode, discarded):
     return list(zip(k.tolist(), l.tolist())), con
 
 
+@pytest.mark.parametrize("class_table", [False, True])
 @pytest.mark.parametrize("name", ["arith", "json", "clike", "clike_row1"])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-def test_table_model_matches_oracle(lexlib, name, mode):
+def test_table_model_matches_oracle(lexlib, name, mode, class_table):
     if mode == 0 and name in ("json", "clike"):
         seg_list = [7]
     else:
@@ -127,7 +128,9 @@ def test_table_model_matches_oracle(lexlib, name, mode):
     dfa = T.tokenset(name)
     I = T.discarded_kinds(name)
     ts = lexlib.lx_compile_tokenset(dfa, I)
-    m = TableModel(lexlib, ts, mode)
+    m = TableModel(lexlib, ts, mode, class_table)
+    if class_table:
+        assert m.i["form"] == 1
     rng = random.Random(hash((name, mode)) & 0xFFFF)
     wl = {"arith": "arith", "json": "json", "clike": "clike", "clike_row1": "clike"}[name]
     base = bytes(corpus.generate(wl, 1 << 15, seed=11))
@@ -144,3 +147,34 @@ def test_table_model_matches_oracle(lexlib, name, mode):
             got = m.lex(w, seg)
             assert got[1] == exp[1], (name, mode, seg, w[:80])
             assert got[0] == exp[0], (name, mode, seg, w[:80])
+
+
+def wide_class_dfa(seed=5, n_states=12, n_bytes=150):
+    """A DFA whose bytes fall into more than 128 classes (each byte maps the
+    states differently) with few states."""
+    from lexinputs.automaton import dfa_from_edges
+    rng = random.Random(seed)
+    alpha = list(range(32, 32 + n_bytes))
+    edges = []
+    for q in range(n_states):
+        for b in alpha:
+            if q == 0 or rng.random() < 0.7:
+                edges.append((q, b, rng.randrange(1, n_states)))
+    acc = {q: rng.randrange(3) for q in range(1, n_states)}
+    return dfa_from_edges(n_states, edges, acc, q0=0, kind_names=["k0", "k1", "k2"]), alpha
+
+
+def test_wide_class_table_model(lexlib):
+    dfa, alpha = wide_class_dfa()
+    assert dfa.n_classes > 128
+    ts = lexlib.lx_compile_tokenset(dfa, [1])
+    rng = random.Random(6)
+    for mode in (0, 1):
+        m = TableModel(lexlib, ts, mode, class_table=True)
+        assert m.i["form"] == 1
+        for _ in range(30):
+            w = bytes(rng.choice(alpha) for _ in range(rng.randint(0, 300)))
+            exp = _expected(dfa, w, mode, [1])
+            for seg in (3, 7, 68):
+                got = m.lex(w, seg)
+                assert got[1] == exp[1] and got[0] == exp[0]
