@@ -896,6 +896,7 @@ __global__ void __launch_bounds__(NT, 3) lex_tiles(Params P)
             if (tid == 0) atomicOr(&P.res->error, ERR_TIMEOUT);
             break;
         }
+        if (tid == 0) *E.spill_used = 0;   // the previous tile's spill blocks are staged (seen after the plan)
         E.tile_base = tile_base;
         E.sm_end = tile_base + staged;
         const uint32_t n_rel = avail < 0x7FFFFFFFull ? (uint32_t)avail : 0x7FFFFFFFu;
@@ -1015,14 +1016,14 @@ __global__ void __launch_bounds__(NT, 3) lex_tiles(Params P)
             // stage it while this tile's output is written
             claim();
         }
-        __syncthreads();
+        const int any_fail = __syncthreads_or(fail != NOPOS);
         const uint64_t my_off = warp_tot[wid] + lane_excl;   // within the tile
-        if (fail != NOPOS) {
-            atomicMin(s_fpos, (unsigned long long)fail);
+        if (any_fail) {   // the first failure of the tile and the kept tokens before it
+            if (fail != NOPOS) atomicMin(s_fpos, (unsigned long long)fail);
+            __syncthreads();
+            if (fail != NOPOS && *s_fpos == fail) *s_fidx = my_off + mycount;
+            __syncthreads();
         }
-        __syncthreads();
-        if (fail != NOPOS && *s_fpos == fail) *s_fidx = my_off + mycount;
-        __syncthreads();
 
         // the previous tile's output: its predecessors have had a whole walk
         // to publish, so its look-back rarely waits
@@ -1088,8 +1089,6 @@ __global__ void __launch_bounds__(NT, 3) lex_tiles(Params P)
             }
         }
         __syncthreads();   // records, stage and spill blocks are free
-        if (tid == 0) *E.spill_used = 0;
-        __syncthreads();
         tile = s_tile[0];
     }
     flush_pending();
