@@ -162,9 +162,13 @@ void lx_ctx_free(lx_ctx *ctx);
  * A wait that runs out makes the call return LX_E_TIMEOUT. */
 int lx_ctx_set_timeout_ms(lx_ctx *ctx, uint32_t ms);
 
-/* Kernel timing: when enabled, lx_lex records a CUDA event pair on its stream
- * around the tile-kernel launch; lx_ctx_last_kernel_ms returns the elapsed
- * time of the most recent launch (milliseconds, host out).  Off by default. */
+/* Kernel timing: when enabled, lx_lex (and the other lexing calls) record a
+ * CUDA event pair on the stream around their kernel launches;
+ * lx_ctx_last_kernel_ms returns the elapsed time of the most recent call's
+ * launches (milliseconds, host out).  Off by default. */
+int lx_ctx_enable_timing(lx_ctx *ctx, int on);
+int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
+
 /*
  * lx_ctx_debug_withhold -- failure-detection test hook.  In later lx_lex
  * calls on this context, the CTA that processes tile `tile` (17 408-byte
@@ -175,8 +179,6 @@ int lx_ctx_set_timeout_ms(lx_ctx *ctx, uint32_t ms);
  * 0xFFFFFFFF turns it off (the default).  No GPU fault is involved.
  */
 int lx_ctx_debug_withhold(lx_ctx *ctx, uint32_t tile);
-int lx_ctx_enable_timing(lx_ctx *ctx, int on);
-int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
 
 /*
  * lx_lex -- lex n bytes at d_in (device) on the context's device.
@@ -197,7 +199,10 @@ int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
  *   consumed   host out: con(w), the offset after the last emitted token;
  *              < n iff the scan halts on malformed input.  The tokens
  *              returned are then exactly those before the failure
- *              (Corollary 1; for modulo cuts, the reading in the design doc).
+ *              (Corollary 1; with modulo cuts the same holds for
+ *              pi_I: every serial token ends at or before con(w), so the
+ *              one-cut argument of Theorem 3 covers every cut below it and
+ *              the chunk holding con(w) halts there).
  *   stream     cudaStream_t.  The call synchronizes this stream once, to
  *              read back the 32-byte result record.
  * Errors: LX_E_INVAL, LX_E_MODE (LX_FULL_EXACT needs exact cuts: modulo
@@ -211,8 +216,12 @@ int lx_lex(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
 /*
  * lx_lex_host -- lx_lex on HOST buffers: copies h_in to the device, lexes it
  * and copies the tokens back into h_kinds / h_lens (host, capacity entries),
- * all on `stream`, using device buffers owned by the context.  Same results
- * and errors as lx_lex.  Host buffers should be pinned for full copy speed.
+ * using device buffers owned by the context.  Same results and errors as
+ * lx_lex.  Inputs of 64 MiB or more with a non-empty cut set are split on the
+ * host into up to 8 pieces at certified bytes (the planner of Section 6) and
+ * piece copies overlap the lexing of other pieces (two context-owned copy
+ * streams; the launches run in order on `stream`).  Host buffers should be
+ * pinned for full copy speed.  Returns after all copies have completed.
  */
 int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_t n, int mode,
                 uint16_t *h_kinds, uint32_t *h_lens, uint64_t capacity, uint64_t *n_tokens,

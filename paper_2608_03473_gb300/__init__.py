@@ -9,6 +9,13 @@ and streams.  The functions keep the C names:
     ctx = lx_ctx_create()
     rc, n_tokens, consumed = lx_lex(ctx, ts, d_in, mode, d_kinds, d_lens)
 
+and the other entry points: ``lx_lex_host`` (host buffers), ``lx_lex_batch``
+(many documents, one graph launch; ``BatchDocs`` prebuilds its arrays),
+``lx_lex_noalloc`` (no allocation), ``lx_lex_enumerative`` and
+``lx_lex_speculative`` (token sets that certify no byte; ``Model`` and
+``train_context_model`` for the entry-context predictor),
+``lx_ctx_set_config`` / ``lx_autotune`` (launch configuration).
+
 ``dfa`` is any object with ``n_states, q0, n_kinds`` and numpy arrays
 ``byte_class[256]``, ``next[n_classes, n_states]`` (-1 = undefined) and
 ``accept[n_states]`` (-1 = not accepting).
