@@ -1468,6 +1468,16 @@ constexpr uint64_t HOST_PIECE = 32ull << 20;
 constexpr uint32_t HOST_PIECES = 8;
 constexpr uint64_t HOST_SLIDE = 4ull << 20;
 
+// A piece's record is written into pinned host memory by a one-warp kernel
+// rather than a device-to-host copy, which would queue on the copy engine
+// behind the previous piece's tokens.
+__global__ void copy_record(const Result *src, Result *dst)
+{
+    if (threadIdx.x < sizeof(Result) / 8)
+        reinterpret_cast<volatile unsigned long long *>(dst)[threadIdx.x] =
+            reinterpret_cast<const volatile unsigned long long *>(src)[threadIdx.x];
+}
+
 static std::vector<uint64_t> host_pieces(const HostTable &h, const uint8_t *in, uint64_t n)
 {
     std::vector<uint64_t> b{0};
@@ -1547,6 +1557,9 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
     uint8_t *scr = static_cast<uint8_t *>(c->scratch);
     Result *res = reinterpret_cast<Result *>(scr);   // one record per piece
     Result *h_res = static_cast<Result *>(c->h_scratch);
+    Result *h_res_dev = nullptr;   // the same pinned records, as the device sees them
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&h_res_dev), c->h_scratch, 0) != cudaSuccess)
+        return LX_E_CUDA;
     uint8_t *d_in_w = static_cast<uint8_t *>(c->d_in);
     rc = cuda_err(cudaMemsetAsync(scr, 0, zero, st));
     if (rc != LX_OK) return rc;
@@ -1585,7 +1598,8 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
         rc = cuda_err(cudaStreamWaitEvent(st, c->ev_in[i], 0));
         if (rc != LX_OK) return rc;
         launch_tiles(h.form, grid[i], L.total, st, P);
-        rc = cuda_err(cudaMemcpyAsync(h_res + i, P.res, sizeof(Result), cudaMemcpyDeviceToHost, st));
+        copy_record<<<1, 32, 0, st>>>(P.res, h_res_dev + i);
+        rc = cuda_err(cudaGetLastError());
         if (rc == LX_OK) rc = cuda_err(cudaEventRecord(c->ev_lex[i], st));
         if (rc != LX_OK) return rc;
     }
