@@ -529,6 +529,32 @@ def main():
             "gpu_launches": (None if refused else args.steps),
             "clocks": clocks,
         }
+        # both certificates of the token set (Definitions 2 and 3)
+        ex_mask, mo_mask = lg.lx_certificates(ts)
+        fmt = lambda m: [f"0x{b:02x}" for b in range(256) if m[b]]
+        line["config"]["certified"] = {"exact": fmt(ex_mask), "modulo": fmt(mo_mask)}
+        if not refused:
+            # the same filtered stream under exact cuts: with no exact-certified
+            # byte the certified path is one chunk, so it runs through the
+            # enumerative path, which needs no certified byte; its output must
+            # equal the modulo-cut output (both are pi_I(tok(w)))
+            x_k = torch.empty_like(d_k)
+            x_l = torch.empty_like(d_l)
+            ex_fn = lg.lx_lex if ex_mask.any() else lg.lx_lex_enumerative
+            x_ms = []
+            for i in range(5):
+                rcx, ntx, conx = ex_fn(ctx, ts, d_in, lg.LX_FILTERED_EXACT, x_k, x_l, stream=stream)
+                if i >= 2:
+                    x_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
+            rc, nt3, con3 = lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
+            same = (rcx == 0 and ntx == nt3 and conx == con3 and torch.equal(x_k[:ntx], d_k[:nt3])
+                    and torch.equal(x_l[:ntx], d_l[:nt3]))
+            line["exact_certificate"] = {
+                "mode": "LX_FILTERED_EXACT",
+                "path": "lx_lex" if ex_mask.any() else "lx_lex_enumerative (no exact-certified byte)",
+                "kernel_ms": statistics.median(x_ms), "value": n / (statistics.median(x_ms) / 1e3) / 1e9,
+                "unit": "GB/s", "same_output_as_modulo": bool(same)}
+            del x_k, x_l
         if refused:
             # the enumerative path on the same input, for comparison
             for _ in range(2):
@@ -544,6 +570,15 @@ def main():
                                    "train_data": "2 x 64 MiB C-like-with-block-comments corpora, other seeds"}
             line["enumerative"] = {"kernel_ms": statistics.median(en_ms),
                                    "value": n / (statistics.median(en_ms) / 1e3) / 1e9, "unit": "GB/s"}
+            # the same speculative path without the model (every chunk guessed BOUNDARY)
+            nm_ms, nm_st = [], {}
+            for i in range(5):
+                _, _, _, nm_st = lg.lx_lex_speculative(ctx, ts, None, d_in, mode, d_k, d_l, stream=stream)
+                if i >= 2:
+                    nm_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
+            line["speculative_no_model"] = {"kernel_ms": statistics.median(nm_ms),
+                                            "value": n / (statistics.median(nm_ms) / 1e3) / 1e9, "unit": "GB/s",
+                                            "rounds": nm_st.get("rounds"), "rescanned": nm_st.get("rescanned")}
             launches = 4 + 2 * (spec_stats.get("rounds") or 1) + (n // 4096 + 16383) // 16384 * 5
             line["gpu_launches"] = launches * args.steps
         print(json.dumps(line), flush=True)

@@ -93,6 +93,7 @@ struct EnParams {
 
 // Shared-memory view of the scan table.
 struct ScanEnv {
+    uint32_t cls_s, next_s;   // shared-window addresses of the class map and next table
     const uint8_t *cls;
     const uint16_t *next, *acc, *cbeg, *cand;
     uint32_t S, q0, keep_all;
@@ -108,6 +109,8 @@ __device__ __forceinline__ ScanEnv stage_scan(const EnParams &P, uint8_t *smem)
     __syncthreads();
     ScanEnv E;
     E.cls = smem;
+    E.cls_s = (uint32_t)__cvta_generic_to_shared(smem);
+    E.next_s = E.cls_s + P.next_off;
     E.next = reinterpret_cast<const uint16_t *>(smem + P.next_off);
     E.acc = reinterpret_cast<const uint16_t *>(smem + P.acc_off);
     E.cbeg = reinterpret_cast<const uint16_t *>(smem + P.cbeg_off);
@@ -120,44 +123,58 @@ __device__ __forceinline__ ScanEnv stage_scan(const EnParams &P, uint8_t *smem)
     return E;
 }
 
-// A thread's view of the input: byte loads through the read-only path (a
-// chunk's consecutive bytes share L1 lines; holding 16-byte blocks in
-// registers measured slower).
+// A lane's view of the input: a 16-byte block of its chunk held in
+// registers, the next block loaded as soon as the lane enters one (its
+// latency hidden behind sixteen steps).  Lanes of a warp read different
+// chunks, so byte loads through L1 would bring a sector per lane and step;
+// a block per lane cuts that sixteenfold.  Unaligned inputs and the last
+// partial block are read byte by byte.
 struct Bytes {
     const uint8_t *in;
-    __device__ __forceinline__ uint32_t operator()(uint64_t p) { return __ldg(in + p); }
+    uint64_t n;
+    bool wide;   // `in` 16-byte aligned
+    uint64_t base = ~0ull, nbase = ~0ull;
+    unsigned long long c0 = 0, c1 = 0, n0 = 0, n1 = 0;
+    __device__ __forceinline__ void load(uint64_t b, unsigned long long &w0, unsigned long long &w1) const
+    {
+        if (wide && b + 16 <= n) {
+            const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(in + b));
+            w0 = v.x;
+            w1 = v.y;
+        } else {
+            w0 = w1 = 0;
+            for (uint32_t k = 0; k < 16 && b + k < n; k++) {
+                const unsigned long long x = (unsigned long long)__ldg(in + b + k);
+                if (k < 8) w0 |= x << (8 * k);
+                else w1 |= x << (8 * (k - 8));
+            }
+        }
+    }
+    __device__ __forceinline__ uint32_t operator()(uint64_t p)
+    {
+        const uint64_t b = p & ~15ull;
+        if (b != base) {
+            if (b == nbase) {
+                c0 = n0;
+                c1 = n1;
+            } else {
+                load(b, c0, c1);
+            }
+            base = b;
+            nbase = b + 16;
+            if (nbase < n) load(nbase, n0, n1);
+        }
+        const unsigned long long w = (p & 8) ? c1 : c0;
+        return (uint32_t)(w >> (8 * (uint32_t)(p & 7))) & 0xFFu;
+    }
 };
 
 __device__ __forceinline__ uint32_t delta(const ScanEnv &E, uint32_t q, uint32_t b)
 {
-    return E.next[(uint32_t)E.cls[b] * E.S + q];
-}
-
-// The DFA run from state q before byte j while transitions are defined: the
-// last accepting end (> j) and its accept word, or NOPOS64.
-__device__ __forceinline__ uint64_t run_last_accept(const ScanEnv &E, Bytes &by, uint32_t q, uint64_t j,
-                                                    uint32_t &acc)
-{
-    uint64_t last = NOPOS64;
-    uint32_t lq = 0;
-    while (j < E.n) {
-        const uint32_t t = delta(E, q, by(j));
-        if (t == SCAN_NONE) break;
-        q = t & ~(uint32_t)SCAN_ACCEPT;
-        j++;
-        if (t & SCAN_ACCEPT) {
-            last = j;
-            lq = q;
-        }
-    }
-    if (last != NOPOS64) acc = E.acc[lq];
-    return last;
-}
-
-__device__ __forceinline__ uint32_t state_after(const ScanEnv &E, Bytes &by, uint32_t q, uint64_t lo, uint64_t hi)
-{
-    for (uint64_t j = lo; j < hi; j++) q = delta(E, q, by(j)) & ~(uint32_t)SCAN_ACCEPT;
-    return q;
+    uint32_t c, t;
+    asm("ld.shared.u8 %0, [%1];" : "=r"(c) : "r"(E.cls_s + b));
+    asm("ld.shared.u16 %0, [%1];" : "=r"(t) : "r"(E.next_s + 2u * (c * E.S + q)));
+    return t;
 }
 
 struct CountTok {
@@ -185,31 +202,63 @@ struct WriteTok {
 // returns CTX_BAD with `fail` set; for an entry from which no accepting
 // position past p0 is reachable (never the true context) returns CTX_BAD
 // with `fail` = NOPOS64.
+//
+// All 32 lanes of a warp call it together (`has` false: no chunk, result
+// unused) and step in lockstep, up to four steps per lane between warp
+// votes, so that their byte loads and table lookups issue together.  Each
+// step is one DFA transition, or the end of a run: the run from `tok` in
+// start state `qs` keeps its last accepting end, and when no transition is
+// defined its token is [tok, last).  The entry run (from `ctx`) ends a token
+// that began before p0 and is not emitted.  The state at p1 of the run that
+// crosses it is kept: when the last token runs past p1, that state is the
+// context at p1.
 template <class Emit>
-__device__ uint16_t chunk_scan(const ScanEnv &E, uint64_t p0, uint64_t p1, uint16_t ctx, Emit &emit,
+__device__ uint16_t chunk_scan(const ScanEnv &E, bool has, uint64_t p0, uint64_t p1, uint16_t ctx, Emit &emit,
                                uint64_t &fail)
 {
     fail = NOPOS64;
-    uint64_t pos = p0;
-    uint32_t acc = 0;
-    Bytes by{E.in};
-    if (ctx != CTX_B) {
-        const uint64_t e = run_last_accept(E, by, ctx, p0, acc);
-        if (e == NOPOS64) return CTX_BAD;
-        if (e >= p1) return e == p1 ? CTX_B : (uint16_t)state_after(E, by, ctx, p0, p1);
-        pos = e;
-    }
-    while (pos < p1) {
-        const uint64_t e = run_last_accept(E, by, E.q0, pos, acc);
-        if (e == NOPOS64) {
-            fail = pos;
-            return CTX_BAD;
+    Bytes by{E.in, E.n, (reinterpret_cast<uintptr_t>(E.in) & 15u) == 0};
+    const bool entered = ctx != CTX_B;
+    uint16_t res = CTX_B;
+    bool run = has && (entered || p0 < p1);
+    uint64_t tok = p0, j = p0, last = NOPOS64;
+    uint32_t qs = entered ? ctx : E.q0, q = qs, lq = 0, qp1 = qs;
+    bool first = entered;
+    while (__any_sync(0xffffffffu, run)) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (!run) break;
+            const uint32_t t = j < E.n ? delta(E, q, by(j)) : (uint32_t)SCAN_NONE;
+            if (t != SCAN_NONE) {
+                q = t & ~(uint32_t)SCAN_ACCEPT;
+                j++;
+                if (j == p1) qp1 = q;
+                if (t & SCAN_ACCEPT) {
+                    last = j;
+                    lq = q;
+                }
+            } else if (last == NOPOS64) {   // no accepting end: a failure, or an impossible entry
+                if (!first) fail = tok;
+                res = CTX_BAD;
+                run = false;
+            } else {
+                if (!first) {
+                    const uint32_t acc = E.acc[lq];
+                    if (E.keep_all || (acc & KIND_KEEP)) emit(acc & 0x7FFFu, last - tok);
+                }
+                if (last >= p1) {
+                    if (last > p1) res = (uint16_t)qp1;
+                    run = false;
+                } else {
+                    tok = j = last;
+                    q = qs = E.q0;
+                    last = NOPOS64;
+                    first = false;
+                }
+            }
         }
-        if (E.keep_all || (acc & KIND_KEEP)) emit(acc & 0x7FFFu, e - pos);
-        if (e >= p1) return e == p1 ? CTX_B : (uint16_t)state_after(E, by, E.q0, pos, p1);
-        pos = e;
     }
-    return CTX_B;
+    return res;
 }
 
 __device__ __forceinline__ uint32_t n_cand(const ScanEnv &E, uint32_t b)
@@ -285,22 +334,32 @@ __global__ void __launch_bounds__(EN_NT) en_enumerate(EnParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const ScanEnv E = stage_scan(P, smem);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
-        const uint64_t p0 = P.start[j];
-        if (p0 == NOPOS64) continue;
-        uint32_t jn;
-        const uint64_t p1 = next_start(P, j, &jn);
-        const uint32_t b = P.cinfo[j] >> 8, K = P.cinfo[j] & 0xFFu;
-        for (uint32_t k = 0; k < K; k++) {
+    // block-uniform loop: the lanes of a warp scan their chunks together
+    for (uint32_t j0 = blockIdx.x * blockDim.x; j0 < P.M; j0 += gridDim.x * blockDim.x) {
+        const uint32_t j = j0 + threadIdx.x;
+        const uint64_t p0 = j < P.M ? P.start[j] : NOPOS64;
+        uint64_t p1 = 0;
+        uint32_t b = 0, K = 0;
+        if (p0 != NOPOS64) {
+            uint32_t jn;
+            p1 = next_start(P, j, &jn);
+            b = P.cinfo[j] >> 8;
+            K = P.cinfo[j] & 0xFFu;
+        }
+        const uint32_t Kw = __reduce_max_sync(0xffffffffu, K);
+        for (uint32_t k = 0; k < Kw; k++) {
+            const bool has = k < K;
             CountTok ct;
             uint64_t fail;
-            const uint16_t x = chunk_scan(E, p0, p1, cand_ctx(E, b, k), ct, fail);
-            ChunkRes r;
-            r.fail = fail;
-            r.count = ct.count;
-            r.exit = x;
-            r.pad = 0;
-            P.res[(size_t)j * KMAX + k] = r;
+            const uint16_t x = chunk_scan(E, has, p0, p1, has ? cand_ctx(E, b, k) : CTX_B, ct, fail);
+            if (has) {
+                ChunkRes r;
+                r.fail = fail;
+                r.count = ct.count;
+                r.exit = x;
+                r.pad = 0;
+                P.res[(size_t)j * KMAX + k] = r;
+            }
         }
     }
 }
@@ -428,14 +487,19 @@ __global__ void __launch_bounds__(EN_NT) en_emit(EnParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const ScanEnv E = stage_scan(P, smem);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
-        const ChunkOut o = P.out[j];
-        if (!o.live) continue;
-        uint32_t jn;
-        const uint64_t p1 = next_start(P, j, &jn);
+    for (uint32_t j0 = blockIdx.x * blockDim.x; j0 < P.M; j0 += gridDim.x * blockDim.x) {
+        const uint32_t j = j0 + threadIdx.x;
+        ChunkOut o{0, CTX_B, 0, 0};
+        if (j < P.M) o = P.out[j];
+        uint64_t p0 = 0, p1 = 0;
+        if (o.live) {
+            uint32_t jn;
+            p0 = P.start[j];
+            p1 = next_start(P, j, &jn);
+        }
         WriteTok wt{P.kinds, P.lens, P.cap, o.off};
         uint64_t fail;
-        chunk_scan(E, P.start[j], p1, o.entry, wt, fail);
+        chunk_scan(E, o.live != 0, p0, p1, o.entry, wt, fail);
     }
 }
 
@@ -467,21 +531,32 @@ __global__ void __launch_bounds__(EN_NT) sp_scan(EnParams P, uint32_t round)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const ScanEnv E = stage_scan(P, smem);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
-        if (!P.dirty[j]) continue;
-        uint32_t jn;
-        const uint64_t p1 = next_start(P, j, &jn);
+    for (uint32_t j0 = blockIdx.x * blockDim.x; j0 < P.M; j0 += gridDim.x * blockDim.x) {
+        const uint32_t j = j0 + threadIdx.x;
+        const bool has = j < P.M && P.dirty[j];
+        // a warp with no dirty chunk skips the scan as a whole
+        if (!__any_sync(0xffffffffu, has)) continue;
+        uint64_t p0 = 0, p1 = 0;
+        uint16_t c = CTX_B;
+        if (has) {
+            uint32_t jn;
+            p0 = P.start[j];
+            p1 = next_start(P, j, &jn);
+            c = P.ctx[j];
+        }
         CountTok ct;
         uint64_t fail;
-        const uint16_t x = chunk_scan(E, P.start[j], p1, P.ctx[j], ct, fail);
-        ChunkRes r;
-        r.fail = fail;
-        r.count = ct.count;
-        r.exit = x;
-        r.pad = 0;
-        P.res[(size_t)j * KMAX] = r;
-        P.dirty[j] = 0;
-        if (round > 0) atomicAdd(P.rescans, 1u);
+        const uint16_t x = chunk_scan(E, has, p0, p1, c, ct, fail);
+        if (has) {
+            ChunkRes r;
+            r.fail = fail;
+            r.count = ct.count;
+            r.exit = x;
+            r.pad = 0;
+            P.res[(size_t)j * KMAX] = r;
+            P.dirty[j] = 0;
+            if (round > 0) atomicAdd(P.rescans, 1u);
+        }
     }
 }
 

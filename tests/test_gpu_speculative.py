@@ -134,6 +134,19 @@ def test_speculative_exact(env, trained, which, mode):
         assert st["rescanned"] < 0.2 * st["chunks"], st
 
 
+def test_trained_model_gains(env, trained):
+    # what the network buys: fewer chunks scanned twice than with BOUNDARY
+    # guesses (no model) or an untrained network, same exact output
+    lg, ctx, ts, S = env
+    w = corpus.generate(NAME, 8 << 20, seed=57)
+    st_none = _check(lg, ctx, ts, None, w, 0)
+    st_rand = _check(lg, ctx, ts, lg.Model(S + 1, hidden=16, seed=10), w, 0)
+    st_tr = _check(lg, ctx, ts, trained, w, 0)
+    assert st_tr["rescanned"] * 3 < st_none["rescanned"], (st_tr, st_none)
+    assert st_tr["rescanned"] * 3 < st_rand["rescanned"], (st_tr, st_rand)
+    assert st_tr["rounds"] <= st_none["rounds"]
+
+
 def test_speculative_malformed_and_ragged(env, trained):
     lg, ctx, ts, S = env
     base = corpus.generate(NAME, 64 * 4096, seed=55)
