@@ -102,6 +102,77 @@ __global__ void k_gemm(const float *A, const TW *Bm, float *Cm, const TW *bias, 
     }
 }
 
+// Inference products: C[M x N] = A[M x K] B[K x N] + bias (ReLU optional),
+// each CTA a 64 x 64 tile of C, each thread a 4 x 4 block of it in
+// registers, K in steps of 16 through shared memory.  With GATHER the rows
+// of A are not stored: A[m, k] = emb[window m's byte k / D, k % D].
+constexpr int RB_T = 64, RB_K = 16;
+
+template <class TW, bool GATHER>
+__global__ void __launch_bounds__(256) k_gemm_rb(const float *A, const uint16_t *win, const TW *emb, const TW *Bm,
+                                                 float *Cm, const TW *bias, uint32_t M, uint32_t N, uint32_t K,
+                                                 int relu_out)
+{
+    __shared__ __align__(16) float As[RB_K][RB_T + 4];   // A tile, k-major
+    __shared__ __align__(16) float Bs[RB_K][RB_T + 4];
+    const uint32_t tid = threadIdx.x, tx = tid & 15u, ty = tid >> 4;
+    const uint32_t m0 = blockIdx.y * RB_T, n0 = blockIdx.x * RB_T;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+    for (uint32_t k0 = 0; k0 < K; k0 += RB_K) {
+        {
+            const uint32_t r = tid >> 2, kk = (tid & 3u) * 4u, m = m0 + r;
+#pragma unroll
+            for (uint32_t i = 0; i < 4; i++) {
+                const uint32_t k = k0 + kk + i;
+                float v = 0.0f;
+                if (m < M && k < K) {
+                    if (GATHER) v = to_f(emb[(size_t)win[(size_t)m * MW + k / MD] * MD + k % MD]);
+                    else v = A[(size_t)m * K + k];
+                }
+                As[kk + i][r] = v;
+            }
+        }
+        {
+            const uint32_t kr = tid >> 4, c = (tid & 15u) * 4u, k = k0 + kr;
+#pragma unroll
+            for (uint32_t i = 0; i < 4; i++) {
+                const uint32_t nn = n0 + c + i;
+                Bs[kr][c + i] = (k < K && nn < N) ? to_f(Bm[(size_t)k * N + nn]) : 0.0f;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < RB_K; k++) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint32_t m = m0 + ty * 4 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t nn = n0 + tx * 4 + j;
+            if (nn >= N) continue;
+            float v = acc[i][j];
+            if (bias) v += to_f(bias[nn]);
+            if (relu_out) v = v > 0.0f ? v : 0.0f;
+            Cm[(size_t)m * N + nn] = v;
+        }
+    }
+}
+
 // softmax cross-entropy per row: dz = (softmax(z) - onehot(y)) / B, loss sum
 __global__ void k_softmax_ce(const float *z, const uint16_t *y, uint32_t B, uint32_t C, float *dz, float *loss)
 {
@@ -242,6 +313,7 @@ int ensure_act(lx_model *m, uint32_t B)
 }
 
 dim3 gemm_grid(uint32_t M, uint32_t N) { return dim3((N + GT - 1) / GT, (M + GT - 1) / GT); }
+dim3 rb_grid(uint32_t M, uint32_t N) { return dim3((N + RB_T - 1) / RB_T, (M + RB_T - 1) / RB_T); }
 
 // Forward (and with labels, backward into m->g) for a batch of windows.
 // Activations: h0 | a1 | h1 | z | dz | dh1 | dh0 | loss
@@ -309,13 +381,14 @@ int lx::model_predict(lx_model *m, const uint8_t *in, uint64_t n, const uint64_t
     const uint32_t H = m->H, C = m->C;
     float *h0 = m->act, *h1 = h0 + (size_t)B * MIN_, *z = h1 + (size_t)B * H;
     const __nv_bfloat16 *w = m->w16;
-    const dim3 t2(GT, GT);
     for (uint32_t j0 = 0; j0 < M; j0 += B) {
         const uint32_t cnt = std::min<uint32_t>(B, M - j0);
         k_windows<<<(cnt * MW + 255) / 256, 256, 0, s>>>(in, n, start, j0, cnt, m->win);
-        k_gather<__nv_bfloat16><<<(cnt * MIN_ + 255) / 256, 256, 0, s>>>(m->win, cnt, w + m->o_emb, h0);
-        k_gemm<__nv_bfloat16><<<gemm_grid(cnt, H), t2, 0, s>>>(h0, w + m->o_w1, h1, w + m->o_b1, cnt, H, MIN_, 0, 0, 1);
-        k_gemm<__nv_bfloat16><<<gemm_grid(cnt, C), t2, 0, s>>>(h1, w + m->o_w2, z, w + m->o_b2, cnt, C, H, 0, 0, 0);
+        // h1 = relu(gather(emb, windows) W1 + b1), z = h1 W2 + b2
+        k_gemm_rb<__nv_bfloat16, true><<<rb_grid(cnt, H), 256, 0, s>>>(nullptr, m->win, w + m->o_emb, w + m->o_w1,
+                                                                      h1, w + m->o_b1, cnt, H, MIN_, 1);
+        k_gemm_rb<__nv_bfloat16, false><<<rb_grid(cnt, C), 256, 0, s>>>(h1, nullptr, nullptr, w + m->o_w2, z,
+                                                                       w + m->o_b2, cnt, C, H, 0);
         k_argmax<<<(cnt * 32 + 255) / 256, 256, 0, s>>>(z, C, j0, cnt, start, cinfo, scan_blob, cbeg_off, cand_off,
                                                         guess);
     }
