@@ -332,7 +332,9 @@ int lx_model_train_step(lx_model *m, const uint16_t *d_windows, const uint16_t *
  * lx_lex_enumerative; LX_E_INVAL when the model does not score states + 1
  * contexts of this token set.  stats (optional): chunk targets, rounds (scans
  * of the dirty chunks, the first included), chunks scanned again after the
- * first round.
+ * first round.  Each scan also stages the chunk's kept tokens in context
+ * scratch (6 bytes of device memory per input byte), so that the settled
+ * chunks are copied to the output rather than scanned again.
  */
 typedef struct {
     uint64_t chunks;

@@ -89,6 +89,8 @@ struct EnParams {
     unsigned int *changed;       // a fix-up round changed some ctx
     unsigned int *rescans;       // chunks scanned again after the first round
     const uint16_t *guess;       // [M] predicted entry contexts (nullptr: BOUNDARY)
+    uint16_t *st_kinds;          // [n] a chunk's kept tokens from its latest scan, at its start offset
+    uint32_t *st_lens;           // [n]
 };
 
 // Shared-memory view of the scan table.
@@ -180,6 +182,22 @@ __device__ __forceinline__ uint32_t delta(const ScanEnv &E, uint32_t q, uint32_t
 struct CountTok {
     uint32_t count = 0;
     __device__ __forceinline__ void operator()(uint32_t, uint64_t) { count++; }
+};
+
+// The kept tokens of a chunk starting at p0 go to st[p0 + i]: tokens start
+// at distinct offsets in [p0, p1), so a chunk's run of entries ends before
+// the next chunk's begins.
+struct StageTok {
+    uint16_t *kinds;
+    uint32_t *lens;
+    uint64_t base;
+    uint32_t count = 0;
+    __device__ __forceinline__ void operator()(uint32_t kind, uint64_t len)
+    {
+        kinds[base + count] = (uint16_t)kind;
+        lens[base + count] = (uint32_t)len;
+        count++;
+    }
 };
 
 struct WriteTok {
@@ -544,7 +562,7 @@ __global__ void __launch_bounds__(EN_NT) sp_scan(EnParams P, uint32_t round)
             p1 = next_start(P, j, &jn);
             c = P.ctx[j];
         }
-        CountTok ct;
+        StageTok ct{P.st_kinds, P.st_lens, p0};
         uint64_t fail;
         const uint16_t x = chunk_scan(E, has, p0, p1, c, ct, fail);
         if (has) {
@@ -588,6 +606,27 @@ __global__ void __launch_bounds__(EN_NT) ctx_export(EnParams P, uint64_t *starts
 // Output offsets along the settled chain (one CTA): each thread sums its run
 // of chunks, thread 0 links the runs and finds the first failure, each
 // thread labels its run.
+// The settled chunks' staged tokens to their output offsets, one warp per
+// chunk, coalesced: the last scan of every chunk ran from its true entry
+// context, so no chunk is walked again to emit.
+__global__ void __launch_bounds__(EN_NT) sp_copy(EnParams P)
+{
+    const uint32_t lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x / 32u);
+    for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) / 32u; j < P.M; j += nw) {
+        const ChunkOut o = P.out[j];
+        if (!o.live) continue;
+        const uint64_t base = P.start[j];
+        const uint32_t cnt = P.res[(size_t)j * KMAX].count;
+        for (uint32_t i = lane; i < cnt; i += 32u) {
+            const uint64_t idx = o.off + i;
+            if (idx < P.cap) {
+                P.kinds[idx] = P.st_kinds[base + i];
+                P.lens[idx] = P.st_lens[base + i];
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(RS_NT) sp_offsets(EnParams P)
 {
     __shared__ unsigned long long run_sum[RS_NT];
@@ -661,7 +700,7 @@ struct EnRun {
 
 // Validate, upload tables, size the scratch and fill the parameters.
 int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
-             uint32_t *d_lens, uint64_t capacity, void *stream, EnRun &R)
+             uint32_t *d_lens, uint64_t capacity, void *stream, EnRun &R, bool stage = false)
 {
     if (!c || !ts) return LX_E_INVAL;
     if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
@@ -684,7 +723,8 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     const size_t o_res = al(o_cinfo + 4 * (size_t)M), o_out = al(o_res + sizeof(ChunkRes) * KMAX * (size_t)M);
     const size_t o_ctx = al(o_out + sizeof(ChunkOut) * (size_t)M), o_prev = al(o_ctx + 2 * (size_t)M);
     const size_t o_dirty = al(o_prev + 4 * (size_t)M), o_guess = al(o_dirty + (size_t)M);
-    const size_t total = al(o_guess + 2 * (size_t)M);
+    const size_t o_stk = al(o_guess + 2 * (size_t)M), o_stl = al(o_stk + (stage ? 2 * (size_t)n : 0));
+    const size_t total = al(o_stl + (stage ? 4 * (size_t)n : 0));
     rc = grow(&c->e_dev, &c->e_dev_bytes, total);
     if (rc != LX_OK) return rc;
     uint8_t *d = static_cast<uint8_t *>(c->e_dev);
@@ -716,6 +756,8 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     P.changed = reinterpret_cast<unsigned int *>(d + o_flags);
     P.rescans = reinterpret_cast<unsigned int *>(d + o_flags + 4);
     P.guess = nullptr;
+    P.st_kinds = stage ? reinterpret_cast<uint16_t *>(d + o_stk) : nullptr;
+    P.st_lens = stage ? reinterpret_cast<uint32_t *>(d + o_stl) : nullptr;
     R.guess_buf = reinterpret_cast<uint16_t *>(d + o_guess);
 
     R.smem = P.blob_bytes;
@@ -807,7 +849,7 @@ extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *mo
     *consumed = 0;
     if (stats) *stats = lx_spec_stats{0, 0, 0, 0};
     EnRun R;
-    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R);
+    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R, true);
     if (rc != LX_OK || n == 0) return rc;
     if (model && model_contexts(model) != ts->scan.S + 1) return LX_E_INVAL;
     if (c->timing) cudaEventRecord(c->ev[0], R.s);
@@ -833,7 +875,7 @@ extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *mo
         if (rounds > R.P.M + 1) return LX_E_CUDA;   // cannot happen: every round settles one more chunk
     }
     sp_offsets<<<1, RS_NT, 0, R.s>>>(R.P);
-    en_emit<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    sp_copy<<<R.grid * (EN_NT / 32), EN_NT, 0, R.s>>>(R.P);
     if (c->timing) cudaEventRecord(c->ev[1], R.s);
     unsigned int rescans = 0;
     rc = en_finish(c, R, capacity, n_tokens, consumed, &rescans);
