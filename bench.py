@@ -579,9 +579,9 @@ def main():
             line["speculative_no_model"] = {"kernel_ms": statistics.median(nm_ms),
                                             "value": n / (statistics.median(nm_ms) / 1e3) / 1e9, "unit": "GB/s",
                                             "rounds": nm_st.get("rounds"), "rescanned": nm_st.get("rescanned")}
-            # en_plan, sp_init, sp_offsets, en_emit; sp_scan + sp_fix per round; per batch of 16 384
-            # windows: k_windows, two k_gemm_rb, k_argmax
-            launches = 4 + 2 * (spec_stats.get("rounds") or 1) + (n // 4096 + 16383) // 16384 * 4
+            # en_plan, sp_init, so_block, so_top, so_out, sp_copy; sp_scan + sp_fix per round; per
+            # batch of 16 384 windows: k_windows, two k_gemm_rb, k_argmax
+            launches = 6 + 2 * (spec_stats.get("rounds") or 1) + (n // 4096 + 16383) // 16384 * 4
             line["gpu_launches"] = launches * args.steps
         print(json.dumps(line), flush=True)
     if world > 1:

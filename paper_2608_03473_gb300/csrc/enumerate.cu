@@ -41,6 +41,7 @@ constexpr uint32_t WIN = 256;          // a chunk start is searched in the targe
 constexpr uint32_t KMAX = 8;           // candidate contexts per chunk start (BOUNDARY included)
 constexpr int EN_NT = 256;             // threads of the plan / enumerate / emit kernels
 constexpr int RS_NT = 1024;            // threads of the resolve kernel
+constexpr int SO_NT = 1024;            // threads of the offset kernels (one chunk each)
 constexpr uint64_t NOPOS64 = ~0ull;
 constexpr uint32_t NONE32_EN = 0xFFFFFFFFu;
 constexpr uint16_t CTX_B = 0xFFFEu;    // context: at a token boundary
@@ -91,6 +92,9 @@ struct EnParams {
     const uint16_t *guess;       // [M] predicted entry contexts (nullptr: BOUNDARY)
     uint16_t *st_kinds;          // [n] a chunk's kept tokens from its latest scan, at its start offset
     uint32_t *st_lens;           // [n]
+    unsigned long long *blk_sum; // [ceil(M / SO_NT)] kept tokens of each block of chunks, to its first failure
+    unsigned long long *blk_off; // [ceil(M / SO_NT)] output offset of each block (~0: after the failure)
+    uint32_t *blk_fail;          // [ceil(M / SO_NT)] first failing chunk of each block (NONE32_EN: none)
 };
 
 // Shared-memory view of the scan table.
@@ -627,57 +631,127 @@ __global__ void __launch_bounds__(EN_NT) sp_copy(EnParams P)
     }
 }
 
-__global__ void __launch_bounds__(RS_NT) sp_offsets(EnParams P)
+// Output offsets along the settled chain: the kept-token counts of the chunks
+// in order, up to and including the first failing chunk (Corollary 1: the
+// chunks after it emit nothing).  Three launches, one chunk per thread: the
+// blocks' sums (so_block), the blocks' offsets (so_top, one CTA), each
+// chunk's offset (so_out).
+
+// Inclusive block-wide scan of v over SO_NT threads; `total` = the block's sum.
+__device__ __forceinline__ unsigned long long so_scan(unsigned long long v, unsigned long long *sh,
+                                                      unsigned long long &total)
 {
-    __shared__ unsigned long long run_sum[RS_NT];
-    __shared__ uint32_t run_fail[RS_NT];   // first failing chunk of the run
-    const uint32_t t = threadIdx.x;
-    const uint32_t per = (P.M + RS_NT - 1) / RS_NT;
-    const uint32_t j0 = min(P.M, t * per), j1 = min(P.M, j0 + per);
-    unsigned long long sum = 0;
-    uint32_t f = NONE32_EN;
-    for (uint32_t j = j0; j < j1; j++) {
-        if (P.start[j] == NOPOS64) continue;
-        const ChunkRes r = P.res[(size_t)j * KMAX];
-        sum += r.count;
-        if (r.fail != NOPOS64) {
-            f = j;
-            break;
-        }
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (uint32_t)o) v += y;
     }
-    run_sum[t] = sum;
-    run_fail[t] = f;
+    if (lane == 31) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long x = sh[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        sh[lane] = x;
+    }
+    __syncthreads();
+    if (w > 0) v += sh[w - 1];
+    total = sh[31];
+    __syncthreads();
+    return v;
+}
+
+// A chunk's kept-token count and whether it fails (0, false for no chunk).
+__device__ __forceinline__ unsigned long long so_count(const EnParams &P, uint32_t j, bool &fails)
+{
+    fails = false;
+    if (j >= P.M || P.start[j] == NOPOS64) return 0;
+    const ChunkRes r = P.res[(size_t)j * KMAX];
+    fails = r.fail != NOPOS64;
+    return r.count;
+}
+
+__global__ void __launch_bounds__(SO_NT) so_block(EnParams P)
+{
+    __shared__ unsigned long long sh[32];
+    __shared__ uint32_t s_first;
+    __shared__ unsigned long long s_at;
+    const uint32_t t = threadIdx.x, j = blockIdx.x * SO_NT + t;
+    if (t == 0) s_first = NONE32_EN;
+    __syncthreads();
+    bool fails;
+    const unsigned long long v = so_count(P, j, fails);
+    if (fails) atomicMin(&s_first, t);
+    unsigned long long total;
+    const unsigned long long incl = so_scan(v, sh, total);
+    const uint32_t f = s_first;
+    if (t == f) s_at = incl;
     __syncthreads();
     if (t == 0) {
-        unsigned long long acc = 0;
-        uint32_t r = 0;
-        bool failed = false;
-        for (; r < RS_NT; r++) {
-            const unsigned long long s = run_sum[r];
-            run_sum[r] = acc;   // exclusive prefix
-            acc += s;
-            if (run_fail[r] != NONE32_EN) {
-                P.rec->fail = P.res[(size_t)run_fail[r] * KMAX].fail;
-                failed = true;
-                r++;
-                break;
+        P.blk_sum[blockIdx.x] = f == NONE32_EN ? total : s_at;
+        P.blk_fail[blockIdx.x] = f == NONE32_EN ? NONE32_EN : blockIdx.x * SO_NT + f;
+    }
+}
+
+__global__ void __launch_bounds__(SO_NT) so_top(EnParams P, uint32_t nb)
+{
+    __shared__ unsigned long long sh[32];
+    __shared__ uint32_t s_first;
+    __shared__ unsigned long long s_at;
+    const uint32_t t = threadIdx.x;
+    unsigned long long carry = 0;
+    bool dead = false;
+    uint32_t fail_chunk = NONE32_EN;
+    for (uint32_t b0 = 0; b0 < nb; b0 += SO_NT) {
+        const uint32_t i = b0 + t;
+        if (t == 0) s_first = NONE32_EN;
+        __syncthreads();
+        const unsigned long long v = i < nb ? P.blk_sum[i] : 0ull;
+        if (i < nb && P.blk_fail[i] != NONE32_EN) atomicMin(&s_first, t);
+        unsigned long long total;
+        const unsigned long long incl = so_scan(v, sh, total);
+        const uint32_t f = s_first;
+        if (i < nb) P.blk_off[i] = (dead || t > f) ? ~0ull : carry + incl - v;
+        if (t == f) s_at = incl;
+        __syncthreads();
+        if (!dead) {
+            if (f != NONE32_EN) {
+                carry += s_at;
+                fail_chunk = P.blk_fail[b0 + f];
+                dead = true;
+            } else {
+                carry += total;
             }
         }
-        for (; r < RS_NT; r++) run_sum[r] = ~0ull;   // after the failure
-        P.rec->total = acc;
-        if (!failed) P.rec->fail = NOPOS64;
+        __syncthreads();
     }
+    if (t == 0) {
+        P.rec->total = carry;
+        P.rec->fail = fail_chunk == NONE32_EN ? NOPOS64 : P.res[(size_t)fail_chunk * KMAX].fail;
+    }
+}
+
+__global__ void __launch_bounds__(SO_NT) so_out(EnParams P)
+{
+    __shared__ unsigned long long sh[32];
+    __shared__ uint32_t s_first;
+    const uint32_t t = threadIdx.x, j = blockIdx.x * SO_NT + t;
+    if (t == 0) s_first = NONE32_EN;
     __syncthreads();
-    unsigned long long off = run_sum[t];
-    for (uint32_t j = j0; j < j1; j++) {
+    bool fails;
+    const unsigned long long v = so_count(P, j, fails);
+    if (fails) atomicMin(&s_first, t);
+    unsigned long long total;
+    const unsigned long long incl = so_scan(v, sh, total);
+    const unsigned long long boff = P.blk_off[blockIdx.x];
+    if (j < P.M) {
         ChunkOut o{0, CTX_BAD, 0, 0};
-        if (P.start[j] != NOPOS64 && off != ~0ull) {
-            const ChunkRes r = P.res[(size_t)j * KMAX];
-            o.off = off;
+        if (P.start[j] != NOPOS64 && boff != ~0ull && t <= s_first) {
+            o.off = boff + incl - v;
             o.entry = P.ctx[j];
             o.live = 1;
-            off += r.count;
-            if (r.fail != NOPOS64) off = ~0ull;   // nothing after the failure
         }
         P.out[j] = o;
     }
@@ -724,7 +798,10 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     const size_t o_ctx = al(o_out + sizeof(ChunkOut) * (size_t)M), o_prev = al(o_ctx + 2 * (size_t)M);
     const size_t o_dirty = al(o_prev + 4 * (size_t)M), o_guess = al(o_dirty + (size_t)M);
     const size_t o_stk = al(o_guess + 2 * (size_t)M), o_stl = al(o_stk + (stage ? 2 * (size_t)n : 0));
-    const size_t total = al(o_stl + (stage ? 4 * (size_t)n : 0));
+    const size_t nb = (M + SO_NT - 1) / SO_NT;
+    const size_t o_bsum = al(o_stl + (stage ? 4 * (size_t)n : 0)), o_boff = al(o_bsum + 8 * nb);
+    const size_t o_bfail = al(o_boff + 8 * nb);
+    const size_t total = al(o_bfail + 4 * nb);
     rc = grow(&c->e_dev, &c->e_dev_bytes, total);
     if (rc != LX_OK) return rc;
     uint8_t *d = static_cast<uint8_t *>(c->e_dev);
@@ -758,6 +835,9 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     P.guess = nullptr;
     P.st_kinds = stage ? reinterpret_cast<uint16_t *>(d + o_stk) : nullptr;
     P.st_lens = stage ? reinterpret_cast<uint32_t *>(d + o_stl) : nullptr;
+    P.blk_sum = reinterpret_cast<unsigned long long *>(d + o_bsum);
+    P.blk_off = reinterpret_cast<unsigned long long *>(d + o_boff);
+    P.blk_fail = reinterpret_cast<uint32_t *>(d + o_bfail);
     R.guess_buf = reinterpret_cast<uint16_t *>(d + o_guess);
 
     R.smem = P.blob_bytes;
@@ -874,7 +954,10 @@ extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *mo
         if (*h_flag == 0) break;
         if (rounds > R.P.M + 1) return LX_E_CUDA;   // cannot happen: every round settles one more chunk
     }
-    sp_offsets<<<1, RS_NT, 0, R.s>>>(R.P);
+    const uint32_t nb = (R.P.M + SO_NT - 1) / SO_NT;
+    so_block<<<nb, SO_NT, 0, R.s>>>(R.P);
+    so_top<<<1, SO_NT, 0, R.s>>>(R.P, nb);
+    so_out<<<nb, SO_NT, 0, R.s>>>(R.P);
     sp_copy<<<R.grid * (EN_NT / 32), EN_NT, 0, R.s>>>(R.P);
     if (c->timing) cudaEventRecord(c->ev[1], R.s);
     unsigned int rescans = 0;
