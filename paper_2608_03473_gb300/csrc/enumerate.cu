@@ -356,32 +356,33 @@ __global__ void __launch_bounds__(EN_NT) en_enumerate(EnParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const ScanEnv E = stage_scan(P, smem);
-    // block-uniform loop: the lanes of a warp scan their chunks together
-    for (uint32_t j0 = blockIdx.x * blockDim.x; j0 < P.M; j0 += gridDim.x * blockDim.x) {
-        const uint32_t j = j0 + threadIdx.x;
-        const uint64_t p0 = j < P.M ? P.start[j] : NOPOS64;
+    // one lane per (candidate k, chunk j), candidate-major so that a warp
+    // holds one candidate of 32 consecutive chunks and warps past every
+    // chunk's candidate count skip; block-uniform loop
+    const uint64_t total = (uint64_t)KMAX * P.M;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total; i0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = i0 + threadIdx.x;
+        const uint32_t k = (uint32_t)(i / P.M), j = (uint32_t)(i % P.M);
+        const uint64_t p0 = i < total ? P.start[j] : NOPOS64;
+        const bool has = p0 != NOPOS64 && k < (P.cinfo[j] & 0xFFu);
+        if (!__any_sync(0xffffffffu, has)) continue;
         uint64_t p1 = 0;
-        uint32_t b = 0, K = 0;
-        if (p0 != NOPOS64) {
+        uint16_t c = CTX_B;
+        if (has) {
             uint32_t jn;
             p1 = next_start(P, j, &jn);
-            b = P.cinfo[j] >> 8;
-            K = P.cinfo[j] & 0xFFu;
+            c = cand_ctx(E, P.cinfo[j] >> 8, k);
         }
-        const uint32_t Kw = __reduce_max_sync(0xffffffffu, K);
-        for (uint32_t k = 0; k < Kw; k++) {
-            const bool has = k < K;
-            CountTok ct;
-            uint64_t fail;
-            const uint16_t x = chunk_scan(E, has, p0, p1, has ? cand_ctx(E, b, k) : CTX_B, ct, fail);
-            if (has) {
-                ChunkRes r;
-                r.fail = fail;
-                r.count = ct.count;
-                r.exit = x;
-                r.pad = 0;
-                P.res[(size_t)j * KMAX + k] = r;
-            }
+        CountTok ct;
+        uint64_t fail;
+        const uint16_t x = chunk_scan(E, has, p0, p1, c, ct, fail);
+        if (has) {
+            ChunkRes r;
+            r.fail = fail;
+            r.count = ct.count;
+            r.exit = x;
+            r.pad = 0;
+            P.res[(size_t)j * KMAX + k] = r;
         }
     }
 }
@@ -767,7 +768,7 @@ namespace {
 // Everything a run over one input needs: parameters, launch shapes, stream.
 struct EnRun {
     EnParams P;
-    uint32_t grid = 0, smem = 0, rs_smem = 0;
+    uint32_t grid = 0, egrid = 0, smem = 0, rs_smem = 0;
     cudaStream_t s = nullptr;
     uint16_t *guess_buf = nullptr;   // [M] scratch for predicted contexts
 };
@@ -856,6 +857,7 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     }
     if (R.rs_smem > 220u * 1024u) return LX_E_TOOBIG;
     R.grid = (uint32_t)std::min<uint64_t>((M + EN_NT - 1) / EN_NT, 4ull * c->num_sms);
+    R.egrid = (uint32_t)std::min<uint64_t>(((uint64_t)KMAX * M + EN_NT - 1) / EN_NT, 8ull * c->num_sms);
     R.s = static_cast<cudaStream_t>(stream);
     return cuda_err(cudaMemsetAsync(d, 0, 256, R.s));
 }
@@ -894,7 +896,7 @@ extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_
     if (rc != LX_OK || n == 0) return rc;
     if (c->timing) cudaEventRecord(c->ev[0], R.s);
     en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
-    en_enumerate<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
     en_resolve<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
     en_emit<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
     if (c->timing) cudaEventRecord(c->ev[1], R.s);
@@ -912,7 +914,7 @@ extern "C" int lx_chunk_contexts(lx_ctx *c, const lx_tokenset *ts, const uint8_t
     *count = R.P.M;
     if (cap < R.P.M) return LX_E_CAPACITY;
     en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
-    en_enumerate<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+    en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
     en_resolve<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
     ctx_export<<<R.grid, EN_NT, 0, R.s>>>(R.P, d_starts, d_ctx);
     uint64_t nt, con;
