@@ -139,3 +139,23 @@ def test_capacity(gpu):
     rc, k, l, nt, con = run(lg, ctx, ts, w, 2, capacity=ek.size // 2)
     assert rc == lg.LX_E_CAPACITY and nt == ek.size and con == econ
     assert np.array_equal(k.astype(np.int64), ek[:ek.size // 2]) and np.array_equal(l.astype(np.int64), el[:ek.size // 2])
+
+
+@pytest.mark.parametrize("off", [1, 3, 8, 15])
+def test_unaligned_input(gpu, off):
+    # an input that does not start on a 16-byte boundary is read byte by byte
+    import torch
+    lg, ctx = gpu
+    dfa, disc = T.tokenset("clike_block"), T.discarded_kinds("clike_block")
+    ts = lg.lx_compile_tokenset(dfa, disc)
+    w = corpus.generate("clike_block", 5 * CH + 77, seed=15)
+    n = int(w.size)
+    d = torch.zeros(n + 64, dtype=torch.uint8, device="cuda")
+    d[off:off + n].copy_(torch.from_numpy(w.copy()))
+    k = torch.zeros(n + 1, dtype=torch.int16, device="cuda")
+    l = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    rc, nt, con = lg.lx_lex_enumerative(ctx, ts, d[off:off + n], 0, k, l)
+    ek, el, econ = oracle.lex(dfa, w)
+    assert rc == 0 and con == econ and nt == ek.size
+    assert np.array_equal(k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), ek)
+    assert np.array_equal(l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), el)

@@ -158,3 +158,39 @@ def test_speculative_malformed_and_ragged(env, trained):
         w[pos] = ord("`")
         _check(lg, ctx, ts, trained, w, 0)
         _check(lg, ctx, ts, None, w, 2)
+
+
+@pytest.mark.parametrize("off", [1, 7, 12])
+def test_speculative_unaligned_input(env, trained, off):
+    # an input that does not start on a 16-byte boundary is read byte by byte
+    import torch
+    lg, ctx, ts, S = env
+    w = corpus.generate(NAME, 3 * 4096 + 1234, seed=58)
+    n = int(w.size)
+    d = torch.zeros(n + 64, dtype=torch.uint8, device="cuda")
+    d[off:off + n].copy_(torch.from_numpy(w.copy()))
+    k = torch.zeros(n + 1, dtype=torch.int16, device="cuda")
+    l = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    rc, nt, con, _ = lg.lx_lex_speculative(ctx, ts, trained, d[off:off + n], 0, k, l)
+    ek, el, econ = oracle.lex(T.tokenset(NAME), w)
+    assert rc == 0 and con == econ and nt == ek.size
+    assert np.array_equal(k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), ek)
+    assert np.array_equal(l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), el)
+
+
+def test_speculative_capacity(env, trained):
+    # too small an output: LX_E_CAPACITY, the required count, and the first
+    # `capacity` tokens written
+    import torch
+    lg, ctx, ts, S = env
+    dfa = T.tokenset(NAME)
+    w = corpus.generate(NAME, 20 * 4096, seed=59)
+    ek, el, econ = oracle.lex(dfa, w)
+    ek, el = oracle.discard(ek, el, T.discarded_kinds(NAME), dfa.n_kinds)
+    cap = ek.size // 2
+    k = torch.zeros(cap, dtype=torch.int16, device="cuda")
+    l = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    rc, nt, con, _ = lg.lx_lex_speculative(ctx, ts, trained, _dev(w), 2, k, l)
+    assert rc == lg.LX_E_CAPACITY and nt == ek.size and con == econ
+    assert np.array_equal(k.cpu().numpy().view(np.uint16).astype(np.int64), ek[:cap])
+    assert np.array_equal(l.cpu().numpy().view(np.uint32).astype(np.int64), el[:cap])
