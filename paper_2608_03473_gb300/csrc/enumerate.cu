@@ -16,11 +16,11 @@
 //                  kept-token count, exit context at the next chunk start
 //                  (the chunk reads past its end to finish its last token),
 //                  or the failure offset;
-//   (3) resolve:   one CTA follows the chain of exits from BOUNDARY at offset
-//                  0 (1024 threads compose their runs of chunks, one thread
-//                  links the runs, then each thread labels its run): every
-//                  chunk's true entry context and output offset, and the first
-//                  failure (Corollary 1);
+//   (3) resolve:   the chain of exits from BOUNDARY at offset 0: runs of 16
+//                  chunks summarised per candidate (one thread each), groups of
+//                  runs composed and linked in one CTA, then each run labelled:
+//                  every chunk's true entry context and output offset, and the
+//                  first failure (Corollary 1);
 //   (4) emit:      per chunk, scan once more from its true context and write
 //                  its tokens at its offset.
 // The result is tok(w) (or pi_I(tok(w))) and con(w) exactly.
@@ -42,6 +42,7 @@ constexpr uint32_t KMAX = 8;           // candidate contexts per chunk start (BO
 constexpr int EN_NT = 256;             // threads of the plan / enumerate / emit kernels
 constexpr int RS_NT = 1024;            // threads of the resolve kernel
 constexpr int SO_NT = 1024;            // threads of the offset kernels (one chunk each)
+constexpr uint32_t R1 = 16;            // chunks per run of the resolve kernels
 constexpr uint64_t NOPOS64 = ~0ull;
 constexpr uint32_t NONE32_EN = 0xFFFFFFFFu;
 constexpr uint16_t CTX_B = 0xFFFEu;    // context: at a token boundary
@@ -66,6 +67,14 @@ struct EnResult {
     unsigned long long fail;    // con(w) when < n, else NOPOS64
     unsigned int error;
     unsigned int pad;
+};
+
+struct Summary {           // a run of chunks entered with one candidate
+    unsigned long long count;
+    uint32_t fail_chunk;   // chunk where the run fails (state 2)
+    uint16_t exit;         // context after the run (state 1)
+    uint8_t state;         // 0 broken, 1 ok, 2 fails
+    uint8_t fail_k;        // candidate index at the failing chunk
 };
 
 struct EnParams {
@@ -95,6 +104,12 @@ struct EnParams {
     unsigned long long *blk_sum; // [ceil(M / SO_NT)] kept tokens of each block of chunks, to its first failure
     unsigned long long *blk_off; // [ceil(M / SO_NT)] output offset of each block (~0: after the failure)
     uint32_t *blk_fail;          // [ceil(M / SO_NT)] first failing chunk of each block (NONE32_EN: none)
+    // resolve: runs of R1 consecutive chunks
+    uint32_t nr1;                // number of runs
+    Summary *sum1;               // [nr1 * KMAX] each run from each candidate of its first chunk
+    uint32_t *first1;            // [nr1] first chunk with a start (NONE32_EN: none)
+    uint32_t *entry1;            // [nr1] resolved candidate index (NONE32_EN: nothing emitted)
+    unsigned long long *prefix1; // [nr1] output offset of the run
 };
 
 // Shared-memory view of the scan table.
@@ -387,79 +402,130 @@ __global__ void __launch_bounds__(EN_NT) en_enumerate(EnParams P)
     }
 }
 
-// (3) resolve: one CTA of RS_NT threads
-struct Summary {           // a thread's run of chunks entered with one candidate
-    unsigned long long count;
-    uint32_t fail_chunk;   // chunk where the run fails (state 2)
-    uint16_t exit;         // context after the run (state 1)
-    uint8_t state;         // 0 broken, 1 ok, 2 fails
-    uint8_t fail_k;        // candidate index at the failing chunk
-};
+// (3) resolve, three launches.  en_sum: one thread per run of R1 chunks
+// follows the run from every candidate of its first chunk (count, exit
+// context, or failure).  en_link (one CTA of RS_NT threads): each thread
+// composes its group of runs from every candidate of the group's first chunk;
+// thread 0 links the groups from BOUNDARY at offset 0 and finds the first
+// failure (Corollary 1); each thread then gives each run of its group its
+// true candidate and output offset.  en_label: one thread per run labels its
+// chunks with their entry contexts and output offsets.
 
-__global__ void __launch_bounds__(RS_NT) en_resolve(EnParams P)
+// Follow the chunks from candidate k of chunk j up to chunk j1 (exclusive);
+// with `label`, give each its true entry context and output offset.
+__device__ Summary follow_run(const EnParams &P, const ScanEnv &E, uint32_t j, uint32_t k, uint32_t j1, bool label,
+                              unsigned long long base)
+{
+    Summary s{0, 0, CTX_BAD, 0, 0};
+    unsigned long long cnt = 0;
+    for (;;) {
+        const ChunkRes r = P.res[(size_t)j * KMAX + k];
+        if (label) {
+            ChunkOut o;
+            o.off = base + cnt;
+            o.entry = cand_ctx(E, P.cinfo[j] >> 8, k);
+            o.live = 1;
+            o.pad = 0;
+            P.out[j] = o;
+        }
+        if (r.fail != NOPOS64) {
+            s.state = 2;
+            s.count = cnt + r.count;
+            s.fail_chunk = j;
+            s.fail_k = (uint8_t)k;
+            return s;
+        }
+        if (r.exit == CTX_BAD) return s;   // broken: not the true chain
+        cnt += r.count;
+        uint32_t jn;
+        next_start(P, j, &jn);
+        if (jn >= j1) {
+            s.state = 1;
+            s.count = cnt;
+            s.exit = r.exit;
+            return s;
+        }
+        const int ki = cand_index(E, P.cinfo[jn] >> 8, r.exit);
+        if (ki < 0) return s;
+        j = jn;
+        k = (uint32_t)ki;
+    }
+}
+
+__global__ void __launch_bounds__(EN_NT) en_sum(EnParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const ScanEnv E = stage_scan(P, smem);
-    Summary *sum = reinterpret_cast<Summary *>(smem + ((P.blob_bytes + 15u) & ~15u));
-    uint32_t *first = reinterpret_cast<uint32_t *>(sum + RS_NT * KMAX);   // first chunk of each run
-    uint32_t *entry = first + RS_NT;                                      // resolved candidate index
-    unsigned long long *prefix = reinterpret_cast<unsigned long long *>(entry + RS_NT);
-    const uint32_t t = threadIdx.x;
-    const uint32_t per = (P.M + RS_NT - 1) / RS_NT;
-    const uint32_t j0 = min(P.M, t * per), j1 = min(P.M, j0 + per);
-
-    // follow the run [j0, j1) from candidate k of its first chunk
-    auto follow = [&](uint32_t j, uint32_t k, bool label, unsigned long long base) -> Summary {
-        Summary s{0, 0, CTX_BAD, 0, 0};
-        unsigned long long cnt = 0;
-        for (;;) {
-            const ChunkRes r = P.res[(size_t)j * KMAX + k];
-            if (label) {
-                ChunkOut o;
-                o.off = base + cnt;
-                o.entry = cand_ctx(E, P.cinfo[j] >> 8, k);
-                o.live = 1;
-                o.pad = 0;
-                P.out[j] = o;
-            }
-            if (r.fail != NOPOS64) {
-                s.state = 2;
-                s.count = cnt + r.count;
-                s.fail_chunk = j;
-                s.fail_k = (uint8_t)k;
-                return s;
-            }
-            if (r.exit == CTX_BAD) return s;   // broken: not the true chain
-            cnt += r.count;
-            uint32_t jn;
-            next_start(P, j, &jn);
-            if (jn >= j1) {
-                s.state = 1;
-                s.count = cnt;
-                s.exit = r.exit;
-                return s;
-            }
-            const int ki = cand_index(E, P.cinfo[jn] >> 8, r.exit);
-            if (ki < 0) return s;
-            j = jn;
-            k = (uint32_t)ki;
-        }
-    };
-
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P.nr1) return;
+    const uint32_t j0 = r * R1, j1 = min(P.M, j0 + R1);
     uint32_t f = NONE32_EN;
     for (uint32_t j = j0; j < j1; j++)
         if (P.start[j] != NOPOS64) {
             f = j;
             break;
         }
+    P.first1[r] = f;
+    if (f == NONE32_EN) return;
+    const uint32_t K = P.cinfo[f] & 0xFFu;
+    for (uint32_t k = 0; k < K; k++) P.sum1[(size_t)r * KMAX + k] = follow_run(P, E, f, k, j1, false, 0);
+}
+
+__global__ void __launch_bounds__(RS_NT) en_link(EnParams P)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const ScanEnv E = stage_scan(P, smem);
+    Summary *sum = reinterpret_cast<Summary *>(smem + ((P.blob_bytes + 15u) & ~15u));
+    uint32_t *first = reinterpret_cast<uint32_t *>(sum + RS_NT * KMAX);   // first run with a chunk
+    uint32_t *entry = first + RS_NT;                                      // resolved candidate index
+    unsigned long long *prefix = reinterpret_cast<unsigned long long *>(entry + RS_NT);
+    const uint32_t t = threadIdx.x;
+    const uint32_t per = (P.nr1 + RS_NT - 1) / RS_NT;
+    const uint32_t g0 = min(P.nr1, t * per), g1 = min(P.nr1, g0 + per);
+
+    // compose the runs [r, g1) entered with candidate k of run r's first chunk
+    auto compose = [&](uint32_t r, uint32_t k) -> Summary {
+        Summary a{0, 0, CTX_BAD, 0, 0};
+        unsigned long long cnt = 0;
+        uint16_t ctx = CTX_B;
+        for (bool head = true; r < g1; r++) {
+            if (P.first1[r] == NONE32_EN) continue;
+            if (!head) {
+                const int ki = cand_index(E, P.cinfo[P.first1[r]] >> 8, ctx);
+                if (ki < 0) return a;
+                k = (uint32_t)ki;
+            }
+            head = false;
+            const Summary s = P.sum1[(size_t)r * KMAX + k];
+            if (s.state == 2) {
+                a = s;
+                a.count += cnt;
+                return a;
+            }
+            if (s.state != 1) return a;
+            cnt += s.count;
+            ctx = s.exit;
+        }
+        a.state = 1;
+        a.count = cnt;
+        a.exit = ctx;
+        return a;
+    };
+
+    uint32_t f = NONE32_EN;
+    for (uint32_t r = g0; r < g1; r++)
+        if (P.first1[r] != NONE32_EN) {
+            f = r;
+            break;
+        }
     first[t] = f;
     if (f != NONE32_EN) {
-        const uint32_t K = P.cinfo[f] & 0xFFu;
-        for (uint32_t k = 0; k < K; k++) sum[t * KMAX + k] = follow(f, k, false, 0);
+        const uint32_t K = P.cinfo[P.first1[f]] & 0xFFu;
+        for (uint32_t k = 0; k < K; k++) sum[t * KMAX + k] = compose(f, k);
     }
     __syncthreads();
 
-    if (t == 0) {   // link the runs from BOUNDARY at offset 0
+    if (t == 0) {   // link the groups from BOUNDARY at offset 0
         uint16_t ctx = CTX_B;
         unsigned long long run = 0;
         uint32_t r = 0;
@@ -468,7 +534,7 @@ __global__ void __launch_bounds__(RS_NT) en_resolve(EnParams P)
             entry[r] = NONE32_EN;
             prefix[r] = run;
             if (first[r] == NONE32_EN) continue;
-            const int k = cand_index(E, P.cinfo[first[r]] >> 8, ctx);
+            const int k = cand_index(E, P.cinfo[P.first1[first[r]]] >> 8, ctx);
             if (k < 0) {
                 P.rec->error = 1;
                 break;
@@ -497,12 +563,52 @@ __global__ void __launch_bounds__(RS_NT) en_resolve(EnParams P)
     }
     __syncthreads();
 
-    // label this run's chunks with their entry contexts and offsets
+    // each run of the group: its true candidate and output offset
+    uint32_t k = entry[t];
+    unsigned long long pre = prefix[t];
+    uint16_t ctx = CTX_B;
+    bool live = k != NONE32_EN, head = true;
+    for (uint32_t r = g0; r < g1; r++) {
+        const uint32_t fc = P.first1[r];
+        if (!live || fc == NONE32_EN) {
+            P.entry1[r] = NONE32_EN;
+            continue;
+        }
+        if (!head) {
+            const int ki = cand_index(E, P.cinfo[fc] >> 8, ctx);
+            if (ki < 0) {
+                live = false;
+                P.entry1[r] = NONE32_EN;
+                continue;
+            }
+            k = (uint32_t)ki;
+        }
+        head = false;
+        const Summary s = P.sum1[(size_t)r * KMAX + k];
+        P.entry1[r] = k;
+        P.prefix1[r] = pre;
+        if (s.state != 1) {   // the failing run (or a break): nothing after it
+            live = false;
+            continue;
+        }
+        pre += s.count;
+        ctx = s.exit;
+    }
+}
+
+__global__ void __launch_bounds__(EN_NT) en_label(EnParams P)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const ScanEnv E = stage_scan(P, smem);
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P.nr1) return;
+    const uint32_t j0 = r * R1, j1 = min(P.M, j0 + R1);
     for (uint32_t j = j0; j < j1; j++) {
         ChunkOut o{0, CTX_BAD, 0, 0};
         P.out[j] = o;
     }
-    if (entry[t] != NONE32_EN) follow(first[t], entry[t], true, prefix[t]);
+    const uint32_t k = P.entry1[r];
+    if (k != NONE32_EN) follow_run(P, E, P.first1[r], k, j1, true, P.prefix1[r]);
 }
 
 // (4) emit
@@ -598,7 +704,7 @@ __global__ void __launch_bounds__(EN_NT) sp_fix(EnParams P)
     }
 }
 
-// Chunk starts and their true entry contexts (after en_resolve), per target.
+// Chunk starts and their true entry contexts (after en_label), per target.
 __global__ void __launch_bounds__(EN_NT) ctx_export(EnParams P, uint64_t *starts, uint16_t *ctx)
 {
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
@@ -608,9 +714,6 @@ __global__ void __launch_bounds__(EN_NT) ctx_export(EnParams P, uint64_t *starts
     }
 }
 
-// Output offsets along the settled chain (one CTA): each thread sums its run
-// of chunks, thread 0 links the runs and finds the first failure, each
-// thread labels its run.
 // The settled chunks' staged tokens to their output offsets, one warp per
 // chunk, coalesced: the last scan of every chunk ran from its true entry
 // context, so no chunk is walked again to emit.
@@ -802,7 +905,10 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     const size_t nb = (M + SO_NT - 1) / SO_NT;
     const size_t o_bsum = al(o_stl + (stage ? 4 * (size_t)n : 0)), o_boff = al(o_bsum + 8 * nb);
     const size_t o_bfail = al(o_boff + 8 * nb);
-    const size_t total = al(o_bfail + 4 * nb);
+    const size_t nr1 = (M + R1 - 1) / R1;
+    const size_t o_sum1 = al(o_bfail + 4 * nb), o_first1 = al(o_sum1 + sizeof(Summary) * KMAX * nr1);
+    const size_t o_entry1 = al(o_first1 + 4 * nr1), o_prefix1 = al(o_entry1 + 4 * nr1);
+    const size_t total = al(o_prefix1 + 8 * nr1);
     rc = grow(&c->e_dev, &c->e_dev_bytes, total);
     if (rc != LX_OK) return rc;
     uint8_t *d = static_cast<uint8_t *>(c->e_dev);
@@ -839,6 +945,11 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     P.blk_sum = reinterpret_cast<unsigned long long *>(d + o_bsum);
     P.blk_off = reinterpret_cast<unsigned long long *>(d + o_boff);
     P.blk_fail = reinterpret_cast<uint32_t *>(d + o_bfail);
+    P.nr1 = (uint32_t)nr1;
+    P.sum1 = reinterpret_cast<Summary *>(d + o_sum1);
+    P.first1 = reinterpret_cast<uint32_t *>(d + o_first1);
+    P.entry1 = reinterpret_cast<uint32_t *>(d + o_entry1);
+    P.prefix1 = reinterpret_cast<unsigned long long *>(d + o_prefix1);
     R.guess_buf = reinterpret_cast<uint16_t *>(d + o_guess);
 
     R.smem = P.blob_bytes;
@@ -850,8 +961,9 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
             cudaFuncSetAttribute(en_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(en_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(sp_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
-            cudaFuncSetAttribute(en_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) !=
-                cudaSuccess)
+            cudaFuncSetAttribute(en_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+            cudaFuncSetAttribute(en_label, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+            cudaFuncSetAttribute(en_link, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
             return LX_E_CUDA;
         attr_done[dev] = true;
     }
@@ -897,7 +1009,9 @@ extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_
     if (c->timing) cudaEventRecord(c->ev[0], R.s);
     en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
     en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
-    en_resolve<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+    en_sum<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
+    en_link<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+    en_label<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
     en_emit<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
     if (c->timing) cudaEventRecord(c->ev[1], R.s);
     return en_finish(c, R, capacity, n_tokens, consumed);
@@ -915,7 +1029,9 @@ extern "C" int lx_chunk_contexts(lx_ctx *c, const lx_tokenset *ts, const uint8_t
     if (cap < R.P.M) return LX_E_CAPACITY;
     en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
     en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
-    en_resolve<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+    en_sum<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
+    en_link<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+    en_label<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
     ctx_export<<<R.grid, EN_NT, 0, R.s>>>(R.P, d_starts, d_ctx);
     uint64_t nt, con;
     rc = en_finish(c, R, ~0ull, &nt, &con);
