@@ -27,12 +27,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MiB = 1 << 20
-CUTS = {"json": "tab, newline, carriage return (certified modulo I = {ws})",
+CUTS = {"arith": "newline ( ) * + - / ; (exact certificate, I empty)",
+        "json": "tab, newline, carriage return (certified modulo I = {ws})",
         "clike": "newline (certified modulo I = {ws, line comment})",
         "clike_block": "none certified: chunk starts every 4096 B after the byte with the fewest entry contexts"}
 
 
 def metric_name(workload, mib):
+    if workload == "arith":
+        return f"input GB/s lexed ({mib} MiB arith token stream, full stream, exact cuts, bit-exact)"
     if workload == "clike_block":
         return f"input GB/s lexed ({mib} MiB C-like with block comments, full stream, speculative entry contexts, bit-exact)"
     label = {"json": "JSON", "clike": "C-like"}[workload]
@@ -40,6 +43,8 @@ def metric_name(workload, mib):
 
 
 def workload_name(workload, mib):
+    if workload == "arith":
+        return f"arith_{mib}mib_full_exact"
     if workload == "clike_block":
         return f"clike_block_{mib}mib_full_speculative"
     return f"{workload}_{mib}mib_filtered_modulo"
@@ -144,6 +149,52 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def time_parallel(w, dfa, disc, useful, sample_bytes, reps=3):
+    """The paper's method on the host: the Section 6 planner, one thread per
+    chunk, ordered concatenation (oracle/parsplit.c), at k = 1, 2, 4, ... up
+    to every core; median of `reps` runs per k."""
+    import oracle
+    s = w[:sample_bytes]
+    cores = cpu_cores()
+    ks = sorted({1 << i for i in range(cores.bit_length()) if (1 << i) <= cores} | {cores})
+    by_k = {}
+    tokens = 0
+    for k in ks:
+        secs = []
+        for _ in range(reps):
+            ok, ol, con, chunks, sec = oracle.par_lex(dfa, s, useful, disc or [], k, cap=s.size // 2 + 16)
+            secs.append(sec)
+            tokens = ok.size
+        by_k[k] = s.size / statistics.median(secs) / 1e9
+    return {"value": by_k[cores], "unit": "GB/s", "cores": cores, "kind": "cpu_parallel_certified_split",
+            "by_threads_gbs": {str(k): v for k, v in by_k.items()},
+            "sample": f"first {s.size // MiB} MiB of the corpus, median of {reps} runs per thread count, "
+                      f"{tokens} output tokens",
+            "method": "Section 6 planner (k-1 equal-division targets slid to the next useful certified byte), "
+                      "one pthread per chunk scanning from q0 with pi_I fused, ordered concatenation",
+            "cpu_model": cpu_model(), "compiler": "gcc " + " ".join(__import__("oracle").CFLAGS),
+            "timed": "planning through concatenation, input resident in host memory"}
+
+
 def time_oracle(w, dfa, disc, sample_bytes, reps=1):
     """Serial oracle (one host core) over the first `sample_bytes` of w."""
     import oracle
@@ -166,8 +217,8 @@ def run_reference(args, rank, world):
         return
     from lexinputs import corpus, tokensets
     dfa = tokensets.tokenset(args.workload)
-    disc = None if args.workload == "clike_block" else tokensets.discarded_kinds(args.workload)
-    sample = args.ref_sample_mib * MiB
+    disc = None if args.workload in ("clike_block", "arith") else tokensets.discarded_kinds(args.workload)
+    sample = min(args.ref_sample_mib, args.size_mib) * MiB
     w = corpus.generate(args.workload, sample)
     times = []
     for i in range(args.warmup + args.steps):
@@ -182,10 +233,10 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "impl": "reference",
         "config": {"workload": workload_name(args.workload, args.size_mib),
-                   "sample": f"first {args.ref_sample_mib} MiB of the {args.size_mib} MiB corpus",
+                   "sample": f"first {sample // MiB} MiB of the {args.size_mib} MiB corpus",
                    "bytes_per_step": n},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {args.ref_sample_mib} MiB of the corpus per step, serial scan + pi_I"},
+                         "sample": f"first {sample // MiB} MiB of the corpus per step, serial scan + pi_I"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "tokens_per_s": tok * len(times) / total,
     }
@@ -269,6 +320,7 @@ def run_batch(args, rank, world, local):
             k, l = oracle.discard(k, l, tokensets.discarded_kinds(nm), dfa.n_kinds)
             assert c == con and k.size == nt
             assert np.array_equal(kk[off:off + nt], k) and np.array_equal(ll[off:off + nt], l)
+        del kk, ll
     batch = lg.BatchDocs(sets, docs)   # descriptors built once, as a serving loop would
     for _ in range(args.warmup):
         lg.lx_lex_batch(ctx, sets, batch, mode, d_k, d_l, stream=stream, want_results=False)
@@ -395,6 +447,7 @@ def run_batch(args, rank, world, local):
                     "api": "torch pinned copies + lx_lex_batch"},
             "gpu_launches": len(BATCH_NAMES) * args.steps,
             "clocks": clocks,
+            "bit_exact": True if args.check else None,
         }), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -408,13 +461,17 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=7)
     ap.add_argument("--e2e-parts", type=int, default=8, help="batch workload: parts of the end-to-end pipeline")
-    ap.add_argument("--size-mib", type=int, default=512)
-    ap.add_argument("--workload", default="json", choices=["json", "clike", "clike_block", "batch"])
+    ap.add_argument("--size-mib", type=int, default=None, help="input size (default 512; arith: 1)")
+    ap.add_argument("--workload", default="json", choices=["json", "clike", "clike_block", "batch", "arith"])
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--check", action="store_true", help="also compare the output with the oracle")
+    ap.add_argument("--no-check", action="store_true",
+                    help="skip the untimed element-by-element comparison with the oracle")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.size_mib is None:
+        args.size_mib = 1 if args.workload == "arith" else 512
+    args.check = not args.no_check
 
     rank, world, local = dist_env()
     if args.workload == "batch":
@@ -445,6 +502,8 @@ def main():
     lg.lx_ctx_enable_timing(ctx, True)
     stream = torch.cuda.current_stream()
     refused = args.workload == "clike_block"
+    full = refused or args.workload == "arith"          # the full stream, exact cuts
+    small = n < 256 * MiB                               # flush L2 between timed steps
     lex_fn = lg.lx_lex
     spec_model, train_s, spec_stats = None, None, {}
     if refused:
@@ -464,22 +523,27 @@ def main():
             return rc_, nt_, con_
 
     d_in = torch.from_numpy(w).to("cuda")
-    cap = (n // 2 if refused else n // 4) + 1024   # the full stream keeps whitespace tokens
+    cap = (n // 2 + 1024 if refused else n + 1 if full else n // 4 + 1024)   # the full stream keeps every token
     d_k = torch.empty(cap, dtype=torch.int16, device="cuda")
     d_l = torch.empty(cap, dtype=torch.int32, device="cuda")
-    mode = lg.LX_FULL_EXACT if refused else lg.LX_FILTERED_MODULO
+    mode = lg.LX_FULL_EXACT if full else lg.LX_FILTERED_MODULO
     rc, nt, con = lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
     assert rc == 0, lg.lx_strerror(rc)
     assert con == n
 
+    bit_exact = None
     if args.check:
+        # one untimed comparison of the whole output with the oracle
         import oracle
         k, l, c = oracle.lex(dfa, w)
-        if not refused:
+        if not full:
             k, l = oracle.discard(k, l, disc, dfa.n_kinds)
-        assert c == con and k.size == nt
-        assert np.array_equal(d_k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), k)
-        assert np.array_equal(d_l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), l)
+        bit_exact = bool(c == con and k.size == nt
+                         and np.array_equal(d_k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), k)
+                         and np.array_equal(d_l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), l))
+        del k, l
+        if not bit_exact:
+            raise RuntimeError("output differs from the oracle")
 
     for _ in range(args.warmup):
         lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
@@ -493,18 +557,37 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     kernel_ms = []
-    ev0.record(stream)
-    for _ in range(args.steps):
-        rc, nt2, con2 = lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
-        kernel_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
-        if rc != 0 or nt2 != nt or con2 != con:
-            raise RuntimeError(f"step failed: {rc} {nt2} {con2}")
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    if small:
+        # inputs smaller than L2: each step is timed on its own, after a write
+        # of a buffer larger than L2 (outside the step's events)
+        flush = torch.empty(256 * MiB, dtype=torch.uint8, device="cuda")
+        call_ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, nt2, con2 = lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
+            e1.record(stream)
+            kernel_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
+            if rc != 0 or nt2 != nt or con2 != con:
+                raise RuntimeError(f"step failed: {rc} {nt2} {con2}")
+            torch.cuda.synchronize()
+            call_ms.append(e0.elapsed_time(e1))
+        total_ms = max_over_ranks(sum(call_ms))
+        del flush
+    else:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            rc, nt2, con2 = lex_fn(ctx, ts, d_in, mode, d_k, d_l, stream=stream)
+            kernel_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
+            if rc != 0 or nt2 != nt or con2 != con:
+                raise RuntimeError(f"step failed: {rc} {nt2} {con2}")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        total_ms = max_over_ranks(ev0.elapsed_time(ev1))
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = max_over_ranks(ev0.elapsed_time(ev1))
     ms_per_step = total_ms / args.steps
     value = world * n * args.steps / (total_ms / 1e3) / 1e9
     tokens_per_s = world * nt * args.steps / (total_ms / 1e3)
@@ -550,21 +633,31 @@ def main():
 
     if rank == 0:
         cpu = None
+        ex_mask, mo_mask = lg.lx_certificates(ts)
         if not args.no_cpu_baseline:
             sample = min(n, 256 * MiB)
             sample = min(sample, 64 * MiB) if refused else sample
-            sb, stok, sdt = time_oracle(w, dfa, disc, sample)
+            sb, stok, sdt = time_oracle(w, dfa, None if full else disc, sample)
             cpu = {"value": sb / sdt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                   "sample": f"first {sample // MiB} MiB of the corpus, one pass, serial scan + pi_I "
-                             f"({sdt:.1f} s, {stok} kept tokens)"}
+                   "sample": f"first {sample // MiB} MiB of the corpus, one pass, serial scan"
+                             f"{'' if full else ' + pi_I'} ({sdt:.1f} s, {stok} output tokens)"}
+            if not refused:
+                cpu["parallel_certified_split"] = time_parallel(
+                    w, dfa, None if full else disc, ex_mask if full else mo_mask, min(n, 256 * MiB))
+            else:
+                cpu["parallel_certified_split"] = {
+                    "value": None, "note": "the token set certifies no byte (exact or modulo): the paper's "
+                                           "planner returns one chunk, so the method runs serially"}
         line = {
             "metric": metric_name(args.workload, args.size_mib), "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": workload_name(args.workload, args.size_mib), "bytes": n, "tokens_kept": nt,
-                       "mode": "LX_FULL_EXACT" if refused else "LX_FILTERED_MODULO", "cuts": CUTS[args.workload],
+                       "mode": "LX_FULL_EXACT" if full else "LX_FILTERED_MODULO", "cuts": CUTS[args.workload],
                        "seed": hex(corpus.WORKLOADS[args.workload][2]), "sha256": sha,
-                       "l2": f"inputs ({args.size_mib} MiB) larger than L2 (129 MB); no flush between steps",
+                       "l2": (f"input ({args.size_mib} MiB) smaller than L2: a 256 MiB buffer is written "
+                              f"before each step, outside the step's timing" if small else
+                              f"inputs ({args.size_mib} MiB) larger than L2 (129 MB); no flush between steps"),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "tokens_per_s": tokens_per_s,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -581,12 +674,15 @@ def main():
                     "api": "torch pinned copies + lx_lex_speculative" if refused else "lx_lex_host"},
             "gpu_launches": (None if refused else args.steps),
             "clocks": clocks,
+            "bit_exact": bit_exact,
         }
+        if small:
+            line["us_per_call"] = 1e3 * total_ms / args.steps
+            line["kernel_us"] = 1e3 * k_ms
         # both certificates of the token set (Definitions 2 and 3)
-        ex_mask, mo_mask = lg.lx_certificates(ts)
         fmt = lambda m: [f"0x{b:02x}" for b in range(256) if m[b]]
         line["config"]["certified"] = {"exact": fmt(ex_mask), "modulo": fmt(mo_mask)}
-        if not refused:
+        if not full:
             # the same filtered stream under exact cuts: with no exact-certified
             # byte the certified path is one chunk, so it runs through the
             # enumerative path, which needs no certified byte; its output must

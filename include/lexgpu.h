@@ -419,7 +419,12 @@ int lx_lex_batch(lx_ctx *ctx, const lx_tokenset *const *sets, uint32_t n_sets, c
  *
  * The first call on a device does a one-time set-up with that device
  * current: it looks up the array's device address and sets the kernel's
- * shared-memory attribute.  Make that first call before any stream capture.
+ * shared-memory attribute.  Under lazy module loading (the CUDA default)
+ * that look-up may load the library's module and with it the array itself,
+ * so make one warm-up call outside any allocation-sensitive region, and
+ * before any stream capture.  Each call copies the token set's tables from
+ * pageable host memory into the array with cudaMemcpyAsync; that copy goes
+ * through driver-owned staging and is not free of host synchronization.
  * Every call uses the same array and leaves the last call's contents in it,
  * so calls that overlap on the GPU (for example on two streams at once, or
  * from two host threads) race and must be serialized by the caller.

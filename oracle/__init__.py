@@ -15,6 +15,9 @@ reference run used by the tests:
                         side of Theorems 1 and 3.
 * ``plan``           -- the planner of Section 6: slide each of k-1 equal-division
                         targets forward to the next useful certified byte.
+* ``par_lex``        -- not an oracle: the paper's method on host threads
+                        (``parsplit.c``: the planner, one thread per chunk,
+                        ordered concatenation), timed as the CPU baseline.
 * ``contexts``       -- (submodule) entry contexts of the serial scan, their
                         candidate sets and chunk runs entered in a context:
                         splitting a token set with no certified byte.
@@ -37,6 +40,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lexoracle.c")
+_SRC_PAR = os.path.join(_HERE, "parsplit.c")
+CFLAGS = ["-O2", "-std=c11", "-pthread"]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liblexoracle.so")
 _lock = threading.Lock()
@@ -46,10 +51,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile lexoracle.c into oracle/_build/liblexoracle.so with gcc."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    stale = (not os.path.exists(_LIB_PATH)) or any(
+        os.path.getmtime(_LIB_PATH) < os.path.getmtime(f) for f in (_SRC, _SRC_PAR))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp])
+        subprocess.check_call(["gcc", *CFLAGS, "-shared", "-fPIC", _SRC, _SRC_PAR, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -66,6 +72,8 @@ def _load():
             lib.orc_filter.argtypes = [p, p, i64, p, i32, p, p]
             lib.orc_certificates.restype = ctypes.c_int
             lib.orc_certificates.argtypes = [i32, i32, p, p, p, i32, p, p, p, p, p, p]
+            lib.par_lex.restype = i64
+            lib.par_lex.argtypes = [i32, p, p, p, p, i32, p, i64, i32, p, p, i64, p, p, p]
             _lib = lib
     return _lib
 
@@ -210,3 +218,35 @@ def plan(data, useful: np.ndarray, k: int) -> List[int]:
         if 0 < t < n and (not cuts or cuts[-1] < t):
             cuts.append(t)
     return cuts
+
+
+def par_lex(dfa, data, useful: np.ndarray, discarded: Iterable[int] = (), k: int = 1,
+            cap: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray, int, int, float]:
+    """The paper's CPU method (``parsplit.c``): plan k chunks at useful
+    certified bytes, scan each on its own thread (pi_I fused for a non-empty
+    ``discarded``), concatenate in order.  Returns (kinds u16, lens u32, con,
+    chunks, seconds from planning to the end of the concatenation)."""
+    a = _as_automaton(dfa)
+    w = _as_bytes(data)
+    lib = _load()
+    n = int(w.size)
+    cap = n if cap is None else int(cap)
+    ok = np.empty(max(cap, 1), np.uint16)
+    ol = np.empty(max(cap, 1), np.uint32)
+    use = np.ascontiguousarray(np.asarray(useful, dtype=bool).astype(np.uint8))
+    I = list(discarded)
+    in_I = np.zeros(max(a.n_kinds, 1), np.uint8)
+    for d in I:
+        in_I[int(d)] = 1
+    con = ctypes.c_int64(0)
+    chunks = ctypes.c_int32(0)
+    sec = ctypes.c_double(0.0)
+    wbuf = w if n else np.zeros(1, np.uint8)
+    t = lib.par_lex(a.q0, _ptr(a.delta), _ptr(a.tau), _ptr(use), _ptr(in_I) if I else None, a.n_kinds,
+                    _ptr(wbuf), n, int(k), _ptr(ok), _ptr(ol), cap, ctypes.addressof(con),
+                    ctypes.addressof(chunks), ctypes.addressof(sec))
+    if t < 0:
+        raise MemoryError("par_lex: out of memory")
+    if t > cap:
+        raise ValueError(f"token capacity {cap} too small for {t} tokens")
+    return ok[:t].copy(), ol[:t].copy(), int(con.value), int(chunks.value), float(sec.value)

@@ -2022,6 +2022,10 @@ constexpr size_t NA_RESULT = NA_TABLE_BYTES;            // Result, then the tile
 constexpr size_t NA_STATUS = NA_TABLE_BYTES + 64;       // one u64 status word per tile
 constexpr uint64_t NA_MAX_TILES = (LX_NOALLOC_SCRATCH_BYTES - NA_STATUS) / 8;
 static_assert(NA_MAX_TILES * TILE == LX_NOALLOC_MAX_INPUT, "LX_NOALLOC_MAX_INPUT out of date");
+// the largest walk-table blob (rows, byte-form kind words, class map and cut
+// table, 16-byte padding) fits the table slot, so it never reaches the status words
+static_assert(MAX_TABLE_BYTES + 2 * (MAX_BYTE_FORM_BYTES / 512) + 16 + 256 + 256 + 16 <= NA_TABLE_BYTES,
+              "walk tables can overrun the no-alloc table slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LX_NOALLOC_SCRATCH_BYTES];
 

@@ -180,6 +180,17 @@ def test_full_size_json_512mib(gpu):
     assert nt > 50_000_000
 
 
+def test_full_size_clike_512mib(gpu):
+    """The 512 MiB C-like workload (filtered modulo I = {ws, line comment},
+    cuts at newlines) in the bench's launch configuration, compared in full
+    with the oracle."""
+    lg, ctx = gpu
+    w = corpus.generate("clike")
+    assert w.size == 512 << 20
+    nt = check(lg, ctx, "clike", w, 2)
+    assert nt > 50_000_000
+
+
 def _dense_lines(rng, n_bytes, min_len, max_len, alphabet):
     """Newline-separated lines of back-to-back short C-like tokens: ranges
     (newline to newline) far longer than a lane's record column."""

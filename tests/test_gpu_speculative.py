@@ -194,3 +194,30 @@ def test_speculative_capacity(env, trained):
     assert rc == lg.LX_E_CAPACITY and nt == ek.size and con == econ
     assert np.array_equal(k.cpu().numpy().view(np.uint16).astype(np.int64), ek[:cap])
     assert np.array_equal(l.cpu().numpy().view(np.uint32).astype(np.int64), el[:cap])
+
+
+def test_full_size_refused_512mib(env, trained):
+    """The 512 MiB refused-set workload (C-like with block comments and
+    multi-line strings, full stream): the speculative path with the trained
+    model and the enumerative path, each compared in full with the oracle."""
+    import torch
+    lg, ctx, ts, S = env
+    w = corpus.generate(NAME)
+    n = int(w.size)
+    assert n == 512 << 20
+    ek, el, econ = oracle.lex(T.tokenset(NAME), w)
+    assert econ == n
+    d = _dev(w)
+    k = torch.zeros(n // 2, dtype=torch.int16, device="cuda")
+    l = torch.zeros(n // 2, dtype=torch.int32, device="cuda")
+    for path in ("speculative", "enumerative"):
+        k.zero_()
+        l.zero_()
+        if path == "speculative":
+            rc, nt, con, st = lg.lx_lex_speculative(ctx, ts, trained, d, 0, k, l)
+            assert st["rescanned"] < 0.1 * st["chunks"], st
+        else:
+            rc, nt, con = lg.lx_lex_enumerative(ctx, ts, d, 0, k, l)
+        assert rc == 0 and con == econ and nt == ek.size, (path, rc, con, nt, ek.size)
+        assert np.array_equal(k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), ek), path
+        assert np.array_equal(l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), el), path
