@@ -99,6 +99,23 @@ int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded, uint32_t n
                         lx_tokenset **out);
 
 /*
+ * lx_compile_tokenset_framed -- lx_compile_tokenset for documents framed at
+ * the producer (Section 7.1, Framing at the producer).  The reserved byte
+ * `frame_byte` (conventionally 0x1E, RECORD SEPARATOR) gets a rule of its own:
+ * a new token kind, numbered dfa->n_kinds, of that one byte from q0; every
+ * other state of `dfa` rejects the byte, so no other token admits it at any
+ * position.  Its only live consumption is then from q0, and with q0 not
+ * re-entrant Definition 2 certifies it: a document whose producer emits the
+ * byte only at token boundaries (escaping it inside tokens) splits at every
+ * occurrence, whatever the rest of the token set certifies.  With
+ * frame_discarded != 0 the frame kind joins the discarded set.  The
+ * automaton gains one state and, when the byte shares its class, one class.
+ * Errors as lx_compile_tokenset; LX_E_INVAL for frame_byte > 255.
+ */
+int lx_compile_tokenset_framed(const lx_dfa *dfa, const uint16_t *discarded, uint32_t n_discarded,
+                               uint32_t frame_byte, int frame_discarded, lx_tokenset **out);
+
+/*
  * lx_certificates -- the useful certified bytes (Corollary 2) and the useful
  * bytes certified modulo I (Proposition 2).  Bit (b & 31) of word (b >> 5) is
  * byte b.  Either output pointer may be NULL.  Host only.
@@ -127,6 +144,24 @@ int lx_tokenset_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, 
  * that is class-indexed already). */
 int lx_tokenset_class_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
                             uint32_t meta_len);
+
+/*
+ * lx_tokenset_walk_table -- the event-code walk table of `mode` that the
+ * warp-tile kernel of lx_lex stages in shared memory (for inspection and
+ * host-side tests).  Copies min(cap, size) bytes of the blob to `out` (host,
+ * may be NULL) and fills the first meta_len (<= 10) entries of meta:
+ *   { blob bytes, table_form, n_rows, row_shift, p_start, p_pre,
+ *     acc_off, kmap_off, cmap_off, cut_off }.
+ * Entries are u16: target row offset (from the blob start) | event code << 1
+ * (code 0: no token ended before the byte; 1: a discarded token ended;
+ * c >= 2: a kept token of kind kind_map[c] ended).  Byte form: row r holds
+ * the entry of byte b at r * 512 + 2b; class form: of class c at
+ * r * 256 + 2c, with cmap2[b] = 2 class(b).  Returns LX_E_TOOBIG when the
+ * automaton has no such table for `mode` (more than 126 kept kinds, or rows
+ * beyond the shared-memory budget); lx_lex then takes the tile kernel.
+ */
+int lx_tokenset_walk_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
+                           uint32_t meta_len);
 
 /* Release a token set (NULL is a no-op).  Frees its device tables. */
 void lx_tokenset_free(lx_tokenset *ts);
@@ -168,6 +203,24 @@ int lx_ctx_set_timeout_ms(lx_ctx *ctx, uint32_t ms);
  * launches (milliseconds, host out).  Off by default. */
 int lx_ctx_enable_timing(lx_ctx *ctx, int on);
 int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
+
+/*
+ * lx_ctx_set_kernel -- which kernel lx_lex uses on this context.
+ *   LX_KERNEL_AUTO (default): the warp-tile kernel (every warp owns 4096-byte
+ *     tiles, event codes in the walk table) when the token set has an
+ *     event-code walk table for the mode (lx_tokenset_walk_table) and d_in is
+ *     16-byte aligned; the tile kernel (CTAs of 256 threads over 17408-byte
+ *     tiles, per-lane token records) otherwise;
+ *   LX_KERNEL_TILE: always the tile kernel;
+ *   LX_KERNEL_WARP: always the warp-tile kernel; lx_lex returns LX_E_INVAL
+ *     for a call it cannot serve.
+ * Both produce the same stream (tests compare them).  Returns LX_E_INVAL
+ * for another value.  lx_lex_host and lx_lex_batch always use the tile kernel.
+ */
+#define LX_KERNEL_AUTO 0
+#define LX_KERNEL_TILE 1
+#define LX_KERNEL_WARP 2
+int lx_ctx_set_kernel(lx_ctx *ctx, int kernel);
 
 /*
  * lx_ctx_debug_withhold -- failure-detection test hook.  In later lx_lex
@@ -330,17 +383,23 @@ int lx_model_train_step(lx_model *m, const uint16_t *d_windows, const uint16_t *
  * chunks whose entry changed, until the chain from offset 0 is consistent:
  * the result is exact whatever the predictions.  Same output and errors as
  * lx_lex_enumerative; LX_E_INVAL when the model does not score states + 1
- * contexts of this token set.  stats (optional): chunk targets, rounds (scans
- * of the dirty chunks, the first included), chunks scanned again after the
- * first round.  Each scan also stages the chunk's kept tokens in context
- * scratch (6 bytes of device memory per input byte), so that the settled
- * chunks are copied to the output rather than scanned again.
+ * contexts of this token set.  At most 4 fix-up rounds run (on the device,
+ * with one read-back after them); chunks still unsettled then are decided by
+ * the enumerative scan of lx_lex_enumerative as the judge (every chunk from
+ * every candidate context, chains resolved from BOUNDARY at offset 0), after
+ * which one more round rescans the chunks whose entry it changed.  stats
+ * (optional): chunk targets, rounds that scanned chunks (the first, the
+ * fix-up rounds that changed an entry, and the round after the judge), chunks
+ * scanned again after the first round, judged = 1 when the judge ran.  Each
+ * scan also stages the chunk's kept tokens in context scratch (6 bytes of
+ * device memory per input byte), so that the settled chunks are copied to the
+ * output rather than scanned again.
  */
 typedef struct {
     uint64_t chunks;
     uint32_t rounds;
     uint32_t rescanned;
-    uint64_t mispredicted_first;   /* reserved, 0 */
+    uint64_t judged;
 } lx_spec_stats;
 int lx_lex_speculative(lx_ctx *ctx, const lx_tokenset *ts, lx_model *model, const uint8_t *d_in, uint64_t n,
                        int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,

@@ -442,7 +442,10 @@ static void c_block_comment(cctx *c)
     puts_(c->s, " */\n");
 }
 
-static uint64_t gen_c_common(uint64_t seed, uint8_t *out, uint64_t n, int block)
+/* block: unrestricted block comments; frame: the producer puts the record
+ * separator 0x1E before every unit (a statement line or a block comment),
+ * which is always a token boundary of its output (Section 7.1). */
+static uint64_t gen_c_common(uint64_t seed, uint8_t *out, uint64_t n, int block, int frame)
 {
     rng_t r; rng_seed(&r, seed);
     uint64_t tmp_cap = 1u << 16;
@@ -452,6 +455,7 @@ static uint64_t gen_c_common(uint64_t seed, uint8_t *out, uint64_t n, int block)
     for (;;) {
         sink_t s = {tmp, 0, tmp_cap, 0};
         cctx c = {&r, &s, block};
+        if (frame) put(&s, 0x1E);
         if (block && chance(&r, 0.025)) c_block_comment(&c);
         else c_line(&c, &indent);
         if (s.full) continue;
@@ -464,5 +468,6 @@ static uint64_t gen_c_common(uint64_t seed, uint8_t *out, uint64_t n, int block)
     return pos;
 }
 
-uint64_t gen_clike(uint64_t seed, uint8_t *out, uint64_t n) { return gen_c_common(seed, out, n, 0); }
-uint64_t gen_clike_block(uint64_t seed, uint8_t *out, uint64_t n) { return gen_c_common(seed, out, n, 1); }
+uint64_t gen_clike(uint64_t seed, uint8_t *out, uint64_t n) { return gen_c_common(seed, out, n, 0, 0); }
+uint64_t gen_clike_block(uint64_t seed, uint8_t *out, uint64_t n) { return gen_c_common(seed, out, n, 1, 0); }
+uint64_t gen_clike_block_framed(uint64_t seed, uint8_t *out, uint64_t n) { return gen_c_common(seed, out, n, 1, 1); }

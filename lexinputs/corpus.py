@@ -9,6 +9,9 @@ arith              arith token stream          1 MiB           0x1EC50001
 json               newline-delimited JSON      512 MiB         0x1EC50002
 clike              C-like statement lines      512 MiB         0x1EC50003
 clike_block        C-like + block comments     512 MiB         0x1EC50005
+clike_block_framed the same, 0x1E before every  512 MiB         0x1EC50006
+                   line or comment (producer
+                   framing, Section 7.1)
 =================  ==========================  ==============  ===========
 """
 
@@ -36,6 +39,7 @@ WORKLOADS = {
     "json": ("gen_json", 512 * MiB, 0x1EC50002),
     "clike": ("gen_clike", 512 * MiB, 0x1EC50003),
     "clike_block": ("gen_clike_block", 512 * MiB, 0x1EC50005),
+    "clike_block_framed": ("gen_clike_block_framed", 512 * MiB, 0x1EC50006),
 }
 
 
@@ -55,7 +59,7 @@ def _load():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
-            for fn in ("gen_arith", "gen_json", "gen_clike", "gen_clike_block"):
+            for fn in ("gen_arith", "gen_json", "gen_clike", "gen_clike_block", "gen_clike_block_framed"):
                 f = getattr(lib, fn)
                 f.restype = ctypes.c_uint64
                 f.argtypes = [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64]

@@ -178,3 +178,22 @@ def tokenset(name: str) -> DFA:
 def discarded_kinds(name: str) -> List[int]:
     dfa = tokenset(name)
     return [dfa.kind_id(n) for n in discarded_names(name)]
+
+
+FRAME = 0x1E   # ASCII RECORD SEPARATOR, reserved for framing at the producer (Section 7.1)
+
+
+def framed(dfa: DFA, frame_byte: int = FRAME) -> DFA:
+    """``dfa`` with ``frame_byte`` given a rule of its own: a new kind
+    ("frame", numbered n_kinds) of that one byte from q0, and no transition on
+    the byte from any other state, so no other token admits it."""
+    import numpy as np
+    from .automaton import dfa_from_full_table, UNDEF
+    d = dfa.delta_full().astype(np.int64)
+    n = dfa.n_states
+    d[:, frame_byte] = UNDEF
+    d[dfa.q0, frame_byte] = n
+    d = np.vstack([d, np.full((1, 256), UNDEF, np.int64)])
+    acc = list(dfa.accept.tolist()) + [dfa.n_kinds]
+    names = list(dfa.kind_names) + ["frame"]
+    return dfa_from_full_table(d.tolist(), acc, dfa.q0, names)

@@ -53,11 +53,11 @@ LX_FILTERED_MODULO = 2
 
 # every function declared in include/lexgpu.h
 EXPORTED = (
-    "lx_compile_tokenset", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_class_table",
-    "lx_tokenset_scan_table",
+    "lx_compile_tokenset", "lx_compile_tokenset_framed", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_class_table",
+    "lx_tokenset_walk_table", "lx_tokenset_scan_table",
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
-    "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold",
+    "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold", "lx_ctx_set_kernel",
     "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative", "lx_chunk_contexts",
     "lx_lex_speculative", "lx_model_create", "lx_model_free", "lx_model_info", "lx_model_get_params",
     "lx_model_set_params", "lx_model_windows", "lx_model_forward", "lx_model_gradient", "lx_model_train_step",
@@ -105,10 +105,12 @@ def load_library(path: Optional[str] = None):
         vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
         sig = {
             "lx_compile_tokenset": (i32, [vp, vp, u32, vp]),
+            "lx_compile_tokenset_framed": (i32, [vp, vp, u32, u32, i32, vp]),
             "lx_certificates": (i32, [vp, vp, vp]),
             "lx_tokenset_info": (i32, [vp, i32, vp, vp, vp, vp, vp]),
             "lx_tokenset_table": (i32, [vp, i32, vp, u32, vp, u32]),
             "lx_tokenset_class_table": (i32, [vp, i32, vp, u32, vp, u32]),
+            "lx_tokenset_walk_table": (i32, [vp, i32, vp, u32, vp, u32]),
             "lx_tokenset_scan_table": (i32, [vp, vp, u32, vp, u32]),
             "lx_tokenset_free": (None, [vp]),
             "lx_ctx_create": (i32, [vp]),
@@ -118,6 +120,7 @@ def load_library(path: Optional[str] = None):
             "lx_ctx_last_kernel_ms": (i32, [vp, vp]),
             "lx_ctx_set_config": (i32, [vp, vp, i32, u32, u32, u32]),
             "lx_ctx_debug_withhold": (i32, [vp, u32]),
+            "lx_ctx_set_kernel": (i32, [vp, i32]),
             "lx_ctx_get_config": (i32, [vp, vp, i32, vp, vp, vp, vp]),
             "lx_autotune": (i32, [vp, vp, i32, vp, u64, vp, vp, u64, vp]),
             "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
@@ -198,6 +201,29 @@ def lx_compile_tokenset(dfa, discarded: Sequence[int] = ()) -> Tokenset:
     return Tokenset(out.value, n_kinds)
 
 
+def lx_compile_tokenset_framed(dfa, discarded: Sequence[int] = (), frame_byte: int = 0x1E,
+                               frame_discarded: bool = False) -> Tokenset:
+    """The token set of ``dfa`` with ``frame_byte`` reserved for framing at the
+    producer: a kind of its own (numbered dfa.n_kinds), rejected inside every
+    other token."""
+    lib = load_library()
+    nxt = np.ascontiguousarray(dfa.next, dtype=np.int64)
+    n_classes, n_states = nxt.shape
+    nxt32 = np.where(nxt < 0, LX_NONE, nxt).astype(np.uint32)
+    acc = np.ascontiguousarray(dfa.accept, dtype=np.int64)
+    acc16 = np.where(acc < 0, LX_NO_KIND, acc).astype(np.uint16)
+    cls = np.ascontiguousarray(dfa.byte_class, dtype=np.uint8)
+    n_kinds = int(getattr(dfa, "n_kinds", 0) or (int(acc.max()) + 1))
+    d = _Dfa(n_states, n_classes, int(dfa.q0), n_kinds, cls.ctypes.data, nxt32.ctypes.data, acc16.ctypes.data)
+    disc = np.ascontiguousarray(list(discarded), dtype=np.uint16)
+    out = ctypes.c_void_p()
+    rc = lib.lx_compile_tokenset_framed(ctypes.byref(d), disc.ctypes.data if disc.size else None, int(disc.size),
+                                        int(frame_byte), 1 if frame_discarded else 0, ctypes.byref(out))
+    if rc != LX_OK:
+        raise LexError(rc, "lx_compile_tokenset_framed")
+    return Tokenset(out.value, n_kinds + 1)
+
+
 def _mask_to_bytes(words) -> np.ndarray:
     w = np.array(words, dtype=np.uint32)
     return np.array([(w[b >> 5] >> (b & 31)) & 1 for b in range(256)], dtype=bool)
@@ -241,6 +267,17 @@ def lx_tokenset_table(ts: Tokenset, mode: int, class_table: bool = False) -> Tup
     return rc, blob[:meta[0]], info
 
 
+def lx_tokenset_walk_table(ts: Tokenset, mode: int) -> Tuple[int, np.ndarray, dict]:
+    """The event-code walk table of ``mode`` (status, blob, layout)."""
+    lib = load_library()
+    meta = (ctypes.c_uint32 * 10)()
+    lib.lx_tokenset_walk_table(ts.handle, int(mode), None, 0, meta, 10)
+    blob = np.zeros(max(int(meta[0]), 1), np.uint8)
+    rc = lib.lx_tokenset_walk_table(ts.handle, int(mode), blob.ctypes.data, int(blob.size), meta, 10)
+    keys = ("bytes", "form", "n_rows", "row_shift", "p_start", "p_pre", "acc_off", "kmap_off", "cmap_off", "cut_off")
+    return rc, blob[:int(meta[0])], dict(zip(keys, [int(x) for x in meta]))
+
+
 def lx_ctx_create() -> Ctx:
     lib = load_library()
     out = ctypes.c_void_p()
@@ -252,6 +289,15 @@ def lx_ctx_create() -> Ctx:
 
 def lx_ctx_set_timeout_ms(ctx: Ctx, ms: int) -> int:
     return load_library().lx_ctx_set_timeout_ms(ctx.handle, int(ms))
+
+
+LX_KERNEL_AUTO, LX_KERNEL_TILE, LX_KERNEL_WARP = 0, 1, 2
+
+
+def lx_ctx_set_kernel(ctx: Ctx, kernel: int) -> int:
+    """Which kernel lx_lex uses: LX_KERNEL_AUTO (warp-tile kernel where it
+    applies), LX_KERNEL_TILE or LX_KERNEL_WARP."""
+    return load_library().lx_ctx_set_kernel(ctx.handle, int(kernel))
 
 
 def lx_ctx_enable_timing(ctx: Ctx, on: bool = True) -> int:
@@ -436,7 +482,7 @@ def lx_chunk_contexts(ctx: Ctx, ts: Tokenset, d_in, n: Optional[int] = None, str
 
 class _SpecStats(ctypes.Structure):
     _fields_ = [("chunks", ctypes.c_uint64), ("rounds", ctypes.c_uint32), ("rescanned", ctypes.c_uint32),
-                ("mispredicted_first", ctypes.c_uint64)]
+                ("judged", ctypes.c_uint64)]
 
 
 class Model:
@@ -526,7 +572,8 @@ def lx_lex_speculative(ctx: Ctx, ts: Tokenset, model: Optional[Model], d_in, mod
     rc = lib.lx_lex_speculative(ctx.handle, ts.handle, model.handle if model is not None else None,
                                 d_in.data_ptr(), n, int(mode), d_kinds.data_ptr(), d_lens.data_ptr(), cap,
                                 ctypes.byref(nt), ctypes.byref(con), ctypes.byref(st), _stream_handle(stream))
-    return rc, nt.value, con.value, {"chunks": st.chunks, "rounds": st.rounds, "rescanned": st.rescanned}
+    return rc, nt.value, con.value, {"chunks": st.chunks, "rounds": st.rounds, "rescanned": st.rescanned,
+                                   "judged": bool(st.judged)}
 
 
 def context_training_set(ctx: Ctx, ts: Tokenset, model: Model, d_in, stream=None):

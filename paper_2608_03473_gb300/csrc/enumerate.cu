@@ -43,6 +43,7 @@ constexpr int EN_NT = 256;             // threads of the plan / enumerate / emit
 constexpr int RS_NT = 1024;            // threads of the resolve kernel
 constexpr int SO_NT = 1024;            // threads of the offset kernels (one chunk each)
 constexpr uint32_t R1 = 16;            // chunks per run of the resolve kernels
+constexpr uint32_t SPEC_ROUNDS = 4;    // speculative rounds before the enumerative judge
 constexpr uint64_t NOPOS64 = ~0ull;
 constexpr uint32_t NONE32_EN = 0xFFFFFFFFu;
 constexpr uint16_t CTX_B = 0xFFFEu;    // context: at a token boundary
@@ -98,6 +99,7 @@ struct EnParams {
     uint8_t *dirty;              // [M] chunk to (re)scan from ctx
     unsigned int *changed;       // a fix-up round changed some ctx
     unsigned int *rescans;       // chunks scanned again after the first round
+    unsigned int *rounds_used;   // fix-up rounds that changed some entry
     const uint16_t *guess;       // [M] predicted entry contexts (nullptr: BOUNDARY)
     uint16_t *st_kinds;          // [n] a chunk's kept tokens from its latest scan, at its start offset
     uint32_t *st_lens;           // [n]
@@ -704,6 +706,38 @@ __global__ void __launch_bounds__(EN_NT) sp_fix(EnParams P)
     }
 }
 
+// Counts the rounds whose fix-up changed some entry (one thread).
+__global__ void sp_count(EnParams P)
+{
+    if (*P.changed) atomicAdd(P.rounds_used, 1u);
+}
+
+// The judge: after a full enumeration (en_enumerate .. en_label) every live
+// chunk takes its true entry context.  A chunk whose latest speculative scan
+// already ran from it keeps that scan (its staged tokens are valid; its
+// result, which the enumeration overwrote in slot 0, is copied back from the
+// slot of that candidate); every other live chunk is marked for one more scan.
+__global__ void __launch_bounds__(EN_NT) jd_apply(EnParams P)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const ScanEnv E = stage_scan(P, smem);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P.M; j += gridDim.x * blockDim.x) {
+        if (P.start[j] == NOPOS64) continue;
+        const ChunkOut o = P.out[j];
+        if (!o.live) {
+            P.dirty[j] = 0;
+            continue;
+        }
+        if (P.dirty[j] || P.ctx[j] != o.entry) {
+            P.ctx[j] = o.entry;
+            P.dirty[j] = 1;
+        } else {
+            const int ki = cand_index(E, P.cinfo[j] >> 8, o.entry);
+            if (ki > 0) P.res[(size_t)j * KMAX] = P.res[(size_t)j * KMAX + ki];
+        }
+    }
+}
+
 // Chunk starts and their true entry contexts (after en_label), per target.
 __global__ void __launch_bounds__(EN_NT) ctx_export(EnParams P, uint64_t *starts, uint16_t *ctx)
 {
@@ -939,6 +973,7 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     P.dirty = d + o_dirty;
     P.changed = reinterpret_cast<unsigned int *>(d + o_flags);
     P.rescans = reinterpret_cast<unsigned int *>(d + o_flags + 4);
+    P.rounds_used = reinterpret_cast<unsigned int *>(d + o_flags + 8);
     P.guess = nullptr;
     P.st_kinds = stage ? reinterpret_cast<uint16_t *>(d + o_stk) : nullptr;
     P.st_lens = stage ? reinterpret_cast<uint32_t *>(d + o_stl) : nullptr;
@@ -960,6 +995,7 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
         if (cudaFuncSetAttribute(en_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(en_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(en_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+            cudaFuncSetAttribute(jd_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(sp_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(en_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
             cudaFuncSetAttribute(en_label, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
@@ -975,6 +1011,8 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
 }
 
 // Read back the record: status, token count and con(w).
+// rescans (optional): chunks scanned again after the first round, then the
+// fix-up rounds that changed some entry (two words).
 int en_finish(lx_ctx *c, const EnRun &R, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed,
               unsigned int *rescans = nullptr)
 {
@@ -982,7 +1020,7 @@ int en_finish(lx_ctx *c, const EnRun &R, uint64_t capacity, uint64_t *n_tokens, 
     if (rc != LX_OK) return rc;
     uint8_t buf[256];
     rc = cuda_err(cudaMemcpyAsync(c->h_res, R.P.rec, sizeof(EnResult), cudaMemcpyDeviceToHost, R.s));
-    if (rc == LX_OK && rescans) rc = cuda_err(cudaMemcpyAsync(rescans, R.P.rescans, 4, cudaMemcpyDeviceToHost, R.s));
+    if (rc == LX_OK && rescans) rc = cuda_err(cudaMemcpyAsync(rescans, R.P.rescans, 8, cudaMemcpyDeviceToHost, R.s));
     if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(R.s));
     if (rc != LX_OK) return rc;
     std::memcpy(buf, c->h_res, sizeof(EnResult));
@@ -1059,18 +1097,31 @@ extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *mo
         R.P.guess = R.guess_buf;
     }
     sp_init<<<R.grid, EN_NT, 0, R.s>>>(R.P);
-    unsigned int *h_flag = static_cast<unsigned int *>(c->h_res);
-    uint32_t rounds = 0;
-    for (;; rounds++) {
-        sp_scan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P, rounds);
+    // SPEC_ROUNDS rounds back to back on the device (a round with nothing
+    // to rescan costs two short launches), one read-back; what is still
+    // unsettled then goes to the judge
+    for (uint32_t r = 0; r < SPEC_ROUNDS; r++) {
+        sp_scan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P, r);
         rc = cuda_err(cudaMemsetAsync(R.P.changed, 0, 4, R.s));
         if (rc != LX_OK) return rc;
         sp_fix<<<R.grid, EN_NT, 0, R.s>>>(R.P);
-        rc = cuda_err(cudaMemcpyAsync(h_flag, R.P.changed, 4, cudaMemcpyDeviceToHost, R.s));
-        if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(R.s));
-        if (rc != LX_OK) return rc;
-        if (*h_flag == 0) break;
-        if (rounds > R.P.M + 1) return LX_E_CUDA;   // cannot happen: every round settles one more chunk
+        sp_count<<<1, 1, 0, R.s>>>(R.P);
+    }
+    unsigned int *h_flag = static_cast<unsigned int *>(c->h_res);
+    rc = cuda_err(cudaMemcpyAsync(h_flag, R.P.changed, 4, cudaMemcpyDeviceToHost, R.s));
+    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(R.s));
+    if (rc != LX_OK) return rc;
+    const bool judged = *h_flag != 0;
+    if (judged) {
+        // the enumerative scan of every chunk from every candidate context
+        // settles all chains at once; one more round rescans the chunks whose
+        // true entry differs from their latest scan
+        en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
+        en_sum<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
+        en_link<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+        en_label<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
+        jd_apply<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+        sp_scan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P, SPEC_ROUNDS);
     }
     const uint32_t nb = (R.P.M + SO_NT - 1) / SO_NT;
     so_block<<<nb, SO_NT, 0, R.s>>>(R.P);
@@ -1078,13 +1129,13 @@ extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *mo
     so_out<<<nb, SO_NT, 0, R.s>>>(R.P);
     sp_copy<<<R.grid * (EN_NT / 32), EN_NT, 0, R.s>>>(R.P);
     if (c->timing) cudaEventRecord(c->ev[1], R.s);
-    unsigned int rescans = 0;
-    rc = en_finish(c, R, capacity, n_tokens, consumed, &rescans);
+    unsigned int rr[2] = {0, 0};
+    rc = en_finish(c, R, capacity, n_tokens, consumed, rr);
     if (stats) {
         stats->chunks = R.P.M;
-        stats->rounds = rounds + 1;
-        stats->rescanned = rescans;
-        stats->mispredicted_first = 0;
+        stats->rounds = 1 + rr[1];
+        stats->rescanned = rr[0];
+        stats->judged = judged ? 1u : 0u;
     }
     return rc;
 }

@@ -82,11 +82,41 @@ struct ScanTable {
 constexpr uint16_t SCAN_NONE = 0xFFFFu;
 constexpr uint16_t SCAN_ACCEPT = 0x8000u;   // next-state flag: the target state accepts
 
+// ---------------------------------------------------------------------------
+// Event-code walk tables (the warp-tile kernel, lexwarp.cu).
+//
+// The same scanner as above, with the token end carried by the transition
+// itself: every entry is the 16-bit shared address of the target row with
+// the EVENT CODE of the transition in bits 1..7 (rows start on 512- or
+// 256-byte boundaries, so those bits are free).  Code 0: no token ended
+// before this byte; 1: a discarded token ended; 2..127: a kept token of kind
+// kind_map[code] ended.  Rows: SLOW (0), R[0..S-1], START, PRE; no E rows.
+//   byte-indexed:  512-byte rows, entry of byte b at row + 2b, so the next
+//                  address is (entry & ~0x1FE) | (b << 1): one LOP3;
+//   class-indexed: 256-byte rows, entry of class c at row + 2c (C <= 127),
+//                  with a 256-byte map cmap2[b] = 2 class(b) on a 256-byte
+//                  boundary, so the map address is one PRMT and the next
+//                  address (entry & ~0xFF) | cmap2[b]: one LOP3.
+// Blob: [rows][acc u8 per row][kind_map u16 x 128][cmap2 u8 x 256][cut u8 x 256].
+// acc[r] is 2 * the code of the kind row r accepts (0: not accepting).
+// ---------------------------------------------------------------------------
+constexpr uint32_t WALK_CODES = 128;   // codes 0..127: at most 126 kept kinds
+struct WalkTable {
+    int status = LX_E_TOOBIG;
+    int form = FORM_BYTE;
+    uint32_t n_rows = 0, row_shift = 9, rows_bytes = 0;
+    uint32_t p_start = 0, p_pre = 0;      // relative row addresses (SLOW is 0)
+    uint32_t acc_off = 0, kmap_off = 0, cmap_off = 0, cut_off = 0;
+    uint32_t n_kept = 0;                  // kept kinds (codes 2 .. n_kept + 1)
+    std::vector<uint8_t> blob;
+};
+
 struct DeviceTables {
     int device = -1;
     void *d_blob[3] = {nullptr, nullptr, nullptr};
     void *d_blob_cls[3] = {nullptr, nullptr, nullptr};
     void *d_scan = nullptr;
+    void *d_walk[3] = {nullptr, nullptr, nullptr};
 };
 
 }  // namespace lx
@@ -103,6 +133,7 @@ struct lx_tokenset {
     lx::HostTable tab[3];       // per mode: byte-indexed when it fits, else class-indexed
     lx::HostTable tab_cls[3];   // per mode: class-indexed (only when tab[m] is byte-indexed)
     lx::ScanTable scan;
+    lx::WalkTable walk[3];      // per mode: event-code walk table (LX_E_TOOBIG when it does not fit)
     std::mutex mu;
     std::vector<lx::DeviceTables> dev;
 };

@@ -32,6 +32,7 @@
 #include <cstring>
 #include <new>
 
+#include "devutil.cuh"
 #include "internal.h"
 #include "runtime.h"
 
@@ -53,9 +54,6 @@ constexpr uint32_t NONE32 = 0xFFFFFFFFu;
 constexpr unsigned ERR_TIMEOUT = 1u;
 constexpr unsigned ERR_SMEM = 2u;
 
-constexpr unsigned long long ST_AGG = 1ull << 62;
-constexpr unsigned long long ST_INCL = 2ull << 62;
-constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 
 // One launch's record.  With a single document it is also that document's
 // record (the first three fields are laid out as in DocResult).
@@ -148,51 +146,7 @@ constexpr uint32_t M_PDOC = 200;    // u32: pending tile's document
 constexpr uint32_t M_PFIRST = 204;  // u32: pending tile is its document's first
 constexpr uint32_t M_TREF = 208;    // TileRef of the claimed tile (40 bytes)
 
-// ---- PTX helpers ----
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint32_t lds_u8(uint32_t a)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ uint32_t lds_u16(uint32_t a)
-{
-    unsigned short v;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v)
-{
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint64_t globaltimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Status words carry a flag and a count in one 64-bit store; nothing else a
-// predecessor wrote is read, so relaxed gpu-scope accesses suffice.
-__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_status(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
+// ---- PTX helpers (shared ones in devutil.cuh) ----
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
@@ -637,70 +591,17 @@ __device__ __forceinline__ int lockstep_walk(const Env &E, bool has, uint32_t st
     return st;
 }
 
-// Decoupled look-back, one warp.  Each tile first publishes its aggregate
-// (tile 0 its inclusive prefix) without waiting; later, one warp resolves
-// the exclusive prefix: each round its 32 lanes read 32 predecessor status
-// words at once, the round ends at the nearest inclusive prefix (summing the
-// aggregates before it) or, with none, adds all 32 aggregates and moves 32
-// tiles back.  A lane that sees an unpublished word before the nearest
-// inclusive prefix makes the round repeat, bounded by the time budget.
+// Decoupled look-back (devutil.cuh): each tile first publishes its
+// aggregate (tile 0 its inclusive prefix) without waiting; later one warp
+// resolves the exclusive prefix.
 __device__ __forceinline__ void publish_aggregate(const Params &P, uint32_t tile, uint64_t agg)
 {
     st_status(&P.status[tile], (tile == 0 ? ST_INCL : ST_AGG) | agg);
 }
 
-constexpr int LB_PER_LANE = 8;   // predecessor words per lane and round: 256 tiles per round
-
-__device__ uint64_t resolve_prefix(const Params &P, uint32_t tile, uint64_t agg, bool &timed_out)
+__device__ __forceinline__ uint64_t resolve_prefix(const Params &P, uint32_t tile, uint64_t agg, bool &timed_out)
 {
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) return 0;
-    uint64_t G = 0;
-    int64_t base = (int64_t)tile - 1;
-    uint64_t t0 = globaltimer();
-    uint32_t spins = 0;
-    for (;;) {
-        // lane l covers tiles base - 8l - j, j = 0..7 (descending)
-        unsigned long long v[LB_PER_LANE];
-#pragma unroll
-        for (int j = 0; j < LB_PER_LANE; j++) {
-            const int64_t k = base - (int64_t)LB_PER_LANE * lane - j;
-            v[j] = k >= 0 ? ld_status(&P.status[k]) : ST_INCL;
-        }
-        int jstar = LB_PER_LANE;   // first inclusive word of this lane
-        bool zero_before = false;
-        unsigned long long lsum = 0;
-#pragma unroll
-        for (int j = 0; j < LB_PER_LANE; j++) {
-            if (jstar == LB_PER_LANE) {
-                const unsigned long long f = v[j] & ~ST_VAL;
-                if (f == 0) zero_before = true;
-                lsum += v[j] & ST_VAL;
-                if (f == ST_INCL) jstar = j;
-            }
-        }
-        const unsigned incl = __ballot_sync(0xffffffffu, jstar < LB_PER_LANE);
-        const unsigned zero = __ballot_sync(0xffffffffu, zero_before);
-        const unsigned upto = incl ? (incl & (0u - incl)) : 0u;            // lowest lane holding one
-        const unsigned lanes = incl ? ((upto - 1u) | upto) : 0xffffffffu;  // lanes to sum
-        if (zero & lanes) {
-            // bounded: the time budget, or another CTA already gave up
-            if ((++spins & 15) == 0 &&
-                (globaltimer() - t0 > P.timeout_ns || *(volatile unsigned int *)&P.res->error != 0)) {
-                timed_out = true;
-                break;
-            }
-            __nanosleep(32);
-            continue;
-        }
-        unsigned long long x = ((lanes >> lane) & 1u) ? lsum : 0ull;
-        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        G += x;
-        if (incl) break;
-        base -= 32 * LB_PER_LANE;
-    }
-    if (lane == 0 && tile != P.withhold) st_status(&P.status[tile], ST_INCL | (G + agg));
-    return G;
+    return lookback(P.status, tile, agg, P.timeout_ns, &P.res->error, P.withhold, timed_out);
 }
 
 // Where global tile g of a launch lies: its document and the document-relative
@@ -1130,10 +1031,13 @@ int lx::ensure_device_tables(const lx_tokenset *cts, int device, DeviceTables *o
             rc = upload(ts->tab_cls[m].blob, &dt.d_blob_cls[m]);
     }
     if (rc == LX_OK && ts->scan.status == LX_OK) rc = upload(ts->scan.blob, &dt.d_scan);
+    for (int m = 0; m < 3 && rc == LX_OK; m++)
+        if (ts->walk[m].status == LX_OK) rc = upload(ts->walk[m].blob, &dt.d_walk[m]);
     if (rc != LX_OK) {
         for (int m = 0; m < 3; m++) {
             if (dt.d_blob[m]) cudaFree(dt.d_blob[m]);
             if (dt.d_blob_cls[m]) cudaFree(dt.d_blob_cls[m]);
+            if (dt.d_walk[m]) cudaFree(dt.d_walk[m]);
         }
         if (dt.d_scan) cudaFree(dt.d_scan);
         return rc;
@@ -1153,6 +1057,7 @@ extern "C" void lx_tokenset_free(lx_tokenset *ts)
         for (int m = 0; m < 3; m++) {
             if (d.d_blob[m]) cudaFree(d.d_blob[m]);
             if (d.d_blob_cls[m]) cudaFree(d.d_blob_cls[m]);
+            if (d.d_walk[m]) cudaFree(d.d_walk[m]);
         }
         if (d.d_scan) cudaFree(d.d_scan);
     }
@@ -1219,6 +1124,13 @@ extern "C" int lx_ctx_last_kernel_ms(lx_ctx *c, float *ms)
 {
     if (!c || !ms || !c->ev[0]) return LX_E_INVAL;
     return cuda_err(cudaEventElapsedTime(ms, c->ev[0], c->ev[1]));
+}
+
+extern "C" int lx_ctx_set_kernel(lx_ctx *c, int kernel)
+{
+    if (!c || kernel < LX_KERNEL_AUTO || kernel > LX_KERNEL_WARP) return LX_E_INVAL;
+    c->kernel = kernel;
+    return LX_OK;
 }
 
 extern "C" int lx_ctx_debug_withhold(lx_ctx *c, uint32_t tile)
@@ -1353,11 +1265,39 @@ static int grid_for(lx_ctx *c, int form, uint32_t smem, const LaunchCfg &g, uint
     return LX_OK;
 }
 
+// A chunk the warp-tile kernel walks byte by byte beyond this length makes
+// lx_lex switch to the enumerative path.
+constexpr uint64_t SPARSE_LIMIT = 32 * 1024;
+
+// Whether the mode's cut set (useful exact certificate for the exact modes,
+// modulo-I certificate for LX_FILTERED_MODULO) holds any byte.
+static bool mode_has_cuts(const lx_tokenset *ts, int mode)
+{
+    const uint32_t *m = mode == LX_FILTERED_MODULO ? ts->modulo : ts->exact;
+    for (int i = 0; i < 8; i++)
+        if (m[i]) return true;
+    return false;
+}
+
 // Launch the tile kernel and read back its result record.
 static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
                       uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
                       uint64_t *consumed, cudaStream_t st, const LaunchCfg *force = nullptr)
 {
+    // Hybrid plan (Section 9): certified cuts where certified bytes occur;
+    // where the mode certifies no byte, or certified bytes turn out too far
+    // apart, entry contexts are enumerated instead (lx_lex_enumerative), so
+    // no call degenerates to one lane walking the input.
+    const bool can_enumerate = !force && c->kernel == LX_KERNEL_AUTO && ts->scan.status == LX_OK;
+    if (can_enumerate && !mode_has_cuts(ts, mode))
+        return lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st);
+    if (!force && c->kernel != LX_KERNEL_TILE && warp_path_ok(ts, mode, d_in)) {
+        const int rc = lex_warp_device(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st,
+                                       can_enumerate ? SPARSE_LIMIT : 0);
+        if (rc != LX_SPARSE) return rc;
+        return lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st);
+    }
+    if (!force && c->kernel == LX_KERNEL_WARP && n) return LX_E_INVAL;   // asked for, not available here
     if (ts->tab[mode].status != LX_OK) return ts->tab[mode].status;
     const LaunchCfg g = force ? *force : config_for(c, ts, mode);
     const HostTable &h = table_for(ts, mode, g);
@@ -1521,6 +1461,24 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
     uint32_t *d_lens = static_cast<uint32_t *>(c->d_out);
     uint16_t *d_kinds = reinterpret_cast<uint16_t *>(d_lens + capacity);
     const uint8_t *d_in = static_cast<const uint8_t *>(c->d_in);
+    cudaStream_t st0 = static_cast<cudaStream_t>(stream);
+    if (c->kernel == LX_KERNEL_AUTO && ts->scan.status == LX_OK && !mode_has_cuts(ts, mode)) {
+        // no certified byte: the whole input in, the enumerative path, the tokens out
+        rc = cuda_err(cudaMemcpyAsync(c->d_in, h_in, n, cudaMemcpyHostToDevice, st0));
+        if (rc != LX_OK) return rc;
+        uint64_t nt = 0, con = 0;
+        rc = lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, &nt, &con, stream);
+        if (rc != LX_OK && rc != LX_E_CAPACITY) return rc;
+        const uint64_t m = std::min(nt, capacity);
+        int r2 = LX_OK;
+        if (m) r2 = cuda_err(cudaMemcpyAsync(h_kinds, d_kinds, 2 * m, cudaMemcpyDeviceToHost, st0));
+        if (m && r2 == LX_OK) r2 = cuda_err(cudaMemcpyAsync(h_lens, d_lens, 4 * m, cudaMemcpyDeviceToHost, st0));
+        if (r2 == LX_OK) r2 = cuda_err(cudaStreamSynchronize(st0));
+        if (r2 != LX_OK) return r2;
+        *n_tokens = nt;
+        *consumed = con;
+        return rc;
+    }
 
     const std::vector<uint64_t> b = host_pieces(h, h_in, n);
     const uint32_t K = (uint32_t)b.size() - 1;

@@ -1,0 +1,965 @@
+// lexwarp.cu -- GB300 (sm_103a) certified-split lexing with warp-owned tiles:
+// the default kernel of lx_lex for token sets with an event-code walk table
+// (internal.h) and 16-byte aligned inputs.
+//
+// Every warp claims tiles of WT input bytes from a global counter and owns
+// them end to end; nothing but the one-time table staging synchronises the
+// CTA.  Per tile:
+//   (a) halo scan: the 32 lanes find the first certified byte at or past the
+//       tile end (the end of the tile's last chunk), 128 bytes per round;
+//   (b) walk, phase 1: lane i starts its SLICE-byte slice in the PRE row,
+//       which absorbs bytes until the first certified byte of the slice
+//       (the planner of Section 6 with one target per lane: the chunk start)
+//       and from there runs the longest-match scanner of Section 3 with every
+//       certified byte ending the token in progress.  Lanes step 16-byte
+//       blocks read from global memory (four bytes per shared-memory lookup
+//       chain); each table entry carries the event code of its transition,
+//       so four codes per word are packed with PRMT and stored at their
+//       positions in the warp's event buffer;
+//   (c) walk, phase 2: a warp suffix minimum gives each lane its chunk end
+//       (the next lane's chunk start, or the halo's certified byte); lanes
+//       run on to it, storing nothing past it, so each position has exactly
+//       one writer.  SLOW (no transition and no accept) replays the token
+//       from q0 to its last accepting position (longest match with
+//       backtracking) and re-walks from there;
+//   (d) count: each lane counts the kept codes of a contiguous slice of the
+//       event buffer; the warp publishes the tile's count for a two-level
+//       decoupled look-back (tiles within groups of GS, groups);
+//   (e) emit: each lane turns its events into (kind, length) pairs in a
+//       shared stage; the warp resolves the tile's output offset after its
+//       next tile's walk (its predecessors have published by then) and copies
+//       the stage to the output with coalesced stores.  The first lexing
+//       failure (Corollary 1) truncates the count.
+// A chunk whose end is not in the halo is walked byte by byte by lane 0 from
+// global memory (counted, then emitted after the look-back).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "devutil.cuh"
+#include "internal.h"
+#include "runtime.h"
+
+namespace lx {
+namespace {
+
+constexpr uint32_t WT = 4096;                 // input bytes per warp tile
+constexpr uint32_t SLICE = WT / 32;           // bytes per lane slice (phase 1)
+constexpr uint32_t BLK = 16;                  // bytes per lockstep step of a lane
+constexpr uint32_t NB1 = SLICE / BLK;         // phase-1 steps
+constexpr uint32_t HALO = 1024;               // positions past the tile a chunk may end at
+constexpr uint32_t EVB = WT + HALO;           // event buffer positions
+constexpr uint32_t LIMIT = EVB - BLK;         // chunk ends must lie below (room for the last block)
+// Event code of position p at ev + p + 4 (p >> 7): a 4-byte pad after every
+// 128 positions, so the 32 lanes' phase-1 stores (slices 128 positions
+// apart) fall in 32 different banks.
+constexpr uint32_t EV_BYTES = ((EVB + 16 + 4 * ((EVB + 16) / 128 + 1)) + 15) / 16 * 16;
+constexpr uint32_t STAGE_CAP = 1024;          // kept tokens per tile staged for coalesced writes
+constexpr uint32_t WAREA = EV_BYTES + 4 * STAGE_CAP;   // shared bytes per warp
+constexpr uint32_t GS = 64;                   // tiles per look-back group
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t BIG = 0x7FFFFFFFu;
+constexpr int NWARPS = 16;
+constexpr int NTHREADS = 32 * NWARPS;
+constexpr unsigned ERR_TIMEOUT = 1u;
+constexpr unsigned ERR_SMEM = 2u;
+constexpr unsigned ERR_SPARSE = 4u;   // a chunk ran past the sparse limit: certified bytes too far apart
+
+static_assert(SLICE % BLK == 0 && WAREA % 16 == 0, "geometry");
+
+struct WResult {
+    unsigned long long total;          // kept tokens over all tiles
+    unsigned long long inv_fail_pos;   // ~min failure offset (atomicMax), 0 = none
+    unsigned long long inv_fail_tok;   // ~output index at that failure
+    unsigned int error;
+    unsigned int pad;
+};
+
+struct WParams {
+    const uint8_t *in;
+    uint64_t n;
+    const uint8_t *blob;
+    uint32_t blob_bytes, rows_bytes, row_shift;
+    uint32_t p_start, p_pre, acc_off, kmap_off, cmap_off, cut_off;
+    uint16_t *out_kinds;
+    uint32_t *out_lens;
+    uint64_t cap;
+    unsigned long long *status;    // per tile: ST_AGG | kept count
+    unsigned long long *gstatus;   // per group of GS tiles: ST_AGG | group count, or ST_INCL | inclusive prefix
+    unsigned int *gdone;           // per group: tiles that have published
+    unsigned int *tile_counter;
+    WResult *res;
+    uint32_t n_tiles;
+    uint64_t timeout_ns;
+    uint32_t withhold;
+    uint64_t sparse_limit;   // longest chunk walked byte by byte before giving up (0: no limit)
+};
+
+// Shared addresses of the tables and of this warp's buffers, and the tile.
+struct WEnv {
+    uint32_t P_start, P_pre, P_slow;
+    uint32_t tb_s, acc_s, kmap_s, cmap_s, cut_s, shift;
+    uint32_t ev;                 // event buffer: code of position p at ev + p
+    const uint8_t *in;           // the tile's first byte
+    uint32_t nrel;               // input bytes from the tile start (clamped)
+    uint64_t nrel64;
+};
+
+__device__ __forceinline__ uint32_t eva(const WEnv &E, uint32_t p) { return E.ev + p + ((p >> 7) << 2); }
+
+__device__ __forceinline__ uint4 ldg16(const uint8_t *p)
+{
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// One byte step: the next entry (row address | code << 1).
+template <int FORM>
+__device__ __forceinline__ uint32_t wstep(const WEnv &E, uint32_t e, uint32_t b)
+{
+    const uint32_t a = FORM == FORM_BYTE ? ((e & ~0x1FEu) | (b << 1)) : ((e & ~0xFFu) | lds_u8(E.cmap_s + b));
+    return lds_u16(a);
+}
+
+__device__ __forceinline__ uint32_t acc_code(const WEnv &E, uint32_t e)
+{
+    return lds_u8(E.acc_s + ((e - E.tb_s) >> E.shift));
+}
+
+// Four byte steps over the little-endian word w as branch-free PTX; the
+// dependent chain per byte is one LOP3 and the table load (the class form
+// adds an independent PRMT and class-map load per byte).  The four event
+// codes (the low byte of each entry) are packed into one word and stored at
+// `ev` when the predicate holds: phase 1 (PH 1) stores a word that did not
+// begin in PRE (x = P_pre); phase 2 (PH 2) a word whose last byte y lies at
+// or before the chunk end x.  cm: the class map's shared address.
+#define LXW_PRED1 "setp.ne.u32 ps, %0, %3;\n\t"
+#define LXW_PRED2 "setp.le.u32 ps, %4, %3;\n\t"
+#define LXW_B(XOP, VIN, VOUT)                                                  \
+    XOP "lop3.b32 a, " VIN ", t, 0x1FE, 0xD8;\n\t"                             \
+        "ld.shared.u16 " VOUT ", [a];\n\t"
+#define LXW_C(SEL, VIN, VOUT)                                                  \
+    "prmt.b32 t, %2, %6, " SEL ";\n\t"                                         \
+    "ld.shared.u8 c, [t];\n\t"                                                 \
+    "lop3.b32 a, " VIN ", c, 0xFF, 0xD8;\n\t"                                  \
+    "ld.shared.u16 " VOUT ", [a];\n\t"
+#define LXW_PACK                                                               \
+    "prmt.b32 t0, v0, v1, 0x0040;\n\t"                                         \
+    "prmt.b32 t1, v2, v3, 0x0040;\n\t"                                         \
+    "prmt.b32 %1, t0, t1, 0x5410;\n\t"                                         \
+    "@ps st.shared.u32 [%5], %1;\n\t"                                          \
+    "mov.b32 %0, v3;\n\t}"
+#define LXW_BYTE_BODY                                                          \
+    LXW_B("shl.b32 t, %2, 1;\n\t", "%0", "v0")                                 \
+    LXW_B("shr.b32 t, %2, 7;\n\t", "v0", "v1")                                 \
+    LXW_B("shr.b32 t, %2, 15;\n\t", "v1", "v2")                                \
+    LXW_B("shr.b32 t, %2, 23;\n\t", "v2", "v3")
+#define LXW_CLASS_BODY                                                         \
+    LXW_C("0x7650", "%0", "v0")                                                \
+    LXW_C("0x7651", "v0", "v1")                                                \
+    LXW_C("0x7652", "v1", "v2")                                                \
+    LXW_C("0x7653", "v2", "v3")
+#define LXW_HEAD "{\n\t.reg .pred ps;\n\t.reg .b32 t, a, c, v0, v1, v2, v3, t0, t1;\n\t"
+
+template <int FORM, int PH>
+__device__ __forceinline__ uint32_t wword(uint32_t &e, uint32_t w, uint32_t ev, uint32_t x, uint32_t y, uint32_t cm)
+{
+    uint32_t pk;
+    if (FORM == FORM_BYTE && PH == 1)
+        asm volatile(LXW_HEAD LXW_PRED1 LXW_BYTE_BODY LXW_PACK
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+    else if (FORM == FORM_BYTE)
+        asm volatile(LXW_HEAD LXW_PRED2 LXW_BYTE_BODY LXW_PACK
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+    else if (PH == 1)
+        asm volatile(LXW_HEAD LXW_PRED1 LXW_CLASS_BODY LXW_PACK
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+    else
+        asm volatile(LXW_HEAD LXW_PRED2 LXW_CLASS_BODY LXW_PACK
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+    return pk;
+}
+
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, uint32_t k) { return (w >> (8 * k)) & 0xFFu; }
+
+__device__ __forceinline__ uint32_t pick4(uint32_t i, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    return i == 0 ? a : i == 1 ? b : i == 2 ? c : d;
+}
+
+// A lane's walk state.
+struct Lane {
+    uint32_t e;       // row entry after the last stepped byte
+    uint32_t p;       // next position to step
+    uint32_t s;       // chunk start (first certified byte of the slice), NONE while in PRE
+    uint32_t fail;    // failure offset (a token start with no accepting prefix), NONE
+    uint32_t own;     // positions below this may record a failure (the chunk end)
+    bool act;
+    bool coarse;      // s is the start of the block in which PRE was left, not yet the byte
+};
+
+// The block walk only notes the 16-byte block in which a lane left PRE; this
+// finds the byte (the first certified byte of the block) and stores the event
+// codes after it in its word, which the block step did not store (the word
+// began in PRE): the state after the certified byte is PRE's step on it.
+template <int FORM>
+__device__ void refine_start(const WEnv &E, Lane &L)
+{
+    if (!L.coarse) return;
+    L.coarse = false;
+    const uint32_t pb = L.s;
+    uint32_t j = 0;
+    while (j < BLK && !lds_u8(E.cut_s + __ldg(E.in + pb + j))) j++;
+    L.s = pb + j;
+    uint32_t e = wstep<FORM>(E, E.P_pre, __ldg(E.in + L.s));
+    for (uint32_t k = L.s + 1; k < ((L.s + 4) & ~3u); k++) {
+        e = wstep<FORM>(E, e, __ldg(E.in + k));
+        sts_u8(eva(E, k), e & 0xFFu);
+    }
+}
+
+// SLOW was reached before position `upto`: replay the token in progress from
+// q0 (its start is the last event at or before hi, or the chunk start) to
+// its last accepting position r, record the token end at r and re-walk from
+// r to `upto`, storing codes only at positions <= hi.  Repeats while the
+// re-walk falls into SLOW again at or before hi; a SLOW past hi belongs to
+// the next chunk and stops the lane.  No accepting prefix: a failure at the
+// token start (Corollary 1), recorded when it lies inside this chunk.
+template <int FORM>
+__device__ void slow_fix(const WEnv &E, Lane &L, uint32_t upto, uint32_t hi)
+{
+    refine_start<FORM>(E, L);
+    for (;;) {
+        uint32_t tok = L.s;
+        for (uint32_t j = min(upto - 1, hi); j > L.s; j--)
+            if (lds_u8(eva(E, j))) {
+                tok = j;
+                break;
+            }
+        uint32_t q = E.P_start, r = NONE, rc = 0;
+        for (uint32_t k = tok; k < upto; k++) {
+            const uint32_t v = wstep<FORM>(E, q, __ldg(E.in + k));
+            if ((v & 0xFFu) || v == E.P_slow) break;
+            q = v;
+            const uint32_t ac = acc_code(E, q);
+            if (ac) {
+                r = k + 1;
+                rc = ac;
+            }
+        }
+        if (r == NONE) {
+            if (tok < L.own) L.fail = tok;
+            L.act = false;
+            return;
+        }
+        if (r <= hi) sts_u8(eva(E, r), rc);
+        uint32_t e = E.P_start, kslow = NONE;
+        for (uint32_t k = r; k < upto; k++) {
+            const uint32_t v = wstep<FORM>(E, e, __ldg(E.in + k));
+            if (k > r && k <= hi) sts_u8(eva(E, k), v & 0xFFu);   // the step at r (from START) ends nothing
+            if (v == E.P_slow && e != E.P_slow) kslow = k;
+            e = v;
+        }
+        L.e = e;
+        if (e != E.P_slow) return;
+        if (kslow > hi || r > hi) {
+            L.act = false;
+            return;
+        }
+    }
+}
+
+// Byte steps from L.p up to `upto` with the storing rule of the block steps.
+template <int FORM>
+__device__ void scalar_steps(const WEnv &E, Lane &L, uint32_t upto, uint32_t hi)
+{
+    while (L.p < upto && L.act) {
+        const uint32_t k = L.p, e0 = L.e;
+        const uint32_t v = wstep<FORM>(E, e0, __ldg(E.in + k));
+        if (e0 == E.P_pre && v != E.P_pre && L.s == NONE) L.s = k;
+        if (e0 != E.P_pre && k <= hi) sts_u8(eva(E, k), v & 0xFFu);
+        L.e = v;
+        L.p = k + 1;
+        if (v == E.P_slow) {
+            if (k > hi) {
+                L.act = false;
+                return;
+            }
+            slow_fix<FORM>(E, L, k + 1, hi);
+        }
+    }
+}
+
+// At the end of the input: an accepting row ends its token there; a row
+// that does not accept backtracks like SLOW.
+template <int FORM>
+__device__ void finalize(const WEnv &E, Lane &L, uint32_t hi)
+{
+    if (E.nrel > hi) {
+        L.act = false;
+        return;
+    }
+    while (L.act) {
+        const uint32_t e = L.e;
+        if (e == E.P_start || e == E.P_pre) return;
+        if (e != E.P_slow) {
+            const uint32_t ac = acc_code(E, e);
+            if (ac) {
+                sts_u8(eva(E, E.nrel), ac);
+                return;
+            }
+            L.e = E.P_slow;
+        }
+        slow_fix<FORM>(E, L, E.nrel, hi);
+    }
+}
+
+// The chunk that starts at the certified byte `start` and leaves the halo,
+// walked byte by byte from global memory up to the first certified byte at
+// or past the tile end (or the end of the input).  Counts its kept tokens
+// and, with out != nullptr, writes them from output index `o`.  Returns the
+// kept count; *fail = the failure offset or NONE64.  With limit != 0 a
+// chunk longer than `limit` bytes stops there and sets *over.
+constexpr uint64_t NONE64 = ~0ull;
+
+template <int FORM>
+__device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail, uint16_t *kinds, uint32_t *lens,
+                                  uint64_t cap, uint64_t o, uint64_t limit = 0, bool *over = nullptr)
+{
+    const uint64_t n = E.nrel64;
+    uint64_t p = start, tok = start, cnt = 0;
+    uint32_t e = E.P_start;
+    *fail = NONE64;
+    const uint64_t stop = limit ? start + limit : ~0ull;
+    auto emit = [&](uint32_t code, uint64_t len) {
+        if (code < 4) return;
+        if (kinds && o + cnt < cap) {
+            kinds[o + cnt] = (uint16_t)lds_u16(E.kmap_s + 2 * (code >> 1));
+            lens[o + cnt] = (uint32_t)len;
+        }
+        cnt++;
+    };
+    for (;;) {
+        if (p == n) {
+            if (e == E.P_start) return cnt;
+            const uint32_t ac = e != E.P_slow ? acc_code(E, e) : 0u;
+            if (ac) {
+                emit(ac, p - tok);
+                return cnt;
+            }
+        } else {
+            if (p >= stop) {
+                *over = true;
+                return cnt;
+            }
+            const uint32_t b = __ldg(E.in + p);
+            const uint32_t v = wstep<FORM>(E, e, b);
+            if (v != E.P_slow) {
+                if (v & 0xFFu) {
+                    emit(v & 0xFFu, p - tok);
+                    tok = p;
+                    if (p >= WT && lds_u8(E.cut_s + b)) return cnt;
+                }
+                e = v;
+                p++;
+                continue;
+            }
+        }
+        // longest match with backtracking: replay [tok, p) from q0
+        uint32_t q = E.P_start, rc = 0;
+        uint64_t r = NONE64;
+        for (uint64_t k = tok; k < p; k++) {
+            const uint32_t v = wstep<FORM>(E, q, __ldg(E.in + k));
+            if ((v & 0xFFu) || v == E.P_slow) break;
+            q = v;
+            const uint32_t ac = acc_code(E, q);
+            if (ac) {
+                r = k + 1;
+                rc = ac;
+            }
+        }
+        if (r == NONE64) {
+            *fail = tok;
+            return cnt;
+        }
+        emit(rc, r - tok);
+        tok = p = r;
+        e = E.P_start;
+        if (r == n) return cnt;
+        if (r >= WT && lds_u8(E.cut_s + __ldg(E.in + r))) return cnt;
+    }
+}
+
+__device__ __forceinline__ uint32_t kept_mask(uint32_t w)   // bit 7 of every byte >= 4 (a kept code)
+{
+    return (((w | 0x80808080u) - 0x04040404u) | w) & 0x80808080u;
+}
+__device__ __forceinline__ uint32_t event_mask(uint32_t w)  // bit 7 of every nonzero byte
+{
+    return (((w | 0x80808080u) - 0x01010101u) | w) & 0x80808080u;
+}
+
+// ---- two-level decoupled look-back ----
+// Tiles form groups of GS.  A tile publishes its kept count (ST_AGG) and
+// counts itself into its group; the warp that completes a group sums the
+// group's counts and publishes the group aggregate (group 0: its inclusive
+// prefix).  A tile's output offset is the exclusive prefix of its group
+// (a look-back over group words, a few dozen deep) plus the counts of the
+// tiles before it in the group.  Every wait is bounded by the time budget
+// and ends early once another warp has given up.
+struct Waiter {
+    uint64_t t0;
+    uint32_t spins;
+    // false (and the error flag raised) once the budget is spent
+    __device__ bool again(const WParams &P)
+    {
+        if ((++spins & 15) == 0 &&
+            (globaltimer() - t0 > P.timeout_ns || *(volatile const unsigned int *)&P.res->error != 0)) {
+            if ((threadIdx.x & 31) == 0) atomicOr(&P.res->error, ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+        return true;
+    }
+};
+
+__device__ void publish_tile(const WParams &P, uint32_t tile, uint64_t agg)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t g = tile / GS, f = g * GS;
+    const uint32_t gsize = min(GS, P.n_tiles - f);
+    uint32_t last = 0;
+    if (lane == 0 && agg) atomicAdd(&P.res->total, agg);
+    if (lane == 0 && tile != P.withhold) {
+        st_status(&P.status[tile], ST_AGG | agg);
+        __threadfence();
+        last = atomicAdd(&P.gdone[g], 1u) + 1 == gsize ? 1u : 0u;
+        if (last) __threadfence();
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    // every tile of the group has published: its aggregate
+    unsigned long long x = 0;
+    for (uint32_t j = lane; j < gsize; j += 32) x += ld_status(&P.status[f + j]) & ST_VAL;
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) st_status(&P.gstatus[g], (g == 0 ? ST_INCL : ST_AGG) | x);
+}
+
+// The output offset of `tile`; false when a wait ran out of time.
+__device__ bool resolve_tile(const WParams &P, uint32_t tile, uint64_t &G)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t g = tile / GS, f = g * GS;
+    Waiter W{globaltimer(), 0};
+    // the tiles before this one in its group (at most GS - 1 < 64 words)
+    unsigned long long w = 0;
+    for (;;) {
+        bool miss = false;
+        w = 0;
+        for (uint32_t j = f + lane; j < tile; j += 32) {
+            const unsigned long long v = ld_status(&P.status[j]);
+            if (v == 0) miss = true;
+            w += v & ST_VAL;
+        }
+        if (!__any_sync(0xffffffffu, miss)) break;
+        if (!W.again(P)) return false;
+    }
+    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    // the groups before: sum aggregates back to the nearest inclusive prefix
+    uint64_t GE = 0;
+    int64_t base = (int64_t)g - 1;
+    while (base >= 0) {
+        unsigned long long v[LB_PER_LANE];
+#pragma unroll
+        for (int j = 0; j < LB_PER_LANE; j++) {
+            const int64_t k = base - (int64_t)LB_PER_LANE * lane - j;
+            v[j] = k >= 0 ? ld_status(&P.gstatus[k]) : ST_INCL;
+        }
+        int jstar = LB_PER_LANE;
+        bool zero_before = false;
+        unsigned long long lsum = 0;
+#pragma unroll
+        for (int j = 0; j < LB_PER_LANE; j++) {
+            if (jstar == LB_PER_LANE) {
+                const unsigned long long fl = v[j] & ~ST_VAL;
+                if (fl == 0) zero_before = true;
+                lsum += v[j] & ST_VAL;
+                if (fl == ST_INCL) jstar = j;
+            }
+        }
+        const unsigned incl = __ballot_sync(0xffffffffu, jstar < LB_PER_LANE);
+        const unsigned zero = __ballot_sync(0xffffffffu, zero_before);
+        const unsigned upto = incl ? (incl & (0u - incl)) : 0u;
+        const unsigned lanes = incl ? ((upto - 1u) | upto) : 0xffffffffu;
+        if (zero & lanes) {
+            if (!W.again(P)) return false;
+            continue;
+        }
+        unsigned long long x = ((lanes >> lane) & 1u) ? lsum : 0ull;
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        GE += x;
+        if (incl) break;
+        base -= 32 * LB_PER_LANE;
+    }
+    // once the group is complete, its inclusive prefix shortens later look-backs
+    if (lane == 0 && g > 0) {
+        const unsigned long long gv = ld_status(&P.gstatus[g]);
+        if ((gv & ~ST_VAL) == ST_AGG) st_status(&P.gstatus[g], ST_INCL | (GE + (gv & ST_VAL)));
+    }
+    G = GE + w;
+    return true;
+}
+
+// A tile whose tokens wait in the warp's stage for their output offset.
+struct Pending {
+    uint32_t tile;      // NONE: nothing pending
+    uint32_t staged;    // tokens in the stage (all of the tile's kept tokens)
+    uint64_t fail;      // failure offset within the tile, or NONE64
+    uint64_t agg;
+};
+
+__device__ void report_failure(const WParams &P, uint32_t tile, uint64_t fail, uint64_t G, uint64_t agg)
+{
+    if ((threadIdx.x & 31) == 0 && fail != NONE64) {
+        atomicMax(&P.res->inv_fail_pos, ~(unsigned long long)((uint64_t)tile * WT + fail));
+        atomicMax(&P.res->inv_fail_tok, ~(unsigned long long)(G + agg));
+    }
+}
+
+// The staged tokens of a tile to the output from index G, coalesced.
+__device__ void copy_stage(const WParams &P, const WEnv &E, uint32_t stage, uint32_t staged, uint64_t G)
+{
+    for (uint32_t i = threadIdx.x & 31; i < staged; i += 32) {
+        const uint64_t o = G + i;
+        if (o < P.cap) {
+            const uint32_t v = lds_u32(stage + 4 * i);
+            P.out_kinds[o] = (uint16_t)lds_u16(E.kmap_s + 2 * (v >> 16));
+            P.out_lens[o] = v & 0xFFFFu;
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 blk_at(const WEnv &E, uint32_t q)
+{
+    return q + BLK <= E.nrel ? ldg16(E.in + q) : make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ void zero16(uint32_t a)
+{
+    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(a), "r"(0u) : "memory");
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t tb_s = (sbase + 511u) & ~511u;
+    if (tb_s + P.rows_bytes > 65536u) {   // 16-bit row addresses must reach every row
+        if (threadIdx.x == 0) atomicOr(&P.res->error, ERR_SMEM);
+        return;
+    }
+    {   // stage the tables; row offsets become shared addresses
+        uint16_t *dst = reinterpret_cast<uint16_t *>(smem + (tb_s - sbase));
+        const uint16_t *src = reinterpret_cast<const uint16_t *>(P.blob);
+        const uint32_t n16 = P.blob_bytes / 2, r16 = P.rows_bytes / 2;
+        for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x) {
+            const uint32_t v = src[i];
+            dst[i] = (uint16_t)(i < r16 ? v + tb_s : v);
+        }
+    }
+    WEnv E;
+    E.P_slow = tb_s;
+    E.P_start = tb_s + P.p_start;
+    E.P_pre = tb_s + P.p_pre;
+    E.tb_s = tb_s;
+    E.acc_s = tb_s + P.acc_off;
+    E.kmap_s = tb_s + P.kmap_off;
+    E.cmap_s = tb_s + P.cmap_off;
+    E.cut_s = tb_s + P.cut_off;
+    E.shift = P.row_shift;
+    const uint32_t warea = ((tb_s + P.blob_bytes + 15u) & ~15u) + (uint32_t)wid * WAREA;
+    E.ev = warea;
+    const uint32_t stage = warea + EV_BYTES;
+    for (uint32_t i = lane; i < EV_BYTES / 16; i += 32) zero16(E.ev + 16 * i);
+    __syncthreads();
+    const uint32_t ahead = gridDim.x * (blockDim.x / 32);   // tiles the other warps take meanwhile
+
+    Pending pend{NONE, 0, NONE64, 0};
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) {
+            tile = atomicAdd(P.tile_counter, 1u);
+            if (*(volatile unsigned int *)&P.res->error != 0) tile = P.n_tiles;   // a wait gave up: stop
+        }
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= P.n_tiles) break;
+        const uint64_t tb = (uint64_t)tile * WT;
+        E.in = P.in + tb;
+        E.nrel64 = P.n - tb;
+        E.nrel = E.nrel64 < BIG ? (uint32_t)E.nrel64 : BIG;
+        const uint32_t nrel = E.nrel;
+        if (lane == 0 && tile + ahead < P.n_tiles) {   // a tile some warp takes about one tile from now, into L2
+            const uint64_t fb = (uint64_t)(tile + ahead) * WT;
+            const uint64_t left = P.n - fb;
+            const uint32_t bytes = (uint32_t)(left < EVB ? left : EVB) & ~15u;
+            if (bytes)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(P.in + fb), "r"(bytes) : "memory");
+        }
+
+        // (a) the first certified byte at or past the tile end, below LIMIT
+        uint32_t c1;
+        if (nrel <= WT) {
+            c1 = nrel;
+        } else {
+            const uint32_t lim = nrel < LIMIT ? nrel : LIMIT;
+            c1 = NONE;
+            for (uint32_t b0 = WT; b0 < lim; b0 += 128) {
+                const uint32_t pos = b0 + 4 * lane;
+                uint32_t m = 0;
+                if (pos + 4 <= lim) {
+                    const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(E.in + pos));
+                    for (uint32_t k = 0; k < 4; k++)
+                        if (lds_u8(E.cut_s + byte_of(w, k))) m |= 1u << k;
+                } else {
+                    for (uint32_t k = 0; pos + k < lim; k++)
+                        if (lds_u8(E.cut_s + __ldg(E.in + pos + k))) m |= 1u << k;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+                if (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const uint32_t mm = __shfl_sync(0xffffffffu, m, src);
+                    c1 = b0 + 4 * src + __ffs(mm) - 1;
+                    break;
+                }
+            }
+            if (c1 == NONE && lim == nrel) c1 = nrel;   // no certified byte before the end of the input
+        }
+
+        // (b) phase 1: every lane walks its slice from the PRE row
+        const uint32_t t0 = (uint32_t)lane * SLICE;
+        const bool first = tile == 0 && lane == 0;
+        Lane L;
+        L.e = first ? E.P_start : E.P_pre;
+        L.s = first ? 0u : NONE;
+        L.p = t0;
+        L.fail = NONE;
+        L.own = NONE;
+        L.act = t0 < nrel;
+        L.coarse = false;
+        uint4 cur = blk_at(E, t0), n1 = blk_at(E, t0 + BLK), n2 = blk_at(E, t0 + 2 * BLK);
+        for (uint32_t it = 0; it < NB1; it++) {
+            if (!L.act) continue;
+            if (L.p + BLK <= nrel) {
+                const uint32_t pb = L.p, ev = eva(E, pb);
+                const uint32_t pk0 = wword<FORM, 1>(L.e, cur.x, ev, E.P_pre, 0, E.cmap_s);
+                const uint32_t pk1 = wword<FORM, 1>(L.e, cur.y, ev + 4, E.P_pre, 0, E.cmap_s);
+                const uint32_t pk2 = wword<FORM, 1>(L.e, cur.z, ev + 8, E.P_pre, 0, E.cmap_s);
+                const uint32_t pk3 = wword<FORM, 1>(L.e, cur.w, ev + 12, E.P_pre, 0, E.cmap_s);
+                (void)pk0;
+                (void)pk1;
+                (void)pk2;
+                (void)pk3;
+                if (L.s == NONE && L.e != E.P_pre) {   // PRE was left in this block (the byte: refine_start)
+                    L.s = pb;
+                    L.coarse = true;
+                }
+                L.p = pb + BLK;
+                cur = n1;
+                n1 = n2;
+                n2 = blk_at(E, L.p + 2 * BLK);
+                if (L.e == E.P_slow) slow_fix<FORM>(E, L, L.p, BIG);
+            } else {
+                scalar_steps<FORM>(E, L, nrel, BIG);
+                finalize<FORM>(E, L, BIG);
+                L.act = false;
+            }
+        }
+
+        refine_start<FORM>(E, L);
+
+        // (c) chunk ends: the next lane's chunk start, else the halo's
+        uint32_t smin = L.s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_down_sync(0xffffffffu, smin, o);
+            if (lane + o < 32) smin = min(smin, y);
+        }
+        uint32_t end = __shfl_down_sync(0xffffffffu, smin, 1);
+        if (lane == 31) end = NONE;
+        if (end == NONE) end = c1;
+        const uint32_t c0 = __shfl_sync(0xffffffffu, smin, 0);
+        const bool long_lane = L.s != NONE && end == NONE;   // its chunk leaves the halo
+        bool act2 = L.act && L.s != NONE && end != NONE;
+        L.own = end;
+        while (__any_sync(0xffffffffu, act2)) {
+            if (!act2) continue;
+            if (L.p + BLK <= nrel) {
+                const uint32_t pb = L.p, ev = eva(E, pb);
+                const uint32_t pk0 = wword<FORM, 2>(L.e, cur.x, ev, end, pb + 3, E.cmap_s);
+                const uint32_t pk1 = wword<FORM, 2>(L.e, cur.y, ev + 4, end, pb + 7, E.cmap_s);
+                const uint32_t pk2 = wword<FORM, 2>(L.e, cur.z, ev + 8, end, pb + 11, E.cmap_s);
+                const uint32_t pk3 = wword<FORM, 2>(L.e, cur.w, ev + 12, end, pb + 15, E.cmap_s);
+                L.p = pb + BLK;
+                if (L.p > end) {
+                    // the block holds the chunk end: the codes of its word up to the end
+                    const uint32_t wk = (end - pb) >> 2, pk = pick4(wk, pk0, pk1, pk2, pk3);
+                    for (uint32_t k = 0; k <= ((end - pb) & 3u); k++) sts_u8(ev + 4 * wk + k, byte_of(pk, k));
+                    if (L.e == E.P_slow && byte_of(pk, (end - pb) & 3u) == 0) slow_fix<FORM>(E, L, L.p, end);
+                    act2 = false;
+                } else {
+                    cur = n1;
+                    n1 = n2;
+                    n2 = blk_at(E, L.p + 2 * BLK);
+                    if (L.e == E.P_slow) {
+                        slow_fix<FORM>(E, L, L.p, end);
+                        act2 = L.act;
+                    }
+                }
+            } else {
+                scalar_steps<FORM>(E, L, nrel, end);
+                finalize<FORM>(E, L, end);
+                act2 = false;
+            }
+        }
+        __syncwarp();
+
+        // (d) count the kept codes of (c0, hi]
+        const uint32_t fail = __reduce_min_sync(0xffffffffu, L.fail);
+        const uint32_t long_s1 = __reduce_max_sync(0xffffffffu, long_lane ? L.s + 1 : 0u);
+        uint32_t hi = c1 != NONE ? c1 : long_s1 - 1;
+        if (fail < hi) hi = fail;
+        uint32_t wa = 0, wb = 0, last = 0, cnt = 0;
+        if (c0 != NONE) {
+            if (hi != c1) {   // a failure or a chunk past the halo: clear every code after hi
+                const uint32_t z0 = eva(E, hi) + 1, z1 = (z0 + 15u) & ~15u;
+                for (uint32_t a = z0 + lane; a < z1; a += 32) sts_u8(a, 0);
+                for (uint32_t a = z1 + 16 * lane; a < E.ev + EV_BYTES; a += 16 * 32) zero16(a);
+                __syncwarp();
+            }
+            const uint32_t w0 = (c0 + 1) >> 2, w1 = max((hi >> 2) + 1, w0);
+            const uint32_t per = (w1 - w0 + 31) / 32;
+            wa = min(w0 + lane * per, w1);
+            wb = min(wa + per, w1);
+            for (uint32_t i = wa; i < wb; i++) {
+                const uint32_t w = lds_u32(eva(E, 4 * i));
+                cnt += __popc(kept_mask(w));
+                if (w) last = 4 * i + (31 - __clz(w)) / 8;
+            }
+        }
+        uint32_t excl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, excl, o);
+            if (lane >= o) excl += y;
+        }
+        const uint32_t fast_total = __shfl_sync(0xffffffffu, excl, 31);
+        excl -= cnt;
+        // the chunk past the halo, counted by lane 0
+        uint64_t gen_cnt = 0, gen_fail = NONE64;
+        const bool do_long = c0 != NONE && long_s1 != 0 && fail > long_s1 - 1;
+        bool over = false;
+        if (do_long && lane == 0) {
+            gen_cnt = generic_chunk<FORM>(E, long_s1 - 1, &gen_fail, nullptr, nullptr, 0, 0, P.sparse_limit, &over);
+            if (over) atomicOr(&P.res->error, ERR_SPARSE);   // the caller lexes the input another way
+        }
+        if (__shfl_sync(0xffffffffu, over ? 1u : 0u, 0)) {
+            publish_tile(P, tile, 0);
+            break;
+        }
+        gen_cnt = __shfl_sync(0xffffffffu, gen_cnt, 0);
+        gen_fail = __shfl_sync(0xffffffffu, gen_fail, 0);
+        const uint64_t agg = fast_total + gen_cnt;
+        const uint64_t fpos = fail != NONE ? (uint64_t)fail : gen_fail;
+        publish_tile(P, tile, agg);
+
+        // the previous tile's output: its predecessors have had a whole tile to publish
+        if (pend.tile != NONE) {
+            uint64_t G = 0;
+            if (!resolve_tile(P, pend.tile, G)) break;
+            report_failure(P, pend.tile, pend.fail, G, pend.agg);
+            copy_stage(P, E, stage, pend.staged, G);
+            pend.tile = NONE;
+            __syncwarp();
+        }
+
+        // (e) emit: (kind, length) of every kept code, in order, into the stage
+        const bool defer = !do_long && fast_total <= STAGE_CAP;
+        uint64_t G = 0;
+        if (!defer) {   // rare: tokens beyond the stage or a chunk past the halo are written at once
+            if (!resolve_tile(P, tile, G)) break;
+            report_failure(P, tile, fpos, G, agg);
+        }
+        if (c0 != NONE) {
+            uint32_t prev = last;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, prev, o);
+                if (lane >= o) prev = max(prev, y);
+            }
+            prev = __shfl_up_sync(0xffffffffu, prev, 1);
+            if (lane == 0 || prev < c0) prev = c0;
+            uint32_t idx = excl;
+            for (uint32_t i = wa; i < wb; i++) {
+                const uint32_t w = lds_u32(eva(E, 4 * i));
+                uint32_t nz = event_mask(w);
+                while (nz) {
+                    const uint32_t bit = __ffs(nz) - 1;   // 8k + 7
+                    nz &= nz - 1;
+                    const uint32_t code = (w >> (bit - 7)) & 0xFFu;
+                    const uint32_t pos = 4 * i + (bit >> 3);
+                    if (code >= 4) {
+                        if (idx < STAGE_CAP) {
+                            sts_u32(stage + 4 * idx, ((code >> 1) << 16) | (pos - prev));
+                        } else if (G + idx < P.cap) {
+                            P.out_kinds[G + idx] = (uint16_t)lds_u16(E.kmap_s + 2 * (code >> 1));
+                            P.out_lens[G + idx] = pos - prev;
+                        }
+                        idx++;
+                    }
+                    prev = pos;
+                }
+            }
+            for (uint32_t i = wa; i < wb; i++) sts_u32(eva(E, 4 * i), 0);   // clear the codes read
+        }
+        __syncwarp();
+        if (defer) {
+            pend.tile = tile;
+            pend.staged = fast_total;
+            pend.fail = fpos;
+            pend.agg = agg;
+        } else {
+            copy_stage(P, E, stage, fast_total < STAGE_CAP ? fast_total : STAGE_CAP, G);
+            if (do_long && lane == 0) {
+                uint64_t f2;
+                generic_chunk<FORM>(E, long_s1 - 1, &f2, P.out_kinds, P.out_lens, P.cap, G + fast_total);
+            }
+            __syncwarp();
+        }
+    }
+    if (pend.tile != NONE) {
+        uint64_t G = 0;
+        if (resolve_tile(P, pend.tile, G)) {
+            report_failure(P, pend.tile, pend.fail, G, pend.agg);
+            copy_stage(P, E, stage, pend.staged, G);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int warp_occupancy(lx_ctx *c, int form, uint32_t smem, int *occ)
+{
+    const uint64_t key = (3ull << 40) | ((uint64_t)form << 32) | smem;
+    for (auto &kv : c->occupancy)
+        if (kv.first == key) {
+            *occ = kv.second;
+            return LX_OK;
+        }
+    cudaError_t e;
+    int o = 0;
+    if (form == FORM_BYTE) {
+        e = cudaFuncSetAttribute(lex_warps<FORM_BYTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_BYTE>, NTHREADS, smem);
+    } else {
+        e = cudaFuncSetAttribute(lex_warps<FORM_CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_CLASS>, NTHREADS, smem);
+    }
+    if (e != cudaSuccess) return LX_E_CUDA;
+    if (o < 1) return LX_E_TOOBIG;
+    c->occupancy.emplace_back(key, o);
+    *occ = o;
+    return LX_OK;
+}
+
+}  // namespace
+
+// True when lx_lex can take the warp-tile kernel for this call.
+bool warp_path_ok(const lx_tokenset *ts, int mode, const uint8_t *d_in)
+{
+    return ts->walk[mode].status == LX_OK && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
+}
+
+int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                    uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed, cudaStream_t st,
+                    uint64_t sparse_limit)
+{
+    const WalkTable &w = ts->walk[mode];
+    if (n == 0) {
+        *n_tokens = 0;
+        *consumed = 0;
+        return LX_OK;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
+    DeviceTables dt;
+    int rc = ensure_device_tables(ts, dev, &dt);
+    if (rc != LX_OK) return rc;
+    const uint64_t n_tiles64 = (n + WT - 1) / WT;
+    if (n_tiles64 > 0xFFFFFFF0ull) return LX_E_INVAL;
+    const uint32_t n_tiles = (uint32_t)n_tiles64;
+    const uint32_t smem = 512 + (uint32_t)w.blob.size() + 16 + NWARPS * WAREA;
+    int occ = 0;
+    rc = warp_occupancy(c, w.form, smem, &occ);
+    if (rc != LX_OK) return rc;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * c->num_sms, (n_tiles + NWARPS - 1) / NWARPS);
+
+    const uint32_t n_groups = (n_tiles + GS - 1) / GS;
+    const size_t o_gstatus = 64 + 8 * (size_t)n_tiles, o_gdone = o_gstatus + 8 * (size_t)n_groups;
+    const size_t need = o_gdone + 4 * (size_t)n_groups;   // zeroed per call
+    rc = grow(&c->scratch, &c->scratch_bytes, need);
+    if (rc != LX_OK) return rc;
+    uint8_t *scr = static_cast<uint8_t *>(c->scratch);
+    WParams P;
+    P.in = d_in;
+    P.n = n;
+    P.blob = static_cast<const uint8_t *>(dt.d_walk[mode]);
+    P.blob_bytes = (uint32_t)w.blob.size();
+    P.rows_bytes = w.rows_bytes;
+    P.row_shift = w.row_shift;
+    P.p_start = w.p_start;
+    P.p_pre = w.p_pre;
+    P.acc_off = w.acc_off;
+    P.kmap_off = w.kmap_off;
+    P.cmap_off = w.cmap_off;
+    P.cut_off = w.cut_off;
+    P.out_kinds = d_kinds;
+    P.out_lens = d_lens;
+    P.cap = capacity;
+    P.res = reinterpret_cast<WResult *>(scr);
+    P.tile_counter = reinterpret_cast<unsigned int *>(scr + 32);
+    P.status = reinterpret_cast<unsigned long long *>(scr + 64);
+    P.gstatus = reinterpret_cast<unsigned long long *>(scr + o_gstatus);
+    P.gdone = reinterpret_cast<unsigned int *>(scr + o_gdone);
+    P.n_tiles = n_tiles;
+    P.timeout_ns = c->timeout_ns;
+    P.withhold = c->withhold;
+    P.sparse_limit = sparse_limit;
+    static_assert(sizeof(WResult) == 32, "record layout");
+
+    rc = cuda_err(cudaMemsetAsync(c->scratch, 0, need, st));
+    if (rc != LX_OK) return rc;
+    if (c->timing) cudaEventRecord(c->ev[0], st);
+    if (w.form == FORM_BYTE) lex_warps<FORM_BYTE><<<grid, NTHREADS, smem, st>>>(P);
+    else lex_warps<FORM_CLASS><<<grid, NTHREADS, smem, st>>>(P);
+    rc = cuda_err(cudaGetLastError());
+    if (c->timing) cudaEventRecord(c->ev[1], st);
+    if (rc != LX_OK) return rc;
+    rc = cuda_err(cudaMemcpyAsync(c->h_res, P.res, sizeof(WResult), cudaMemcpyDeviceToHost, st));
+    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(st));
+    if (rc != LX_OK) return rc;
+    const WResult r = *static_cast<const WResult *>(c->h_res);
+    if (r.error & ERR_SPARSE) return LX_SPARSE;
+    if (r.error & ERR_TIMEOUT) return LX_E_TIMEOUT;
+    if (r.error & ERR_SMEM) return LX_E_TOOBIG;
+    uint64_t tokens = r.total, con = n;
+    if (r.inv_fail_pos) {
+        con = ~r.inv_fail_pos;
+        tokens = ~r.inv_fail_tok;
+    }
+    *n_tokens = tokens;
+    *consumed = con;
+    return tokens > capacity ? LX_E_CAPACITY : LX_OK;
+}
+
+}  // namespace lx

@@ -53,6 +53,8 @@ struct lx_ctx {
     size_t h_scratch_bytes = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_lex;
+    // lx_lex kernel choice (lx_ctx_set_kernel): LX_KERNEL_AUTO, _TILE or _WARP
+    int kernel = 0;
     // optional kernel timing
     bool timing = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -70,6 +72,17 @@ int grow_host(void **p, size_t *have, size_t need);
 // blobs of each mode (both forms where both exist) and the plain scan table
 // (nullptr where a table does not exist for this token set).
 int ensure_device_tables(const lx_tokenset *ts, int device, DeviceTables *out);
+// The warp-tile kernel (lexwarp.cu): whether lx_lex can take it for this
+// token set, mode and input pointer (an event-code walk table and a 16-byte
+// aligned input), and the call itself (same contract as lx_lex).  With
+// sparse_limit != 0 a chunk longer than that many bytes (certified bytes too
+// far apart) makes the call stop early and return LX_SPARSE, leaving the
+// input to the enumerative path.
+constexpr int LX_SPARSE = -100;   // internal status, never returned by the C ABI
+bool warp_path_ok(const lx_tokenset *ts, int mode, const uint8_t *d_in);
+int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                    uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed, cudaStream_t st,
+                    uint64_t sparse_limit);
 // The entry-context model (model.cu): number of contexts it scores, and the
 // BF16 prediction of the entry context of every chunk start (0xFFFE =
 // BOUNDARY) into guess[M], restricted to the candidates of the byte before.

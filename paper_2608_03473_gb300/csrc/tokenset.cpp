@@ -261,6 +261,100 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht, bool class_form)
     }
 }
 
+// Event-code walk table (internal.h).  Same transitions as build_table
+// without E rows: the token end and its kind travel in the entry.
+void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt)
+{
+    const uint32_t S = t.n_states, C = t.n_classes, q0 = t.q0;
+    auto nx = [&](uint32_t c, uint32_t q) { return t.next[(size_t)c * S + q]; };
+    const uint32_t *cutmask = (mode == LX_FILTERED_MODULO) ? t.modulo : t.exact;
+    std::vector<uint8_t> cut_c(C, 0);
+    for (uint32_t b = 0; b < 256; b++)
+        if (bit(cutmask, b)) cut_c[t.byte_class[b]] = 1;
+    wt = lx::WalkTable();
+    // event codes: 1 for a discarded kind, 2.. for kept kinds in state order
+    std::vector<uint32_t> code(t.n_kinds, 0);
+    std::vector<uint16_t> kmap(lx::WALK_CODES, 0);
+    uint32_t next_code = 2;
+    for (uint32_t q = 0; q < S; q++) {
+        const uint32_t k = t.accept[q];
+        if (k == LX_NO_KIND || code[k]) continue;
+        if (mode != LX_FULL_EXACT && t.discard[k]) {
+            code[k] = 1;
+        } else {
+            if (next_code >= lx::WALK_CODES) return;   // more kept kinds than codes
+            kmap[next_code] = (uint16_t)k;
+            code[k] = next_code++;
+        }
+    }
+    wt.n_kept = next_code - 2;
+    const uint32_t SLOW = 0, START = S + 1, PRE = S + 2, R = S + 3;
+    auto Rq = [](uint32_t q) { return 1 + q; };
+    if ((uint64_t)R * 512 <= lx::MAX_BYTE_FORM_BYTES) {
+        wt.form = lx::FORM_BYTE;
+        wt.row_shift = 9;
+    } else if (C <= 127 && (uint64_t)R * 256 <= lx::MAX_TABLE_BYTES) {
+        wt.form = lx::FORM_CLASS;
+        wt.row_shift = 8;
+    } else {
+        return;
+    }
+    const uint32_t row_bytes = 1u << wt.row_shift;
+    wt.n_rows = R;
+    wt.rows_bytes = R * row_bytes;
+    wt.p_start = START * row_bytes;
+    wt.p_pre = PRE * row_bytes;
+    auto entry = [&](uint32_t row, uint32_t c) -> uint16_t {
+        uint32_t to = SLOW, cd = 0;
+        const uint32_t d0 = nx(c, q0);
+        if (row == SLOW) {
+            to = SLOW;
+        } else if (row == START) {
+            to = d0 != LX_NONE ? Rq(d0) : SLOW;
+        } else if (row == PRE) {
+            to = cut_c[c] ? (d0 != LX_NONE ? Rq(d0) : SLOW) : PRE;
+        } else {
+            const uint32_t q = row - 1, d = nx(c, q);
+            const bool acc = t.accept[q] != LX_NO_KIND;
+            if (cut_c[c]) {
+                if (acc && d0 != LX_NONE) {
+                    to = Rq(d0);
+                    cd = code[t.accept[q]];
+                }
+            } else if (d != LX_NONE) {
+                to = Rq(d);
+            } else if (acc && d0 != LX_NONE) {
+                to = Rq(d0);
+                cd = code[t.accept[q]];
+            }
+        }
+        return (uint16_t)((to << wt.row_shift) | (cd << 1));
+    };
+    auto al = [](uint32_t x, uint32_t a) { return (x + a - 1) / a * a; };
+    wt.acc_off = wt.rows_bytes;
+    wt.kmap_off = al(wt.acc_off + R, 16);
+    wt.cmap_off = al(wt.kmap_off + 2 * lx::WALK_CODES, 256);
+    wt.cut_off = wt.cmap_off + 256;
+    wt.blob.assign(wt.cut_off + 256, 0);
+    uint16_t *ent = reinterpret_cast<uint16_t *>(wt.blob.data());
+    for (uint32_t r = 0; r < R; r++) {
+        if (wt.form == lx::FORM_BYTE) {
+            for (uint32_t b = 0; b < 256; b++) ent[(size_t)r * 256 + b] = entry(r, t.byte_class[b]);
+        } else {
+            for (uint32_t c = 0; c < 128; c++) ent[(size_t)r * 128 + c] = c < C ? entry(r, c) : (uint16_t)0;
+        }
+        const uint32_t q = r - 1;
+        if (r >= 1 && r <= S && t.accept[q] != LX_NO_KIND)
+            wt.blob[wt.acc_off + r] = (uint8_t)(2 * code[t.accept[q]]);
+    }
+    std::memcpy(wt.blob.data() + wt.kmap_off, kmap.data(), 2 * lx::WALK_CODES);
+    for (uint32_t b = 0; b < 256; b++) {
+        wt.blob[wt.cmap_off + b] = (uint8_t)(2 * t.byte_class[b]);
+        wt.blob[wt.cut_off + b] = bit(cutmask, b) ? 1 : 0;
+    }
+    wt.status = LX_OK;
+}
+
 void build_scan_table(const lx_tokenset &t, ScanTable &st)
 {
     const uint32_t S = t.n_states, C = t.n_classes;
@@ -365,6 +459,7 @@ extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
             // the class-indexed form as well when the default is byte-indexed:
             // far smaller, so more CTAs fit per SM
             if (t->tab[m].form == lx::FORM_BYTE) build_table(*t, m, t->tab_cls[m], true);
+            build_walk_table(*t, m, t->walk[m]);
         }
         build_scan_table(*t, t->scan);
     } catch (const std::bad_alloc &) {
@@ -373,6 +468,42 @@ extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
     }
     *out = t;
     return LX_OK;
+}
+
+// Framing at the producer (Section 7.1): the reserved byte gets a rule of its
+// own -- a new kind n_kinds, one byte long, from q0 -- and no other token
+// admits it at any position, so its only live consumption is from q0.
+extern "C" int lx_compile_tokenset_framed(const lx_dfa *dfa, const uint16_t *discarded, uint32_t n_discarded,
+                                          uint32_t frame_byte, int frame_discarded, lx_tokenset **out)
+{
+    if (!dfa || !out || frame_byte > 255 || !dfa->byte_class || !dfa->next || !dfa->accept_kind) return LX_E_INVAL;
+    const uint32_t S = dfa->n_states, C = dfa->n_classes;
+    if (S == 0 || S >= (1u << 20) || C == 0 || C > 256 || dfa->q0 >= S || dfa->n_kinds >= 32767 ||
+        (n_discarded && !discarded))
+        return LX_E_INVAL;
+    const uint32_t cr = dfa->byte_class[frame_byte];
+    if (cr >= C) return LX_E_INVAL;
+    uint32_t share = 0;   // other bytes in the reserved byte's class
+    for (uint32_t b = 0; b < 256; b++) share += (b != frame_byte && dfa->byte_class[b] == cr);
+    const uint32_t C2 = share ? C + 1 : C, c_new = share ? C : cr, F = S;   // F: the new accepting state
+    if (C2 > 256) return LX_E_INVAL;
+    try {
+        std::vector<uint8_t> cls(dfa->byte_class, dfa->byte_class + 256);
+        cls[frame_byte] = (uint8_t)c_new;
+        std::vector<uint32_t> nx((size_t)C2 * (S + 1), LX_NONE);
+        for (uint32_t c = 0; c < C; c++)
+            for (uint32_t q = 0; q < S; q++)
+                if (c != c_new) nx[(size_t)c * (S + 1) + q] = dfa->next[(size_t)c * S + q];
+        nx[(size_t)c_new * (S + 1) + dfa->q0] = F;   // the frame token; every other state rejects the byte
+        std::vector<uint16_t> acc(dfa->accept_kind, dfa->accept_kind + S);
+        acc.push_back((uint16_t)dfa->n_kinds);
+        std::vector<uint16_t> disc(discarded, discarded + n_discarded);
+        if (frame_discarded) disc.push_back((uint16_t)dfa->n_kinds);
+        lx_dfa d{S + 1, C2, dfa->q0, dfa->n_kinds + 1, cls.data(), nx.data(), acc.data()};
+        return lx_compile_tokenset(&d, disc.empty() ? nullptr : disc.data(), (uint32_t)disc.size(), out);
+    } catch (const std::bad_alloc &) {
+        return LX_E_NOMEM;
+    }
 }
 
 extern "C" int lx_certificates(const lx_tokenset *ts, uint32_t exact_useful[8], uint32_t modulo_useful[8])
@@ -420,6 +551,18 @@ static int table_out(const HostTable &h, void *out, uint32_t cap, uint32_t *meta
                             h.cert_off, h.p_pre};
     if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 12));
     return h.status;
+}
+
+extern "C" int lx_tokenset_walk_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
+                                      uint32_t meta_len)
+{
+    if (!ts || mode < 0 || mode > 2) return LX_E_INVAL;
+    const lx::WalkTable &w = ts->walk[mode];
+    if (out && cap) std::memcpy(out, w.blob.data(), std::min<size_t>(cap, w.blob.size()));
+    const uint32_t m[10] = {(uint32_t)w.blob.size(), (uint32_t)w.form, w.n_rows, w.row_shift, w.p_start,
+                            w.p_pre, w.acc_off, w.kmap_off, w.cmap_off, w.cut_off};
+    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 10));
+    return w.status;
 }
 
 extern "C" int lx_tokenset_scan_table(const lx_tokenset *ts, void *out, uint32_t cap, uint32_t *meta,

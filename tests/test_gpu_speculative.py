@@ -221,3 +221,31 @@ def test_full_size_refused_512mib(env, trained):
         assert rc == 0 and con == econ and nt == ek.size, (path, rc, con, nt, ek.size)
         assert np.array_equal(k[:nt].cpu().numpy().view(np.uint16).astype(np.int64), ek), path
         assert np.array_equal(l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), el), path
+
+
+def _adversarial(seed):
+    """Block comments and a multi-line string that each span well over 64
+    chunks of 4096 bytes, their bodies made of ordinary C-like code (so a
+    window inside them looks like code), between stretches of the corpus."""
+    base = corpus.generate(NAME, 2 << 20, seed=seed)
+    code = corpus.generate("clike", 700_000, seed=seed + 1).tobytes()
+    body = code.replace(b"*/", b"* /")
+    text = code.replace(b'"', b"'").replace(b"\\", b"/")
+    parts = [base[:600_000].tobytes(), b"\n/*", body[:400_000], b"*/\n",
+             base[600_000:1_200_000].tobytes(), b'\nx = "', text[:350_000], b'";\n',
+             base[1_200_000:].tobytes(), b"\n/*", body[400_000:], b"*/\n"]
+    return np.frombuffer(b"".join(parts), np.uint8)
+
+
+def test_long_cascades_go_to_the_judge(env, trained):
+    """Comments and strings spanning hundreds of chunks: the fix-up rounds are
+    bounded, the enumerative judge settles the rest, the output is exact."""
+    lg, ctx, ts, S = env
+    w = _adversarial(71)
+    for model in (trained, None):
+        for mode in (0, 2):
+            st = _check(lg, ctx, ts, model, w, mode)
+            assert st["rounds"] <= 5, st
+            assert st["judged"], st
+    st = _check(lg, ctx, ts, trained, corpus.generate(NAME, 8 << 20, seed=72), 0)
+    assert st["rounds"] <= 5, st

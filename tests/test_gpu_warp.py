@@ -1,0 +1,175 @@
+"""The warp-tile kernel of lx_lex (every warp owns 4096-byte tiles, event
+codes in the walk table) against the oracle and against the tile kernel,
+element by element, through the C ABI.
+
+Cases: every token set and mode on seeded corpora at ragged sizes; lexing
+errors near tile and slice edges; lines longer than the halo (the last chunk
+of a tile leaves it and is walked byte by byte); inputs with no certified
+byte at all; more kept tokens per tile than the shared stage holds;
+backtracking-heavy inputs; the capacity protocol; empty and one-byte inputs.
+"""
+
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from lexinputs import corpus
+from lexinputs import tokensets as T
+
+pytestmark = pytest.mark.gpu
+
+WT = 4096
+
+
+@pytest.fixture(scope="module")
+def env(lexlib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lg = lexlib
+    warp = lg.lx_ctx_create()
+    assert lg.lx_ctx_set_kernel(warp, lg.LX_KERNEL_WARP) == 0
+    tile = lg.lx_ctx_create()
+    assert lg.lx_ctx_set_kernel(tile, lg.LX_KERNEL_TILE) == 0
+    return lg, warp, tile
+
+
+_ts = {}
+
+
+def tokenset(lg, name):
+    if name not in _ts:
+        _ts[name] = lg.lx_compile_tokenset(T.tokenset(name), T.discarded_kinds(name))
+    return _ts[name]
+
+
+def run(lg, ctx, name, w, mode, capacity=None):
+    import torch
+    w = np.ascontiguousarray(np.frombuffer(bytes(w), np.uint8) if isinstance(w, (bytes, bytearray)) else w)
+    n = int(w.size)
+    cap = n + 1 if capacity is None else capacity
+    d = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+    if n:
+        d[:n].copy_(torch.from_numpy(w.copy()))
+    k = torch.zeros(max(cap, 1), dtype=torch.int16, device="cuda")
+    l = torch.zeros(max(cap, 1), dtype=torch.int32, device="cuda")
+    rc, nt, con = lg.lx_lex(ctx, tokenset(lg, name), d, mode, k, l, n=n, capacity=cap)
+    m = min(nt, cap)
+    return rc, nt, con, k[:m].cpu().numpy().view(np.uint16).astype(np.int64), \
+        l[:m].cpu().numpy().view(np.uint32).astype(np.int64)
+
+
+def expected(name, w, mode):
+    dfa = T.tokenset(name)
+    k, l, con = oracle.lex(dfa, w)
+    if mode:
+        k, l = oracle.discard(k, l, T.discarded_kinds(name), dfa.n_kinds)
+    return k.astype(np.int64), l.astype(np.int64), con
+
+
+def check(env, name, w, mode, both=True):
+    lg, warp, tile = env
+    ek, el, econ = expected(name, w, mode)
+    rc, nt, con, k, l = run(lg, warp, name, w, mode)
+    assert rc == 0, lg.lx_strerror(rc)
+    assert con == econ and nt == ek.size, (name, mode, con, econ, nt, ek.size)
+    assert np.array_equal(k, ek) and np.array_equal(l, el), (name, mode)
+    if both:
+        rc2, nt2, con2, k2, l2 = run(lg, tile, name, w, mode)
+        assert rc2 == 0 and nt2 == nt and con2 == con
+        assert np.array_equal(k2, k) and np.array_equal(l2, l)
+    return nt
+
+
+SETS = [("arith", 0), ("arith", 1), ("arith", 2), ("json", 1), ("json", 2), ("clike", 1), ("clike", 2),
+        ("clike_row1", 0), ("clike_row1", 1), ("clike_row1", 2)]
+
+
+@pytest.mark.parametrize("name,mode", SETS)
+def test_corpora_ragged(env, name, mode):
+    gen = "clike" if name == "clike_row1" else name
+    base = corpus.generate(gen, 3 << 20, seed=101)
+    for n in (1, 15, 16, 17, 127, 128, 129, 4095, 4096, 4097, 5119, 5120, 5121, 3 * WT + 77, 100_003, base.size):
+        check(env, name, base[:n], mode, both=n == base.size)
+
+
+@pytest.mark.parametrize("name,mode", [("json", 2), ("clike", 2), ("arith", 0)])
+def test_errors_near_edges(env, name, mode):
+    base = corpus.generate(name, 64 * WT, seed=102)
+    rng = random.Random(7)
+    spots = [0, 1, 127, 128, 129, WT - 1, WT, WT + 1, 2 * WT - 3, 5 * WT + 128, 9 * WT + 4095]
+    spots += [rng.randrange(base.size) for _ in range(6)]
+    for pos in spots:
+        w = base.copy()
+        w[pos] = 0x01 if name != "arith" else ord("?")
+        check(env, name, w, mode, both=False)
+
+
+def test_lines_longer_than_the_halo(env):
+    rng = random.Random(8)
+    parts = []
+    for _ in range(300):
+        if rng.random() < 0.3:
+            parts.append(b'{"long":"' + b"y" * rng.randint(900, 9000) + b'"}\n')
+        else:
+            parts.append(b'{"a":[1,2.5,true],"b":"x"}\n')
+    w = b"".join(parts)
+    check(env, "json", w, 2)
+    check(env, "json", w[:-1] + b"\x01", 2)
+
+
+def test_no_certified_byte(env):
+    # minified JSON (no newline): one chunk from offset 0, walked byte by byte
+    w = corpus.generate("json", 200_000, seed=103).copy()
+    w[w == ord("\n")] = ord(" ")
+    w[w == ord("\r")] = ord(" ")
+    w[w == ord("\t")] = ord(" ")
+    check(env, "json", w, 2)
+
+
+def test_dense_tokens_overflow_the_stage(env):
+    # one-byte tokens: over 1024 kept tokens per 4096-byte tile
+    rng = random.Random(9)
+    line = lambda: bytes(rng.choice(b"+-*/%~!;,") for _ in range(rng.randint(30, 300))) + b"\n"
+    w = b"".join(line() for _ in range(3000))
+    check(env, "clike", w, 2)
+    check(env, "clike", w, 1, both=False)
+
+
+def test_backtracking(env):
+    rng = random.Random(10)
+    parts = [b"a..b", b"0x", b"x...y", b"1.", b".5", b"a->b", b"a-->b", b" ", b"\n", b";", b"1e+", b"1e5"]
+    w = b"".join(rng.choice(parts) for _ in range(200_000))
+    check(env, "clike", w, 2)
+    w = b"".join(rng.choice([b"===", b"=", b"==", b"a", b"\n", b"(", b" "]) for _ in range(200_000))
+    check(env, "arith", w, 0)
+
+
+def test_capacity_and_small(env):
+    lg, warp, tile = env
+    w = corpus.generate("json", 300_000, seed=104)
+    ek, el, econ = expected("json", w, 2)
+    cap = ek.size // 3
+    rc, nt, con, k, l = run(lg, warp, "json", w, 2, capacity=cap)
+    assert rc == lg.LX_E_CAPACITY and nt == ek.size and con == econ
+    assert np.array_equal(k, ek[:cap]) and np.array_equal(l, el[:cap])
+    for w in (b"", b"{", b"\n", b"1", b"\x01", b"[1]\n"):
+        check(env, "json", w, 2)
+
+
+def test_warp_kernel_needs_aligned_input(env):
+    import torch
+    lg, warp, tile = env
+    w = corpus.generate("json", 10_000, seed=105)
+    d = torch.zeros(w.size + 32, dtype=torch.uint8, device="cuda")
+    d[3:3 + w.size].copy_(torch.from_numpy(w.copy()))
+    k = torch.zeros(w.size, dtype=torch.int16, device="cuda")
+    l = torch.zeros(w.size, dtype=torch.int32, device="cuda")
+    rc, _, _ = lg.lx_lex(warp, tokenset(lg, "json"), d[3:3 + w.size], 2, k, l)
+    assert rc == lg.LX_E_INVAL          # asked for the warp kernel, which needs 16-byte alignment
+    auto = lg.lx_ctx_create()
+    rc, nt, con = lg.lx_lex(auto, tokenset(lg, "json"), d[3:3 + w.size], 2, k, l)
+    ek, el, econ = expected("json", w, 2)
+    assert rc == 0 and nt == ek.size and con == econ     # the tile kernel serves it

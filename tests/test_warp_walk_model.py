@@ -1,0 +1,427 @@
+"""Host model of the warp-tile lexer (lexwarp.cu) over the event-code walk
+tables of ``lx_tokenset_walk_table``, checked against the oracle.
+
+The model follows the kernel step for step, with the lanes of a warp run one
+after the other (each input position has exactly one owning lane, so the
+order does not matter): lanes start their slices in the PRE row, step whole
+16-byte blocks, store the packed event codes of words that did not begin in
+PRE (and, byte by byte, the codes after the first certified byte of the word
+where PRE was left), take the next lane's first certified byte (or the first
+one past the tile, found by a scan of the halo) as their range end, store
+nothing past it, replay a token from q0 on reaching SLOW (longest match with
+backtracking), and finish at the end of the input.  Counting and emission
+read the event codes of (c0, hi] in order; a last range that leaves the
+halo is walked byte by byte.  The geometry is a parameter, so small tiles
+exercise every edge on short inputs.
+"""
+
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from lexinputs import corpus
+from lexinputs import tokensets as T
+
+NONE = 0xFFFFFFFF
+
+
+class Walk:
+    def __init__(self, blob, meta):
+        self.blob = blob
+        self.form = meta["form"]
+        self.shift = meta["row_shift"]
+        self.ent = blob[:meta["n_rows"] << self.shift].view(np.uint16).astype(np.int64)
+        self.P_start, self.P_pre, self.P_slow = meta["p_start"], meta["p_pre"], 0
+        self.acc = blob[meta["acc_off"]:meta["acc_off"] + meta["n_rows"]].astype(np.int64)
+        self.kmap = blob[meta["kmap_off"]:meta["kmap_off"] + 256].view(np.uint16).astype(np.int64)
+        self.cmap2 = blob[meta["cmap_off"]:meta["cmap_off"] + 256].astype(np.int64)
+        self.cut = blob[meta["cut_off"]:meta["cut_off"] + 256].astype(bool)
+
+    def step(self, e, b):
+        if self.form == 0:
+            a = (e & ~0x1FE) | (b << 1)
+        else:
+            a = (e & ~0xFF) | int(self.cmap2[b])
+        return int(self.ent[a >> 1])
+
+    def acc_code(self, e):
+        return int(self.acc[e >> self.shift])
+
+
+class WarpModel:
+    def __init__(self, walk, wt=4096, halo=1024, blk=16):
+        self.W = walk
+        self.WT, self.SLICE, self.HALO, self.BLK = wt, wt // 32, halo, blk
+        self.EVB = wt + halo
+        self.LIMIT = self.EVB - blk
+
+    # one lane's SLOW handling: replay its token from the token start, then
+    # re-walk to `upto`.  Only positions <= hi are stored; a SLOW entered past
+    # hi belongs to the next range and just stops the lane.
+    def slow_fix(self, L, upto, hi):
+        W = self.W
+        while True:
+            tok = L["s"]
+            for j in range(min(upto - 1, hi), L["s"], -1):
+                if self.ev[j]:
+                    tok = j
+                    break
+            q, r, rc = W.P_start, None, 0
+            for k in range(tok, upto):
+                v = W.step(q, self.inb(k))
+                if (v & 0xFF) or v == W.P_slow:
+                    break
+                q = v
+                ac = W.acc_code(q)
+                if ac:
+                    r, rc = k + 1, ac
+            if r is None:
+                if tok < L["own_hi"]:
+                    L["fail"] = tok
+                L["act"] = False
+                return
+            if r <= hi:
+                self.ev[r] = rc
+            e, kslow = W.P_start, None
+            for k in range(r, upto):
+                v = W.step(e, self.inb(k))
+                if r < k <= hi:          # the step at r (from START) ends nothing
+                    self.ev[k] = v & 0xFF
+                if v == W.P_slow and e != W.P_slow:
+                    kslow = k
+                e = v
+            L["e"] = e
+            if e != W.P_slow:
+                return
+            if kslow > hi or r > hi:
+                L["act"] = False
+                return
+
+    def finalize(self, L, hi):
+        # at the end of the input: an accepting row ends its token there
+        W = self.W
+        if self.nrel > hi:
+            L["act"] = False
+            return
+        while L["act"]:
+            e = L["e"]
+            if e in (W.P_start, W.P_pre):
+                return
+            if e != W.P_slow:
+                ac = W.acc_code(e)
+                if ac:
+                    self.ev[self.nrel] = ac
+                    return
+                L["e"] = W.P_slow
+            self.slow_fix(L, self.nrel, hi)
+
+    def scalar(self, L, upto, hi):
+        # byte steps up to `upto` with the kernel's storing rule
+        W = self.W
+        while L["p"] < upto and L["act"]:
+            k = L["p"]
+            e0 = L["e"]
+            v = W.step(e0, self.inb(k))
+            if e0 == W.P_pre and v != W.P_pre and L["s"] == NONE:
+                L["s"] = k
+            if e0 != W.P_pre and k <= hi:
+                self.ev[k] = v & 0xFF
+            L["e"] = v
+            L["p"] = k + 1
+            if v == W.P_slow:
+                if k > hi:
+                    L["act"] = False
+                    return
+                self.slow_fix(L, k + 1, hi)
+
+    def block(self, L, hi_rule):
+        """One lockstep block: 4 words, packed stores.  hi_rule: None (phase 1,
+        store words that did not begin in PRE) or the range end (phase 2,
+        store whole words at or before it)."""
+        W = self.W
+        pb = L["p"]
+        words = []
+        for wk in range(self.BLK // 4):
+            e0 = L["e"]
+            codes = []
+            for k in range(4):
+                L["e"] = W.step(L["e"], self.inb(pb + 4 * wk + k))
+                codes.append(L["e"] & 0xFF)
+            words.append((e0, codes))
+            wpos = pb + 4 * wk
+            if (hi_rule is None and e0 != W.P_pre) or (hi_rule is not None and wpos + 3 <= hi_rule):
+                self.ev[wpos:wpos + 4] = codes
+        if hi_rule is None and L["s"] == NONE and L["e"] != W.P_pre:
+            # PRE was left in this block: its first certified byte starts the range
+            s = next(k for k in range(pb, pb + self.BLK) if W.cut[self.inb(k)])
+            L["s"] = s
+            wk = (s - pb) // 4
+            for j in range(s + 1, pb + 4 * wk + 4):
+                self.ev[j] = words[wk][1][j - pb - 4 * wk]
+        L["p"] = pb + self.BLK
+        return words
+
+    def inb(self, k):
+        return int(self.w[self.tb + k])
+
+    def generic(self, start, emit):
+        """The last range when it leaves the halo: byte steps from the
+        certified byte at `start` to the first certified byte at or past the
+        tile end (or the end of the input).  Returns (count, fail)."""
+        W = self.W
+        e, p, tok, cnt = W.P_start, start, start, 0
+        while True:
+            if p == self.nrel:
+                if e == W.P_start:
+                    return cnt, NONE
+                ac = W.acc_code(e) if e != W.P_slow else 0
+                if ac:
+                    cnt += self._emit(emit, ac, p - tok)
+                    return cnt, NONE
+                slow = True
+            else:
+                b = self.inb(p)
+                v = W.step(e, b)
+                slow = v == W.P_slow
+                if not slow:
+                    if v & 0xFF:
+                        cnt += self._emit(emit, v & 0xFF, p - tok)
+                        tok = p
+                        if p >= self.WT and W.cut[b]:
+                            return cnt, NONE
+                    e = v
+                    p += 1
+                    continue
+            q, r, rc = W.P_start, None, 0
+            for k in range(tok, p):
+                v = W.step(q, self.inb(k))
+                if (v & 0xFF) or v == W.P_slow:
+                    break
+                q = v
+                if W.acc_code(q):
+                    r, rc = k + 1, W.acc_code(q)
+            if r is None:
+                return cnt, tok
+            cnt += self._emit(emit, rc, r - tok)
+            tok = p = r
+            e = W.P_start
+            if r == self.nrel:
+                return cnt, NONE
+            if r >= self.WT and W.cut[self.inb(r)]:
+                return cnt, NONE
+
+    def _emit(self, emit, code, ln):
+        if code >= 4:
+            if emit is not None:
+                emit.append((int(self.W.kmap[code >> 1]), ln))
+            return 1
+        return 0
+
+    def tile(self, w, tile):
+        W = self.W
+        self.w = w
+        self.tb = tile * self.WT
+        n = int(w.size)
+        self.nrel = nrel = n - self.tb
+        self.ev = np.zeros(self.EVB + 16, np.int64)
+        # c1: the first certified byte at or past the tile end, inside the halo
+        if nrel <= self.WT:
+            c1 = nrel
+        else:
+            lim = min(nrel, self.LIMIT)
+            c1 = next((k for k in range(self.WT, lim) if W.cut[self.inb(k)]), NONE)
+            if c1 == NONE and lim == nrel:
+                c1 = nrel
+        lanes = []
+        for l in range(32):
+            t0 = l * self.SLICE
+            first = tile == 0 and l == 0
+            L = dict(p=t0, e=W.P_start if first else W.P_pre, s=0 if first else NONE, fail=NONE,
+                     act=t0 < nrel, own_hi=NONE)
+            lanes.append(L)
+        # phase 1
+        for l, L in enumerate(lanes):
+            end1 = (l + 1) * self.SLICE
+            L["own_hi"] = NONE
+            while L["act"] and L["p"] < end1:
+                if L["p"] + self.BLK <= nrel:
+                    self.block(L, None)
+                    if L["e"] == W.P_slow:
+                        self.slow_fix(L, L["p"], 1 << 40)
+                else:
+                    self.scalar(L, nrel, 1 << 40)
+                    self.finalize(L, 1 << 40)
+                    L["act"] = False
+        s = [L["s"] for L in lanes]
+        ends = []
+        for l in range(32):
+            nxt = min([x for x in s[l + 1:] if x != NONE], default=NONE)
+            ends.append(c1 if nxt == NONE else nxt)
+        have = [x for x in s if x != NONE]
+        c0 = min(have) if have else NONE
+        long_s = NONE
+        # phase 2
+        for l, L in enumerate(lanes):
+            end = ends[l]
+            if s[l] == NONE or not L["act"]:
+                continue
+            if end == NONE:
+                long_s = s[l]
+                continue
+            L["own_hi"] = end
+            while L["act"] and L["p"] <= end:
+                if L["p"] + self.BLK <= nrel:
+                    pb = L["p"]
+                    words = self.block(L, end)
+                    if L["p"] > end:
+                        wk = (end - pb) // 4
+                        wpos = pb + 4 * wk
+                        for j in range(wpos, end + 1):
+                            self.ev[j] = words[wk][1][j - wpos]
+                        if L["e"] == W.P_slow and self.ev[end] == 0:
+                            self.slow_fix(L, L["p"], end)
+                        L["act"] = False
+                    elif L["e"] == W.P_slow:
+                        self.slow_fix(L, L["p"], end)
+                else:
+                    self.scalar(L, nrel, end)
+                    self.finalize(L, end)
+                    L["act"] = False
+        fails = [L["fail"] for L in lanes]
+        fail = min(fails)
+        out = []
+        if c0 == NONE:
+            return out, NONE, False
+        hi = c1 if long_s == NONE else long_s
+        if fail < hi:
+            hi = fail
+        prev = c0
+        for p in range(c0 + 1, hi + 1):
+            code = int(self.ev[p])
+            if code:
+                if code >= 4:
+                    out.append((int(W.kmap[code >> 1]), p - prev))
+                prev = p
+        if long_s != NONE and fail > long_s:
+            _, f2 = self.generic(long_s, out)
+            fail = f2 if f2 != NONE else fail
+        return out, fail, True
+
+
+def model_lex(lg, name, mode, w, **geo):
+    ts = lg.lx_compile_tokenset(T.tokenset(name), T.discarded_kinds(name))
+    rc, blob, meta = lg.lx_tokenset_walk_table(ts, mode)
+    assert rc == 0, rc
+    m = WarpModel(Walk(blob, meta), **geo)
+    n = int(w.size)
+    toks = []
+    n_tiles = (n + m.WT - 1) // m.WT
+    for t in range(n_tiles):
+        out, fail, _ = m.tile(w, t)
+        if fail != NONE:
+            # the tokens before the failure, and nothing after it (Corollary 1)
+            return toks + out, t * m.WT + fail
+        toks += out
+    return toks, n
+
+
+def expected(name, mode, w):
+    dfa = T.tokenset(name)
+    k, l, con = oracle.lex(dfa, w)
+    if mode:
+        k, l = oracle.discard(k, l, T.discarded_kinds(name), dfa.n_kinds)
+    return list(zip(k.tolist(), l.tolist())), con
+
+
+SMALL = dict(wt=512, halo=128, blk=16)   # 16-byte slices: one block per lane
+
+
+@pytest.fixture(scope="module")
+def lg(lexlib):
+    return lexlib
+
+
+@pytest.mark.parametrize("name,mode", [("arith", 0), ("arith", 2), ("json", 2), ("clike", 2), ("clike_row1", 0)])
+def test_model_matches_oracle_corpora(lg, name, mode):
+    gen = "clike" if name == "clike_row1" else name
+    w = corpus.generate(gen, 20000, seed=11)
+    got, con = model_lex(lg, name, mode, w, **SMALL)
+    want, econ = expected(name, mode, w)
+    assert con == econ and got == want
+
+
+@pytest.mark.parametrize("name,mode", [("json", 2), ("clike", 2), ("arith", 0)])
+def test_model_full_geometry(lg, name, mode):
+    w = corpus.generate(name, 3 * 4096 + 999, seed=12)
+    got, con = model_lex(lg, name, mode, w)
+    want, econ = expected(name, mode, w)
+    assert con == econ and got == want
+
+
+def test_model_errors_long_lines_and_ragged(lg):
+    rng = random.Random(5)
+    base = corpus.generate("json", 6000, seed=13)
+    for n in (1, 15, 16, 17, 255, 256, 257, 300, 511, 600, 6000):
+        w = base[:n]
+        got, con = model_lex(lg, "json", 2, w, **SMALL)
+        assert (got, con) == expected("json", 2, w), n
+    for _ in range(12):
+        w = base.copy()
+        w[rng.randrange(w.size)] = 0x01
+        got, con = model_lex(lg, "json", 2, w, **SMALL)
+        assert (got, con) == expected("json", 2, w)
+    # lines longer than the halo: the last range leaves it
+    line = b'{"k":"' + b"x" * 700 + b'"}\n'
+    w = np.frombuffer(line * 6 + base[:900].tobytes(), np.uint8)
+    got, con = model_lex(lg, "json", 2, w, **SMALL)
+    assert (got, con) == expected("json", 2, w)
+
+
+def test_model_backtracking(lg):
+    # '..' in C-like backtracks from the '...' prefix; '0x' from a hex prefix;
+    # arith '===' is '==' then '='
+    rng = random.Random(6)
+    parts = [b"a..b", b"0x", b"x...y", b"1.", b".5", b"a->b", b"a-->b", b" ", b"\n", b";"]
+    w = np.frombuffer(b"".join(rng.choice(parts) for _ in range(3000)), np.uint8)
+    got, con = model_lex(lg, "clike", 2, w, **SMALL)
+    assert (got, con) == expected("clike", 2, w)
+    w = np.frombuffer(b"".join(rng.choice([b"===", b"=", b"==", b"a", b"\n", b"(", b" "]) for _ in range(3000)),
+                      np.uint8)
+    got, con = model_lex(lg, "arith", 0, w, **SMALL)
+    assert (got, con) == expected("arith", 0, w)
+
+
+def test_walk_table_codes(lg):
+    # every event code of a transition is the code of the kind its row accepts
+    ts = lg.lx_compile_tokenset(T.tokenset("clike"), T.discarded_kinds("clike"))
+    rc, blob, meta = lg.lx_tokenset_walk_table(ts, 2)
+    assert rc == 0 and meta["form"] == 1
+    W = Walk(blob, meta)
+    for r in range(meta["n_rows"]):
+        e = r << W.shift
+        for b in range(256):
+            v = W.step(e, b)
+            if v & 0xFF:
+                assert W.acc_code(e) == v & 0xFF
+    rc, blob, meta = lg.lx_tokenset_walk_table(lg.lx_compile_tokenset(T.tokenset("json"), T.discarded_kinds("json")), 2)
+    assert rc == 0 and meta["form"] == 0
+
+
+@pytest.mark.parametrize("name,mode", [("arith", 0), ("arith", 1), ("json", 2), ("json", 1), ("clike", 2),
+                                       ("clike_row1", 0), ("clike_row1", 2)])
+def test_model_random_snippets(lg, name, mode):
+    """Random slices of the corpora (some with a malformed byte) at every
+    alignment, tile and slice boundary of the small geometry."""
+    gen = "clike" if name == "clike_row1" else name
+    base = corpus.generate(gen, 1 << 16, seed=21)
+    rng = random.Random(hash((name, mode)) & 0xFFFF)
+    for _ in range(60):
+        a = rng.randrange(0, len(base) - 1300)
+        s = bytearray(base[a:a + rng.randint(1, 1300)])
+        if rng.random() < 0.3 and s:
+            s[rng.randrange(len(s))] = rng.choice(b"\x01`@#$\x7f")
+        w = np.frombuffer(bytes(s), np.uint8)
+        got, con = model_lex(lg, name, mode, w, **SMALL)
+        assert (got, con) == expected(name, mode, w), (a, len(s))
