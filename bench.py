@@ -28,12 +28,15 @@ sys.path.insert(0, ROOT)
 
 MiB = 1 << 20
 CUTS = {"arith": "newline ( ) * + - / ; (exact certificate, I empty)",
+        "clike_block_framed": "0x1E, reserved at the producer before every line or comment (exact certificate)",
         "json": "tab, newline, carriage return (certified modulo I = {ws})",
         "clike": "newline (certified modulo I = {ws, line comment})",
         "clike_block": "none certified: chunk starts every 4096 B after the byte with the fewest entry contexts"}
 
 
 def metric_name(workload, mib):
+    if workload == "clike_block_framed":
+        return f"input GB/s lexed ({mib} MiB framed C-like with block comments, full stream, exact cuts, bit-exact)"
     if workload == "arith":
         return f"input GB/s lexed ({mib} MiB arith token stream, full stream, exact cuts, bit-exact)"
     if workload == "clike_block":
@@ -43,6 +46,8 @@ def metric_name(workload, mib):
 
 
 def workload_name(workload, mib):
+    if workload == "clike_block_framed":
+        return f"clike_block_framed_{mib}mib_full_exact"
     if workload == "arith":
         return f"arith_{mib}mib_full_exact"
     if workload == "clike_block":
@@ -131,8 +136,8 @@ def profiled_traffic(workload_key):
     import hashlib
     import re
     try:
-        src = open(os.path.join(ROOT, "paper_2608_03473_gb300", "csrc", "lex.cu"), "rb").read()
-        text = open(os.path.join(ROOT, "profiles", "lex_tiles_dram_512mib.md")).read()
+        src = open(os.path.join(ROOT, "paper_2608_03473_gb300", "csrc", "lexwarp.cu"), "rb").read()
+        text = open(os.path.join(ROOT, "profiles", "lex_warps_dram_512mib.md")).read()
     except OSError:
         return None
     h = hashlib.sha256(src).hexdigest()
@@ -462,7 +467,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=7)
     ap.add_argument("--e2e-parts", type=int, default=8, help="batch workload: parts of the end-to-end pipeline")
     ap.add_argument("--size-mib", type=int, default=None, help="input size (default 512; arith: 1)")
-    ap.add_argument("--workload", default="json", choices=["json", "clike", "clike_block", "batch", "arith"])
+    ap.add_argument("--workload", default="json",
+                    choices=["json", "clike", "clike_block", "batch", "arith", "clike_block_framed"])
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true",
@@ -495,14 +501,23 @@ def main():
     n = args.size_mib * MiB
     w = corpus.generate(args.workload, n)
     sha = corpus.sha256(w) if rank == 0 else None
-    dfa = tokensets.tokenset(args.workload)
-    disc = tokensets.discarded_kinds(args.workload)
-    ts = lg.lx_compile_tokenset(dfa, disc)
+    framed = args.workload == "clike_block_framed"
+    if framed:
+        # Section 7.1: the refused C-like set with 0x1E reserved at the producer;
+        # the oracle lexes with the same automaton built on the host side
+        base = tokensets.tokenset("clike_block")
+        disc = tokensets.discarded_kinds("clike_block")
+        dfa = tokensets.framed(base)
+        ts = lg.lx_compile_tokenset_framed(base, disc, tokensets.FRAME)
+    else:
+        dfa = tokensets.tokenset(args.workload)
+        disc = tokensets.discarded_kinds(args.workload)
+        ts = lg.lx_compile_tokenset(dfa, disc)
     ctx = lg.lx_ctx_create()
     lg.lx_ctx_enable_timing(ctx, True)
     stream = torch.cuda.current_stream()
     refused = args.workload == "clike_block"
-    full = refused or args.workload == "arith"          # the full stream, exact cuts
+    full = refused or framed or args.workload == "arith"   # the full stream, exact cuts
     small = n < 256 * MiB                               # flush L2 between timed steps
     lex_fn = lg.lx_lex
     spec_model, train_s, spec_stats = None, None, {}
@@ -665,7 +680,8 @@ def main():
                          "traffic": profiled_traffic(workload_name(args.workload, args.size_mib)),
                          "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "kernel": "en_plan + model + sp_scan/sp_fix rounds + sp_offsets + en_emit" if refused
-                         else "lex_tiles",
+                         else ("lex_warps (warp-tile kernel)" if lg.lx_tokenset_walk_table(ts, mode)[0] == 0
+                               else "lex_tiles"),
                          "kernel_ms": k_ms,
                          "algorithmic_bytes": alg_bytes, "frac_of_nominal_8tbs": achieved / 8000.0},
             "cpu_baseline": cpu,
@@ -714,7 +730,7 @@ def main():
                 en_ms.append(lg.lx_ctx_last_kernel_ms(ctx))
             line["speculative"] = {"rounds": spec_stats.get("rounds"), "chunks": spec_stats.get("chunks"),
                                    "rescanned": spec_stats.get("rescanned"),
-                                   "model": "MLP 64-byte window, 8-d embedding, 64 hidden, BF16 inference",
+                                   "model": "64-byte window: 8-d embedding, conv1d 32x5 + ReLU, max-pool 4, 512-64-C MLP; BF16 weights, FP32 accumulation, AdamW",
                                    "train_s": train_s,
                                    "train_data": "2 x 64 MiB C-like-with-block-comments corpora, other seeds"}
             line["enumerative"] = {"kernel_ms": statistics.median(en_ms),

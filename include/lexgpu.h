@@ -344,15 +344,21 @@ int lx_chunk_contexts(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, u
                       uint16_t *d_ctx, uint64_t cap, uint64_t *count, void *stream);
 
 /*
- * Entry-context model (opaque, lives on the device that created it): a small
- * MLP over the 64 bytes around a chunk start (32 before, 32 after; a padding
- * value outside the input) scoring n_contexts = states + 1 classes
- * (class states = BOUNDARY): byte embedding (257 x 8), hidden layer of
- * `hidden` ReLU units, linear output.  FP32 master parameters trained with
- * Adam on mean softmax cross-entropy; predictions use a BF16 copy and take
- * the argmax over the candidate contexts of the byte before the start.
- * Parameters are exchanged as one FP32 array in the order: embedding
- * [257][8], W1 [512][hidden], b1 [hidden], W2 [hidden][n_contexts],
+ * Entry-context model (opaque, lives on the device that created it): a
+ * byte-window network over the 64 bytes around a chunk start (32 before, 32
+ * after; a padding value outside the input) scoring n_contexts = states + 1
+ * classes (class states = BOUNDARY): byte embedding (257 x 8), a 1D
+ * convolution of 32 filters of width 5 with ReLU, max pooling by 4 (16
+ * positions x 32 filters = 512 features), a hidden layer of `hidden` ReLU
+ * units and a linear output (49 915 parameters for hidden 64 and the 211
+ * contexts of the refused C-like set).  Every product reads BF16 weights
+ * and accumulates in FP32; the FP32 master parameters are trained with AdamW
+ * (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay 0.01 on the
+ * convolution and dense weight matrices) on mean softmax cross-entropy.
+ * Predictions take the argmax over the candidate contexts of the byte before
+ * the start.  Parameters are exchanged as one FP32 array in the order:
+ * embedding [257][8], conv weights [32][5][8], conv bias [32], W1
+ * [512][hidden] (feature u * 32 + f), b1 [hidden], W2 [hidden][n_contexts],
  * b2 [n_contexts].  Windows are u16 arrays of 64 byte values (256 = pad),
  * labels u16 class indices.
  */
@@ -371,7 +377,7 @@ int lx_model_forward(lx_model *m, const uint16_t *d_windows, uint32_t batch, flo
 /* gradient of the mean loss w.r.t. the parameters (host, parameter order) and the loss */
 int lx_model_gradient(lx_model *m, const uint16_t *d_windows, const uint16_t *d_labels, uint32_t batch,
                       float *host_grad, uint64_t count, float *loss, void *stream);
-/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on a batch; returns its loss before the step */
+/* one AdamW step on a batch (see above); returns its loss before the step */
 int lx_model_train_step(lx_model *m, const uint16_t *d_windows, const uint16_t *d_labels, uint32_t batch,
                         float lr, float *loss, void *stream);
 

@@ -49,7 +49,7 @@ constexpr uint32_t WT = 4096;                 // input bytes per warp tile
 constexpr uint32_t SLICE = WT / 32;           // bytes per lane slice (phase 1)
 constexpr uint32_t BLK = 16;                  // bytes per lockstep step of a lane
 constexpr uint32_t NB1 = SLICE / BLK;         // phase-1 steps
-constexpr uint32_t HALO = 1024;               // positions past the tile a chunk may end at
+constexpr uint32_t HALO = 512;                // positions past the tile a chunk may end at
 constexpr uint32_t EVB = WT + HALO;           // event buffer positions
 constexpr uint32_t LIMIT = EVB - BLK;         // chunk ends must lie below (room for the last block)
 // Event code of position p at ev + p + 4 (p >> 7): a 4-byte pad after every
@@ -61,8 +61,7 @@ constexpr uint32_t WAREA = EV_BYTES + 4 * STAGE_CAP;   // shared bytes per warp
 constexpr uint32_t GS = 64;                   // tiles per look-back group
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t BIG = 0x7FFFFFFFu;
-constexpr int NWARPS = 16;
-constexpr int NTHREADS = 32 * NWARPS;
+constexpr int MAX_WARPS = 20;                 // warps per CTA at most (as many as shared memory allows)
 constexpr unsigned ERR_TIMEOUT = 1u;
 constexpr unsigned ERR_SMEM = 2u;
 constexpr unsigned ERR_SPARSE = 4u;   // a chunk ran past the sparse limit: certified bytes too far apart
@@ -137,47 +136,47 @@ __device__ __forceinline__ uint32_t acc_code(const WEnv &E, uint32_t e)
 #define LXW_PRED1 "setp.ne.u32 ps, %0, %3;\n\t"
 #define LXW_PRED2 "setp.le.u32 ps, %4, %3;\n\t"
 #define LXW_B(XOP, VIN, VOUT)                                                  \
-    XOP "lop3.b32 a, " VIN ", t, 0x1FE, 0xD8;\n\t"                             \
+    XOP "lop3.b32 a, " VIN ", t, %7, 0xD8;\n\t"                                \
         "ld.shared.u16 " VOUT ", [a];\n\t"
 #define LXW_C(SEL, VIN, VOUT)                                                  \
     "prmt.b32 t, %2, %6, " SEL ";\n\t"                                         \
     "ld.shared.u8 c, [t];\n\t"                                                 \
-    "lop3.b32 a, " VIN ", c, 0xFF, 0xD8;\n\t"                                  \
+    "lop3.b32 a, " VIN ", c, %7, 0xD8;\n\t"                                    \
     "ld.shared.u16 " VOUT ", [a];\n\t"
 #define LXW_PACK                                                               \
     "prmt.b32 t0, v0, v1, 0x0040;\n\t"                                         \
-    "prmt.b32 t1, v2, v3, 0x0040;\n\t"                                         \
+    "prmt.b32 t1, v2, %0, 0x0040;\n\t"                                         \
     "prmt.b32 %1, t0, t1, 0x5410;\n\t"                                         \
-    "@ps st.shared.u32 [%5], %1;\n\t"                                          \
-    "mov.b32 %0, v3;\n\t}"
+    "@ps st.shared.u32 [%5], %1;\n\t}"
 #define LXW_BYTE_BODY                                                          \
     LXW_B("shl.b32 t, %2, 1;\n\t", "%0", "v0")                                 \
     LXW_B("shr.b32 t, %2, 7;\n\t", "v0", "v1")                                 \
     LXW_B("shr.b32 t, %2, 15;\n\t", "v1", "v2")                                \
-    LXW_B("shr.b32 t, %2, 23;\n\t", "v2", "v3")
+    LXW_B("shr.b32 t, %2, 23;\n\t", "v2", "%0")
 #define LXW_CLASS_BODY                                                         \
     LXW_C("0x7650", "%0", "v0")                                                \
     LXW_C("0x7651", "v0", "v1")                                                \
     LXW_C("0x7652", "v1", "v2")                                                \
-    LXW_C("0x7653", "v2", "v3")
+    LXW_C("0x7653", "v2", "%0")
 #define LXW_HEAD "{\n\t.reg .pred ps;\n\t.reg .b32 t, a, c, v0, v1, v2, v3, t0, t1;\n\t"
 
 template <int FORM, int PH>
 __device__ __forceinline__ uint32_t wword(uint32_t &e, uint32_t w, uint32_t ev, uint32_t x, uint32_t y, uint32_t cm)
 {
     uint32_t pk;
+    const uint32_t mask = FORM == FORM_BYTE ? 0x1FEu : 0xFFu;   // the address bits an entry's byte or class replaces
     if (FORM == FORM_BYTE && PH == 1)
         asm volatile(LXW_HEAD LXW_PRED1 LXW_BYTE_BODY LXW_PACK
-                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm), "r"(mask) : "memory");
     else if (FORM == FORM_BYTE)
         asm volatile(LXW_HEAD LXW_PRED2 LXW_BYTE_BODY LXW_PACK
-                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm), "r"(mask) : "memory");
     else if (PH == 1)
         asm volatile(LXW_HEAD LXW_PRED1 LXW_CLASS_BODY LXW_PACK
-                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm), "r"(mask) : "memory");
     else
         asm volatile(LXW_HEAD LXW_PRED2 LXW_CLASS_BODY LXW_PACK
-                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm) : "memory");
+                     : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm), "r"(mask) : "memory");
     return pk;
 }
 
@@ -323,11 +322,36 @@ __device__ void finalize(const WEnv &E, Lane &L, uint32_t hi)
 // chunk longer than `limit` bytes stops there and sets *over.
 constexpr uint64_t NONE64 = ~0ull;
 
+// Bytes of the input read through one 16-byte block held in registers (the
+// byte-by-byte walk of a long chunk would otherwise wait on a load per byte).
+struct ByteReader {
+    const uint8_t *in;
+    uint64_t n, pos = ~0ull;
+    uint4 b;
+    __device__ __forceinline__ uint32_t at(uint64_t q)
+    {
+        const uint64_t base = q & ~15ull;
+        if (base != pos) {
+            pos = base;
+            if (base + 16 <= n) {
+                b = __ldg(reinterpret_cast<const uint4 *>(in + base));
+            } else {
+                uint32_t w[4] = {0, 0, 0, 0};
+                for (uint32_t k = 0; base + k < n; k++) w[k >> 2] |= (uint32_t)__ldg(in + base + k) << (8 * (k & 3));
+                b = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        const uint32_t r = (uint32_t)(q & 15);
+        return byte_of(pick4(r >> 2, b.x, b.y, b.z, b.w), r & 3);
+    }
+};
+
 template <int FORM>
 __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail, uint16_t *kinds, uint32_t *lens,
                                   uint64_t cap, uint64_t o, uint64_t limit = 0, bool *over = nullptr)
 {
     const uint64_t n = E.nrel64;
+    ByteReader rd{E.in, n};
     uint64_t p = start, tok = start, cnt = 0;
     uint32_t e = E.P_start;
     *fail = NONE64;
@@ -353,7 +377,7 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
                 *over = true;
                 return cnt;
             }
-            const uint32_t b = __ldg(E.in + p);
+            const uint32_t b = rd.at(p);
             const uint32_t v = wstep<FORM>(E, e, b);
             if (v != E.P_slow) {
                 if (v & 0xFFu) {
@@ -370,7 +394,7 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
         uint32_t q = E.P_start, rc = 0;
         uint64_t r = NONE64;
         for (uint64_t k = tok; k < p; k++) {
-            const uint32_t v = wstep<FORM>(E, q, __ldg(E.in + k));
+            const uint32_t v = wstep<FORM>(E, q, rd.at(k));
             if ((v & 0xFFu) || v == E.P_slow) break;
             q = v;
             const uint32_t ac = acc_code(E, q);
@@ -387,8 +411,34 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
         tok = p = r;
         e = E.P_start;
         if (r == n) return cnt;
-        if (r >= WT && lds_u8(E.cut_s + __ldg(E.in + r))) return cnt;
+        if (r >= WT && lds_u8(E.cut_s + rd.at(r))) return cnt;
     }
+}
+
+// One byte of a word in the emission: byte K of w is an event code; d is
+// the distance from the previous event to this byte.  A kept code (>= 4)
+// stores (code << 16 | d) at s and advances s; any event sets d to 0; d
+// then steps to the next byte.  The PRMT takes d's low half and the code
+// byte (d < 65536, so d's byte 3 is zero).
+#define LXE_BYTE(K, SEL)                                                       \
+    "bfe.u32 c, %2, " #K "*8, 8;\n\t"                                         \
+    "setp.gt.u32 pk, c, 3;\n\t"                                                \
+    "setp.ne.u32 pe, c, 0;\n\t"                                                \
+    "prmt.b32 v, %1, %2, " SEL ";\n\t"                                         \
+    "@pk st.shared.u32 [%0], v;\n\t"                                           \
+    "@pk add.u32 %0, %0, 4;\n\t"                                               \
+    "@pe mov.u32 %1, 0;\n\t"                                                   \
+    "add.u32 %1, %1, 1;\n\t"
+
+// The kept codes of one word of the event buffer, in position order, into
+// the stage (s: next stage address, d: distance from the previous event to
+// the word's first byte); both are updated.
+__device__ __forceinline__ void emit_word(uint32_t &s, uint32_t &d, uint32_t w)
+{
+    asm volatile("{\n\t.reg .pred pk, pe;\n\t.reg .b32 c, v;\n\t"
+                 LXE_BYTE(0, "0x3410") LXE_BYTE(1, "0x3510") LXE_BYTE(2, "0x3610") LXE_BYTE(3, "0x3710")
+                 "}"
+                 : "+r"(s), "+r"(d) : "r"(w) : "memory");
 }
 
 __device__ __forceinline__ uint32_t kept_mask(uint32_t w)   // bit 7 of every byte >= 4 (a kept code)
@@ -408,18 +458,21 @@ __device__ __forceinline__ uint32_t event_mask(uint32_t w)  // bit 7 of every no
 // (a look-back over group words, a few dozen deep) plus the counts of the
 // tiles before it in the group.  Every wait is bounded by the time budget
 // and ends early once another warp has given up.
+// Polls back off exponentially (64 ns doubling to 4 us): while one slow tile
+// (say, a chunk walked byte by byte) holds up its group, thousands of waiting
+// warps must not flood L2 with status reads and starve that tile's own loads.
 struct Waiter {
     uint64_t t0;
     uint32_t spins;
     // false (and the error flag raised) once the budget is spent
     __device__ bool again(const WParams &P)
     {
-        if ((++spins & 15) == 0 &&
+        if ((++spins & 3) == 0 &&
             (globaltimer() - t0 > P.timeout_ns || *(volatile const unsigned int *)&P.res->error != 0)) {
             if ((threadIdx.x & 31) == 0) atomicOr(&P.res->error, ERR_TIMEOUT);
             return false;
         }
-        __nanosleep(64);
+        __nanosleep(64u << min(spins, 6u));
         return true;
     }
 };
@@ -445,6 +498,22 @@ __device__ void publish_tile(const WParams &P, uint32_t tile, uint64_t agg)
     if (lane == 0) st_status(&P.gstatus[g], (g == 0 ? ST_INCL : ST_AGG) | x);
 }
 
+// Lane 0 waits until status word *p is published; the warp learns whether
+// the wait ended in time.  Only one word is polled: thousands of waiting warps
+// re-reading whole rounds of status words would crowd the L2 lines that
+// every warp reads and slow the very tile they wait for.
+__device__ bool wait_word(const WParams &P, Waiter &W, const unsigned long long *p)
+{
+    uint32_t ok = 1;
+    if ((threadIdx.x & 31) == 0)
+        while (ld_status(p) == 0)
+            if (!W.again(P)) {
+                ok = 0;
+                break;
+            }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 // The output offset of `tile`; false when a wait ran out of time.
 __device__ bool resolve_tile(const WParams &P, uint32_t tile, uint64_t &G)
 {
@@ -454,15 +523,16 @@ __device__ bool resolve_tile(const WParams &P, uint32_t tile, uint64_t &G)
     // the tiles before this one in its group (at most GS - 1 < 64 words)
     unsigned long long w = 0;
     for (;;) {
-        bool miss = false;
+        uint32_t miss = NONE;
         w = 0;
         for (uint32_t j = f + lane; j < tile; j += 32) {
             const unsigned long long v = ld_status(&P.status[j]);
-            if (v == 0) miss = true;
+            if (v == 0) miss = min(miss, j);
             w += v & ST_VAL;
         }
-        if (!__any_sync(0xffffffffu, miss)) break;
-        if (!W.again(P)) return false;
+        miss = __reduce_min_sync(0xffffffffu, miss);
+        if (miss == NONE) break;
+        if (!wait_word(P, W, &P.status[miss])) return false;
     }
     for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     // the groups before: sum aggregates back to the nearest inclusive prefix
@@ -476,23 +546,23 @@ __device__ bool resolve_tile(const WParams &P, uint32_t tile, uint64_t &G)
             v[j] = k >= 0 ? ld_status(&P.gstatus[k]) : ST_INCL;
         }
         int jstar = LB_PER_LANE;
-        bool zero_before = false;
+        uint32_t zk = NONE;   // an unpublished group word of this lane before its first inclusive one
         unsigned long long lsum = 0;
 #pragma unroll
         for (int j = 0; j < LB_PER_LANE; j++) {
             if (jstar == LB_PER_LANE) {
                 const unsigned long long fl = v[j] & ~ST_VAL;
-                if (fl == 0) zero_before = true;
+                if (fl == 0 && zk == NONE) zk = (uint32_t)(base - (int64_t)LB_PER_LANE * lane - j);
                 lsum += v[j] & ST_VAL;
                 if (fl == ST_INCL) jstar = j;
             }
         }
         const unsigned incl = __ballot_sync(0xffffffffu, jstar < LB_PER_LANE);
-        const unsigned zero = __ballot_sync(0xffffffffu, zero_before);
         const unsigned upto = incl ? (incl & (0u - incl)) : 0u;
         const unsigned lanes = incl ? ((upto - 1u) | upto) : 0xffffffffu;
-        if (zero & lanes) {
-            if (!W.again(P)) return false;
+        const uint32_t wait_k = __reduce_min_sync(0xffffffffu, ((lanes >> lane) & 1u) ? zk : NONE);
+        if (wait_k != NONE) {
+            if (!wait_word(P, W, &P.gstatus[wait_k])) return false;
             continue;
         }
         unsigned long long x = ((lanes >> lane) & 1u) ? lsum : 0ull;
@@ -533,7 +603,7 @@ __device__ void copy_stage(const WParams &P, const WEnv &E, uint32_t stage, uint
         const uint64_t o = G + i;
         if (o < P.cap) {
             const uint32_t v = lds_u32(stage + 4 * i);
-            P.out_kinds[o] = (uint16_t)lds_u16(E.kmap_s + 2 * (v >> 16));
+            P.out_kinds[o] = (uint16_t)lds_u16(E.kmap_s + (v >> 16));
             P.out_lens[o] = v & 0xFFFFu;
         }
     }
@@ -549,8 +619,64 @@ __device__ __forceinline__ void zero16(uint32_t a)
     asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(a), "r"(0u) : "memory");
 }
 
+// Phase 1, one lockstep step of a lane: the block at L.p (words in `cur`),
+// or, where fewer than 16 bytes remain, the rest of the input byte by byte.
 template <int FORM>
-__global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
+__device__ __forceinline__ void phase1_step(const WEnv &E, Lane &L, const uint4 &cur)
+{
+    if (!L.act) return;
+    if (L.p + BLK <= E.nrel) {
+        const uint32_t pb = L.p, ev = eva(E, pb);
+        wword<FORM, 1>(L.e, cur.x, ev, E.P_pre, 0, E.cmap_s);
+        wword<FORM, 1>(L.e, cur.y, ev + 4, E.P_pre, 0, E.cmap_s);
+        wword<FORM, 1>(L.e, cur.z, ev + 8, E.P_pre, 0, E.cmap_s);
+        wword<FORM, 1>(L.e, cur.w, ev + 12, E.P_pre, 0, E.cmap_s);
+        if (L.s == NONE && L.e != E.P_pre) {   // PRE was left in this block (the byte: refine_start)
+            L.s = pb;
+            L.coarse = true;
+        }
+        L.p = pb + BLK;
+        if (L.e == E.P_slow) slow_fix<FORM>(E, L, L.p, BIG);
+    } else {
+        scalar_steps<FORM>(E, L, E.nrel, BIG);
+        finalize<FORM>(E, L, BIG);
+        L.act = false;
+    }
+}
+
+// Phase 2, one lockstep step of a lane: the block at L.p, storing the codes of
+// positions up to the chunk end `end`; the lane stops after the block that
+// holds the end.  `act` is the lane's phase-2 activity.
+template <int FORM>
+__device__ __forceinline__ void phase2_step(const WEnv &E, Lane &L, const uint4 &cur, uint32_t end, bool &act)
+{
+    if (!act) return;
+    if (L.p + BLK <= E.nrel) {
+        const uint32_t pb = L.p, ev = eva(E, pb);
+        const uint32_t pk0 = wword<FORM, 2>(L.e, cur.x, ev, end, pb + 3, E.cmap_s);
+        const uint32_t pk1 = wword<FORM, 2>(L.e, cur.y, ev + 4, end, pb + 7, E.cmap_s);
+        const uint32_t pk2 = wword<FORM, 2>(L.e, cur.z, ev + 8, end, pb + 11, E.cmap_s);
+        const uint32_t pk3 = wword<FORM, 2>(L.e, cur.w, ev + 12, end, pb + 15, E.cmap_s);
+        L.p = pb + BLK;
+        if (L.p > end) {
+            // the block holds the chunk end: the codes of its word up to the end
+            const uint32_t wk = (end - pb) >> 2, pk = pick4(wk, pk0, pk1, pk2, pk3);
+            for (uint32_t k = 0; k <= ((end - pb) & 3u); k++) sts_u8(ev + 4 * wk + k, byte_of(pk, k));
+            if (L.e == E.P_slow && byte_of(pk, (end - pb) & 3u) == 0) slow_fix<FORM>(E, L, L.p, end);
+            act = false;
+        } else if (L.e == E.P_slow) {
+            slow_fix<FORM>(E, L, L.p, end);
+            act = L.act;
+        }
+    } else {
+        scalar_steps<FORM>(E, L, E.nrel, end);
+        finalize<FORM>(E, L, end);
+        act = false;
+    }
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -648,33 +774,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
         L.own = NONE;
         L.act = t0 < nrel;
         L.coarse = false;
-        uint4 cur = blk_at(E, t0), n1 = blk_at(E, t0 + BLK), n2 = blk_at(E, t0 + 2 * BLK);
-        for (uint32_t it = 0; it < NB1; it++) {
-            if (!L.act) continue;
-            if (L.p + BLK <= nrel) {
-                const uint32_t pb = L.p, ev = eva(E, pb);
-                const uint32_t pk0 = wword<FORM, 1>(L.e, cur.x, ev, E.P_pre, 0, E.cmap_s);
-                const uint32_t pk1 = wword<FORM, 1>(L.e, cur.y, ev + 4, E.P_pre, 0, E.cmap_s);
-                const uint32_t pk2 = wword<FORM, 1>(L.e, cur.z, ev + 8, E.P_pre, 0, E.cmap_s);
-                const uint32_t pk3 = wword<FORM, 1>(L.e, cur.w, ev + 12, E.P_pre, 0, E.cmap_s);
-                (void)pk0;
-                (void)pk1;
-                (void)pk2;
-                (void)pk3;
-                if (L.s == NONE && L.e != E.P_pre) {   // PRE was left in this block (the byte: refine_start)
-                    L.s = pb;
-                    L.coarse = true;
-                }
-                L.p = pb + BLK;
-                cur = n1;
-                n1 = n2;
-                n2 = blk_at(E, L.p + 2 * BLK);
-                if (L.e == E.P_slow) slow_fix<FORM>(E, L, L.p, BIG);
-            } else {
-                scalar_steps<FORM>(E, L, nrel, BIG);
-                finalize<FORM>(E, L, BIG);
-                L.act = false;
-            }
+        // two register blocks in turn: a block is loaded two steps before it is walked
+        uint4 A = blk_at(E, t0), B = blk_at(E, t0 + BLK);
+#pragma unroll 1
+        for (uint32_t it = 0; it < NB1; it += 2) {
+            phase1_step<FORM>(E, L, A);
+            A = blk_at(E, L.p + BLK);
+            phase1_step<FORM>(E, L, B);
+            B = blk_at(E, L.p + BLK);
         }
 
         refine_start<FORM>(E, L);
@@ -693,34 +800,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
         bool act2 = L.act && L.s != NONE && end != NONE;
         L.own = end;
         while (__any_sync(0xffffffffu, act2)) {
-            if (!act2) continue;
-            if (L.p + BLK <= nrel) {
-                const uint32_t pb = L.p, ev = eva(E, pb);
-                const uint32_t pk0 = wword<FORM, 2>(L.e, cur.x, ev, end, pb + 3, E.cmap_s);
-                const uint32_t pk1 = wword<FORM, 2>(L.e, cur.y, ev + 4, end, pb + 7, E.cmap_s);
-                const uint32_t pk2 = wword<FORM, 2>(L.e, cur.z, ev + 8, end, pb + 11, E.cmap_s);
-                const uint32_t pk3 = wword<FORM, 2>(L.e, cur.w, ev + 12, end, pb + 15, E.cmap_s);
-                L.p = pb + BLK;
-                if (L.p > end) {
-                    // the block holds the chunk end: the codes of its word up to the end
-                    const uint32_t wk = (end - pb) >> 2, pk = pick4(wk, pk0, pk1, pk2, pk3);
-                    for (uint32_t k = 0; k <= ((end - pb) & 3u); k++) sts_u8(ev + 4 * wk + k, byte_of(pk, k));
-                    if (L.e == E.P_slow && byte_of(pk, (end - pb) & 3u) == 0) slow_fix<FORM>(E, L, L.p, end);
-                    act2 = false;
-                } else {
-                    cur = n1;
-                    n1 = n2;
-                    n2 = blk_at(E, L.p + 2 * BLK);
-                    if (L.e == E.P_slow) {
-                        slow_fix<FORM>(E, L, L.p, end);
-                        act2 = L.act;
-                    }
-                }
-            } else {
-                scalar_steps<FORM>(E, L, nrel, end);
-                finalize<FORM>(E, L, end);
-                act2 = false;
-            }
+            phase2_step<FORM>(E, L, A, end, act2);
+            if (act2) A = blk_at(E, L.p + BLK);
+            if (!__any_sync(0xffffffffu, act2)) break;
+            phase2_step<FORM>(E, L, B, end, act2);
+            if (act2) B = blk_at(E, L.p + BLK);
         }
         __syncwarp();
 
@@ -730,6 +814,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
         uint32_t hi = c1 != NONE ? c1 : long_s1 - 1;
         if (fail < hi) hi = fail;
         uint32_t wa = 0, wb = 0, last = 0, cnt = 0;
+        uint64_t wm = 0;   // words of this lane's slice holding a code (bit i: word wa + i)
         if (c0 != NONE) {
             if (hi != c1) {   // a failure or a chunk past the halo: clear every code after hi
                 const uint32_t z0 = eva(E, hi) + 1, z1 = (z0 + 15u) & ~15u;
@@ -744,7 +829,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
             for (uint32_t i = wa; i < wb; i++) {
                 const uint32_t w = lds_u32(eva(E, 4 * i));
                 cnt += __popc(kept_mask(w));
-                if (w) last = 4 * i + (31 - __clz(w)) / 8;
+                wm |= (uint64_t)(w != 0) << (i - wa);
+            }
+            if (wm) {   // the lane's last code
+                const uint32_t i = wa + 63 - __clzll(wm);
+                last = 4 * i + (31 - __clz(lds_u32(eva(E, 4 * i)))) / 8;
             }
         }
         uint32_t excl = cnt;
@@ -797,18 +886,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
             }
             prev = __shfl_up_sync(0xffffffffu, prev, 1);
             if (lane == 0 || prev < c0) prev = c0;
-            uint32_t idx = excl;
-            for (uint32_t i = wa; i < wb; i++) {
-                const uint32_t w = lds_u32(eva(E, 4 * i));
-                uint32_t nz = event_mask(w);
-                while (nz) {
+            if (fast_total <= STAGE_CAP) {
+                // every lane its words, four codes per word without branches;
+                // the words read are cleared for the next tile
+                uint32_t sa = stage + 4 * excl, d = 4 * wa - prev;
+                for (uint32_t i = wa; i < wb; i++) {
+                    const uint32_t a = eva(E, 4 * i);
+                    emit_word(sa, d, lds_u32(a));
+                    sts_u32(a, 0);
+                }
+            } else {
+            // more kept codes than the stage holds: one code per lane and
+            // iteration, the next non-empty word taken from the word mask
+            uint32_t idx = excl, w = 0, nz = 0, wpos = 0;
+            uint64_t todo = wm;
+            for (;;) {
+                if (nz == 0 && todo) {
+                    const uint32_t i = wa + __ffsll(todo) - 1;
+                    todo &= todo - 1;
+                    w = lds_u32(eva(E, 4 * i));
+                    nz = event_mask(w);
+                    wpos = 4 * i;
+                }
+                if (!__any_sync(0xffffffffu, nz != 0)) break;
+                if (nz) {
                     const uint32_t bit = __ffs(nz) - 1;   // 8k + 7
                     nz &= nz - 1;
                     const uint32_t code = (w >> (bit - 7)) & 0xFFu;
-                    const uint32_t pos = 4 * i + (bit >> 3);
+                    const uint32_t pos = wpos + (bit >> 3);
                     if (code >= 4) {
                         if (idx < STAGE_CAP) {
-                            sts_u32(stage + 4 * idx, ((code >> 1) << 16) | (pos - prev));
+                            sts_u32(stage + 4 * idx, (code << 16) | (pos - prev));
                         } else if (G + idx < P.cap) {
                             P.out_kinds[G + idx] = (uint16_t)lds_u16(E.kmap_s + 2 * (code >> 1));
                             P.out_lens[G + idx] = pos - prev;
@@ -819,6 +927,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
                 }
             }
             for (uint32_t i = wa; i < wb; i++) sts_u32(eva(E, 4 * i), 0);   // clear the codes read
+            }
         }
         __syncwarp();
         if (defer) {
@@ -847,9 +956,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) lex_warps(WParams P)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-int warp_occupancy(lx_ctx *c, int form, uint32_t smem, int *occ)
+constexpr uint32_t SMEM_BUDGET = 227 * 1024;   // dynamic shared memory one CTA may use
+
+int warp_occupancy(lx_ctx *c, int form, uint32_t threads, uint32_t smem, int *occ)
 {
-    const uint64_t key = (3ull << 40) | ((uint64_t)form << 32) | smem;
+    const uint64_t key = (3ull << 40) | ((uint64_t)threads << 33) | ((uint64_t)form << 32) | smem;
     for (auto &kv : c->occupancy)
         if (kv.first == key) {
             *occ = kv.second;
@@ -858,12 +969,12 @@ int warp_occupancy(lx_ctx *c, int form, uint32_t smem, int *occ)
     cudaError_t e;
     int o = 0;
     if (form == FORM_BYTE) {
-        e = cudaFuncSetAttribute(lex_warps<FORM_BYTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_BYTE>, NTHREADS, smem);
+        e = cudaFuncSetAttribute(lex_warps<FORM_BYTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_BYTE>, threads, smem);
     } else {
-        e = cudaFuncSetAttribute(lex_warps<FORM_CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        e = cudaFuncSetAttribute(lex_warps<FORM_CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_CLASS>, NTHREADS, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_CLASS>, threads, smem);
     }
     if (e != cudaSuccess) return LX_E_CUDA;
     if (o < 1) return LX_E_TOOBIG;
@@ -898,11 +1009,15 @@ int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint6
     const uint64_t n_tiles64 = (n + WT - 1) / WT;
     if (n_tiles64 > 0xFFFFFFF0ull) return LX_E_INVAL;
     const uint32_t n_tiles = (uint32_t)n_tiles64;
-    const uint32_t smem = 512 + (uint32_t)w.blob.size() + 16 + NWARPS * WAREA;
+    // as many warps per CTA as one SM's shared memory holds next to the table
+    const uint32_t fixed = 512 + (uint32_t)w.blob.size() + 16;
+    const uint32_t nwarps = std::min<uint32_t>(MAX_WARPS, (SMEM_BUDGET - fixed) / WAREA);
+    if (nwarps < 1) return LX_E_TOOBIG;
+    const uint32_t smem = fixed + nwarps * WAREA;
     int occ = 0;
-    rc = warp_occupancy(c, w.form, smem, &occ);
+    rc = warp_occupancy(c, w.form, 32 * nwarps, smem, &occ);
     if (rc != LX_OK) return rc;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * c->num_sms, (n_tiles + NWARPS - 1) / NWARPS);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * c->num_sms, (n_tiles + nwarps - 1) / nwarps);
 
     const uint32_t n_groups = (n_tiles + GS - 1) / GS;
     const size_t o_gstatus = 64 + 8 * (size_t)n_tiles, o_gdone = o_gstatus + 8 * (size_t)n_groups;
@@ -940,8 +1055,8 @@ int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint6
     rc = cuda_err(cudaMemsetAsync(c->scratch, 0, need, st));
     if (rc != LX_OK) return rc;
     if (c->timing) cudaEventRecord(c->ev[0], st);
-    if (w.form == FORM_BYTE) lex_warps<FORM_BYTE><<<grid, NTHREADS, smem, st>>>(P);
-    else lex_warps<FORM_CLASS><<<grid, NTHREADS, smem, st>>>(P);
+    if (w.form == FORM_BYTE) lex_warps<FORM_BYTE><<<grid, 32 * nwarps, smem, st>>>(P);
+    else lex_warps<FORM_CLASS><<<grid, 32 * nwarps, smem, st>>>(P);
     rc = cuda_err(cudaGetLastError());
     if (c->timing) cudaEventRecord(c->ev[1], st);
     if (rc != LX_OK) return rc;

@@ -1,8 +1,9 @@
 """Speculative lexing of a refused token set and its entry-context model (GPU).
 
 * lx_chunk_contexts labels equal the oracle's context() at every chunk start;
-* model windows, FP32 forward and gradient equal the FP64 reference
-  (oracle/model.py) within FP32 tolerances; Adam steps lower the loss;
+* model windows, the BF16-weight forward and gradient equal the FP64
+  reference (oracle/model.py, at the BF16-rounded weights) within FP32
+  tolerances, block by block; AdamW steps lower the loss;
 * lx_lex_speculative equals the serial oracle bit for bit with no model, a
   random model and a trained one (predictions only change the rescans), on
   the refused C-like corpus, malformed and ragged inputs.
@@ -72,7 +73,10 @@ def test_model_forward_and_gradient_match_reference(env):
     win = m.windows(d, torch.from_numpy(pos).cuda())
     ref_win = OM.windows(w, pos)
     assert np.array_equal(win.cpu().numpy().astype(np.int64) & 0xFFFF, ref_win)
-    p = m.get_params().astype(np.float64)
+    # the device computes with BF16 weights and FP32 activations and sums:
+    # against the FP64 reference at the BF16-rounded weights only FP32
+    # rounding remains
+    p = OM.to_bf16(m.get_params().astype(np.float64))
     z = m.forward(win).cpu().numpy()
     rz, _ = OM.forward(p, ref_win, 32, C)
     assert np.max(np.abs(z - rz)) < 1e-4 * (1 + np.max(np.abs(rz)))
@@ -80,7 +84,11 @@ def test_model_forward_and_gradient_match_reference(env):
     g, loss = m.gradient(win, torch.from_numpy(y.astype(np.int16)).cuda())
     rl, rg = OM.loss_and_grad(p, ref_win, y, 32, C)
     assert abs(loss - rl) < 1e-4 * (1 + abs(rl))
-    assert np.max(np.abs(g - rg)) < 1e-5 + 1e-3 * np.max(np.abs(rg)), np.max(np.abs(g - rg))
+    blocks = np.cumsum([0] + OM.sizes(32, C))
+    for lo, hi in zip(blocks[:-1], blocks[1:]):   # every parameter block
+        assert np.max(np.abs(g[lo:hi] - rg[lo:hi])) < 1e-5 + 1e-3 * np.max(np.abs(rg[lo:hi])), (lo, hi)
+    # and the BF16 weights are the round-to-nearest-even of the FP32 ones
+    assert m.n_params == OM.n_params(32, C)
 
 
 def test_training_lowers_the_loss(env):

@@ -51,7 +51,7 @@ class Walk:
 
 
 class WarpModel:
-    def __init__(self, walk, wt=4096, halo=1024, blk=16):
+    def __init__(self, walk, wt=4096, halo=512, blk=16):
         self.W = walk
         self.WT, self.SLICE, self.HALO, self.BLK = wt, wt // 32, halo, blk
         self.EVB = wt + halo
@@ -304,10 +304,43 @@ class WarpModel:
                 if code >= 4:
                     out.append((int(W.kmap[code >> 1]), p - prev))
                 prev = p
+        assert self.emit_words(c0, hi) == out
         if long_s != NONE and fail > long_s:
             _, f2 = self.generic(long_s, out)
             fail = f2 if f2 != NONE else fail
         return out, fail, True
+
+
+    def emit_words(self, c0, hi):
+        """The kernel's emission: the words holding positions c0 + 1 .. hi
+        split into 32 contiguous lane ranges; each lane starts from the last
+        event of the lanes before it (or c0) and runs four bytes per word with
+        a 32-bit wrapping distance, of which the stage keeps the low 16 bits."""
+        W = self.W
+        ev = np.zeros(len(self.ev) + 4, np.int64)
+        ev[:len(self.ev)] = self.ev
+        ev[hi + 1:] = 0          # the kernel clears the codes after hi when hi is not the halo's byte
+        w0, w1 = (c0 + 1) >> 2, max((hi >> 2) + 1, (c0 + 1) >> 2)
+        per = (w1 - w0 + 31) // 32
+        lanes = [(min(w0 + i * per, w1), min(min(w0 + i * per, w1) + per, w1)) for i in range(32)]
+        last = []
+        for wa, wb in lanes:
+            nz = [p for p in range(4 * wa, 4 * wb) if ev[p]]
+            last.append(nz[-1] if nz else 0)
+        out = []
+        for i, (wa, wb) in enumerate(lanes):
+            prev = max(last[:i], default=0)
+            if i == 0 or prev < c0:
+                prev = c0
+            d = (4 * wa - prev) & 0xFFFFFFFF
+            for p in range(4 * wa, 4 * wb):
+                c = int(ev[p])
+                if c > 3:
+                    out.append((int(W.kmap[c >> 1]), d & 0xFFFF))
+                if c:
+                    d = 0
+                d = (d + 1) & 0xFFFFFFFF
+        return out
 
 
 def model_lex(lg, name, mode, w, **geo):
