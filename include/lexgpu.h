@@ -163,6 +163,28 @@ int lx_tokenset_class_table(const lx_tokenset *ts, int mode, void *out, uint32_t
 int lx_tokenset_walk_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
                            uint32_t meta_len);
 
+/*
+ * lx_tokenset_liveness -- the liveness automaton of the failed-lookahead guard
+ * (for inspection and tests).  Read from right to left over the input, its
+ * state after w[k..n) stands for the set
+ *   live_k = { q in Q+ : delta+*(q, w[k..m)) is accepting for some m > k }
+ * (empty at k = n): the states from which a scan at offset k still has an
+ * accepting position ahead.  A scan whose state is outside live_k has passed
+ * its last accepting position and may end its token at once -- the memo of
+ * failed (state, position) pairs of Reps' maximal-munch scanner, computed in
+ * one pass before the scan.  Its states are the distinct sets reachable from
+ * the empty set under F_c(X) = { q in Q+ : delta+(q, c) accepts or lies in X }.
+ * Copies min(cap, size) bytes of the blob to `out` (host, may be NULL) and
+ * fills meta[0..7] = { blob bytes, R (automaton states), C (classes), S (DFA
+ * states), W (member words per state), next offset, reset offset, member
+ * offset }.  Blob: byte_class u8[256]; next u8[C * R] (state r on class c at
+ * c * R + r; state 0 is the empty set); reset u8[C] (1: F_c is the same for
+ * every state); member u32[R * W] (bit q of state r's words: q in the set).
+ * LX_E_TOOBIG when more than 255 sets are reachable (no guard: the scans then
+ * run unguarded, exact and possibly quadratic).
+ */
+int lx_tokenset_liveness(const lx_tokenset *ts, void *out, uint32_t cap, uint32_t *meta, uint32_t meta_len);
+
 /* Release a token set (NULL is a no-op).  Frees its device tables. */
 void lx_tokenset_free(lx_tokenset *ts);
 
@@ -326,10 +348,32 @@ int lx_autotune(lx_ctx *ctx, const lx_tokenset *ts, int mode, const uint8_t *d_s
  * (the certificates play no part), con(w) in *consumed (Corollary 1).
  * Works for any token set; LX_E_TOOBIG when its plain DFA table exceeds the
  * shared-memory budget.  Synchronizes `stream`.
+ *
+ * Failed-lookahead guard (Section 9): a chunk scan that takes more than
+ * 32 x 4096 steps (failed lookahead repeated at successive token starts, as
+ * over the tokens a, a+b and ; on a^n, or a token spanning many chunks) makes
+ * the call run again with the liveness prepass (lx_liveness): every scan then
+ * ends its token as soon as no accepting position lies ahead, and a chunk
+ * entered inside a token that runs past its end stops there, so the work is
+ * linear in n.  Same output; lx_lex takes this route too when its own
+ * backtracking exceeds a budget linear in the chunk lengths.
  */
 int lx_lex_enumerative(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
                        uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
                        uint64_t *consumed, void *stream);
+
+/*
+ * lx_liveness -- the guard's prepass on its own: the state of the liveness
+ * automaton (lx_tokenset_liveness) at every offset 0..n of the device buffer
+ * d_in into d_live[0..n] (device, n + 1 bytes, caller-owned; d_live[n] = 0,
+ * the empty set).  The run from right to left is split into 4096-byte pieces:
+ * each piece's map from its end state to its start state (runs that meet a
+ * reset class merge), composed in groups and linked from offset n, then
+ * every piece run from its end state.  Stream-ordered, no synchronization.
+ * LX_E_TOOBIG when the token set has no liveness automaton.
+ */
+int lx_liveness(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, uint8_t *d_live,
+                void *stream);
 
 /*
  * lx_chunk_contexts -- the chunk starts lx_lex_enumerative plans for `d_in`

@@ -136,6 +136,13 @@ def utf8_tokens() -> List[Token]:
     ]
 
 
+def lookahead_tokens() -> List[Token]:
+    """Section 9's failed-lookahead example: a, a+b and ;.  On a^n every token
+    start reads on to the end looking for b (Theta(n^2) steps unguarded), and
+    ';' certifies but never occurs."""
+    return [Token("a", "a"), Token("apb", "a+b"), Token("semi", lit(";"))]
+
+
 def ab_dead_chain() -> DFA:
     """T1 = ab.(empty) beside T2 = b, as the paper's automaton:
     q0 -a-> q2 -b-> q1 (no acceptance reachable), q0 -b-> q3 accepting T2."""
@@ -158,6 +165,7 @@ _SETS: Dict[str, Tuple] = {
     "clike_block": (lambda: clike_tokens(True), ("ws", "line_comment", "block_comment")),
     "clike_row1": (single_byte_clike_tokens, ("ws",)),
     "utf8": (utf8_tokens, ()),
+    "lookahead": (lookahead_tokens, ()),
 }
 
 

@@ -54,7 +54,7 @@ LX_FILTERED_MODULO = 2
 # every function declared in include/lexgpu.h
 EXPORTED = (
     "lx_compile_tokenset", "lx_compile_tokenset_framed", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_class_table",
-    "lx_tokenset_walk_table", "lx_tokenset_scan_table",
+    "lx_tokenset_walk_table", "lx_tokenset_scan_table", "lx_tokenset_liveness", "lx_liveness",
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
     "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold", "lx_ctx_set_kernel",
@@ -112,6 +112,8 @@ def load_library(path: Optional[str] = None):
             "lx_tokenset_class_table": (i32, [vp, i32, vp, u32, vp, u32]),
             "lx_tokenset_walk_table": (i32, [vp, i32, vp, u32, vp, u32]),
             "lx_tokenset_scan_table": (i32, [vp, vp, u32, vp, u32]),
+            "lx_tokenset_liveness": (i32, [vp, vp, u32, vp, u32]),
+            "lx_liveness": (i32, [vp, vp, vp, u64, vp, vp]),
             "lx_tokenset_free": (None, [vp]),
             "lx_ctx_create": (i32, [vp]),
             "lx_ctx_free": (None, [vp]),
@@ -431,6 +433,28 @@ def lx_tokenset_scan_table(ts: Tokenset):
     rc = lib.lx_tokenset_scan_table(ts.handle, blob.ctypes.data, meta[0], meta, 9)
     keys = ("bytes", "S", "C", "q0", "next_off", "acc_off", "cbeg_off", "cand_off", "max_cand")
     return rc, blob[:meta[0]], dict(zip(keys, list(meta)))
+
+
+def lx_tokenset_liveness(ts: Tokenset):
+    """(status, blob uint8 array, meta dict) of the liveness automaton of the
+    failed-lookahead guard."""
+    lib = load_library()
+    meta = (ctypes.c_uint32 * 8)()
+    lib.lx_tokenset_liveness(ts.handle, None, 0, meta, 8)
+    blob = np.zeros(max(meta[0], 1), np.uint8)
+    rc = lib.lx_tokenset_liveness(ts.handle, blob.ctypes.data, meta[0], meta, 8)
+    keys = ("bytes", "R", "C", "S", "W", "next_off", "reset_off", "member_off")
+    return rc, blob[:meta[0]], dict(zip(keys, list(meta)))
+
+
+def lx_liveness(ctx: Ctx, ts: Tokenset, d_in, d_live, n: Optional[int] = None, stream=None) -> int:
+    """The liveness automaton's state at every offset 0..n of the device
+    buffer d_in into the device buffer d_live (n + 1 bytes)."""
+    lib = load_library()
+    n = d_in.numel() if n is None else int(n)
+    if d_live.numel() < n + 1:
+        raise ValueError("d_live needs n + 1 bytes")
+    return lib.lx_liveness(ctx.handle, ts.handle, d_in.data_ptr(), n, d_live.data_ptr(), _stream_handle(stream))
 
 
 LX_KS_MIN, LX_KS_MAX = 16, 96

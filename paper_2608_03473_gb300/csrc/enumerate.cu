@@ -44,6 +44,9 @@ constexpr int RS_NT = 1024;            // threads of the resolve kernel
 constexpr int SO_NT = 1024;            // threads of the offset kernels (one chunk each)
 constexpr uint32_t R1 = 16;            // chunks per run of the resolve kernels
 constexpr uint32_t SPEC_ROUNDS = 4;    // speculative rounds before the enumerative judge
+constexpr uint32_t STEP_BUDGET = 32 * 4096;   // steps of one unguarded chunk scan before the guard is called for
+constexpr unsigned EN_ERR_STATE = 1u;  // the resolve step met an impossible chain (never on valid tables)
+constexpr unsigned EN_ERR_LOOKAHEAD = 2u;   // a scan ran past STEP_BUDGET
 constexpr uint64_t NOPOS64 = ~0ull;
 constexpr uint32_t NONE32_EN = 0xFFFFFFFFu;
 constexpr uint16_t CTX_B = 0xFFFEu;    // context: at a token boundary
@@ -84,6 +87,13 @@ struct EnParams {
     const uint8_t *blob;         // ScanTable blob
     uint32_t blob_bytes, S, q0, next_off, acc_off, cbeg_off, cand_off;
     uint32_t keep_all;           // full stream: every token is kept
+    // the failed-lookahead guard: the liveness automaton's state at every
+    // offset and its member bitsets (live == nullptr: unguarded, each scan
+    // within a step budget)
+    const uint8_t *live;
+    const uint32_t *lmem;
+    uint32_t lw;                 // member words per automaton state
+    uint32_t budget;             // steps of an unguarded scan (~0u: no limit)
     uint32_t M;                  // chunk targets
     uint64_t *start;             // [M] chunk start offset, NOPOS64 = no chunk
     uint32_t *cinfo;             // [M] byte before the start << 8 | candidates
@@ -122,6 +132,10 @@ struct ScanEnv {
     uint32_t S, q0, keep_all;
     const uint8_t *in;
     uint64_t n;
+    const uint8_t *live;
+    const uint32_t *lmem;
+    uint32_t lw, budget;
+    unsigned int *error;
 };
 
 __device__ __forceinline__ ScanEnv stage_scan(const EnParams &P, uint8_t *smem)
@@ -143,7 +157,19 @@ __device__ __forceinline__ ScanEnv stage_scan(const EnParams &P, uint8_t *smem)
     E.keep_all = P.keep_all;
     E.in = P.in;
     E.n = P.n;
+    E.live = P.live;
+    E.lmem = P.lmem;
+    E.lw = P.lw;
+    E.budget = P.budget;
+    E.error = &P.rec->error;
     return E;
+}
+
+// Whether state q has an accepting position ahead of offset k (the guard).
+__device__ __forceinline__ bool lv_has(const ScanEnv &E, uint32_t q, uint64_t k)
+{
+    const uint32_t r = __ldg(E.live + k);
+    return (__ldg(E.lmem + r * E.lw + (q >> 5)) >> (q & 31)) & 1u;
 }
 
 // A lane's view of the input: a 16-byte block of its chunk held in
@@ -251,6 +277,13 @@ struct WriteTok {
 // that began before p0 and is not emitted.  The state at p1 of the run that
 // crosses it is kept: when the last token runs past p1, that state is the
 // context at p1.
+//
+// Guarded (E.live set): a run also ends where its state has no accepting
+// position ahead (it has passed its last one, so the token is the same), and
+// an entry run that reaches p1 with one ahead stops there: its token runs
+// past p1, so the context at p1 is its state.  Every token then costs its own
+// length plus one step.  Unguarded, a lane that takes more than STEP_BUDGET
+// steps gives up and flags EN_ERR_LOOKAHEAD; the caller runs again guarded.
 template <class Emit>
 __device__ uint16_t chunk_scan(const ScanEnv &E, bool has, uint64_t p0, uint64_t p1, uint16_t ctx, Emit &emit,
                                uint64_t &fail)
@@ -261,13 +294,29 @@ __device__ uint16_t chunk_scan(const ScanEnv &E, bool has, uint64_t p0, uint64_t
     uint16_t res = CTX_B;
     bool run = has && (entered || p0 < p1);
     uint64_t tok = p0, j = p0, last = NOPOS64;
-    uint32_t qs = entered ? ctx : E.q0, q = qs, lq = 0, qp1 = qs;
+    uint32_t qs = entered ? ctx : E.q0, q = qs, lq = 0, qp1 = qs, steps = 0;
     bool first = entered;
+    const bool guarded = E.live != nullptr;
     while (__any_sync(0xffffffffu, run)) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             if (!run) break;
-            const uint32_t t = j < E.n ? delta(E, q, by(j)) : (uint32_t)SCAN_NONE;
+            uint32_t t = j < E.n ? delta(E, q, by(j)) : (uint32_t)SCAN_NONE;
+            if (guarded) {
+                if (!lv_has(E, q, j)) {
+                    t = SCAN_NONE;   // no accepting position ahead: the run ends here
+                } else if (first && j == p1) {
+                    res = (uint16_t)q;   // the entered token runs past p1
+                    run = false;
+                    break;
+                }
+            } else if (++steps > E.budget) {
+                atomicOr(E.error, EN_ERR_LOOKAHEAD);
+                res = CTX_BAD;
+                fail = NOPOS64;
+                run = false;
+                break;
+            }
             if (t != SCAN_NONE) {
                 q = t & ~(uint32_t)SCAN_ACCEPT;
                 j++;
@@ -538,7 +587,7 @@ __global__ void __launch_bounds__(RS_NT) en_link(EnParams P)
             if (first[r] == NONE32_EN) continue;
             const int k = cand_index(E, P.cinfo[P.first1[first[r]]] >> 8, ctx);
             if (k < 0) {
-                P.rec->error = 1;
+                P.rec->error |= EN_ERR_STATE;
                 break;
             }
             const Summary s = sum[r * KMAX + k];
@@ -551,7 +600,7 @@ __global__ void __launch_bounds__(RS_NT) en_link(EnParams P)
                 break;
             }
             if (s.state != 1) {
-                P.rec->error = 1;
+                P.rec->error |= EN_ERR_STATE;
                 break;
             }
             run += s.count;
@@ -975,6 +1024,10 @@ int en_setup(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
     P.rescans = reinterpret_cast<unsigned int *>(d + o_flags + 4);
     P.rounds_used = reinterpret_cast<unsigned int *>(d + o_flags + 8);
     P.guess = nullptr;
+    P.live = nullptr;
+    P.lmem = nullptr;
+    P.lw = 0;
+    P.budget = STEP_BUDGET;
     P.st_kinds = stage ? reinterpret_cast<uint16_t *>(d + o_stk) : nullptr;
     P.st_lens = stage ? reinterpret_cast<uint32_t *>(d + o_stl) : nullptr;
     P.blk_sum = reinterpret_cast<unsigned long long *>(d + o_bsum);
@@ -1026,69 +1079,50 @@ int en_finish(lx_ctx *c, const EnRun &R, uint64_t capacity, uint64_t *n_tokens, 
     std::memcpy(buf, c->h_res, sizeof(EnResult));
     EnResult r;
     std::memcpy(&r, buf, sizeof r);
+    if (r.error & EN_ERR_LOOKAHEAD) return LX_LOOKAHEAD;
     if (r.error) return LX_E_CUDA;
     *n_tokens = r.total;
     *consumed = r.fail == NOPOS64 ? R.P.n : r.fail;
     return r.total > capacity ? LX_E_CAPACITY : LX_OK;
 }
 
-}  // namespace
-
-extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
-                                  uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
-                                  uint64_t *consumed, void *stream)
+// After a scan flagged EN_ERR_LOOKAHEAD: the guard's prepass over the input,
+// and the record cleared for the next run.  Without a liveness automaton the
+// next run goes unguarded with no step budget (exact, possibly quadratic).
+int en_guard(lx_ctx *c, const lx_tokenset *ts, EnRun &R)
 {
-    if (!n_tokens || !consumed) return LX_E_INVAL;
-    *n_tokens = 0;
-    *consumed = 0;
-    EnRun R;
-    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R);
-    if (rc != LX_OK || n == 0) return rc;
-    if (c->timing) cudaEventRecord(c->ev[0], R.s);
+    const uint8_t *live = nullptr;
+    const uint32_t *member = nullptr;
+    const int rc = liveness_device(c, ts, R.P.in, R.P.n, nullptr, R.s, &live, &member);
+    if (rc == LX_OK) {
+        R.P.live = live;
+        R.P.lmem = member;
+        R.P.lw = ts->liveness.W;
+    } else if (rc == LX_E_TOOBIG) {
+        R.P.budget = ~0u;
+    } else {
+        return rc;
+    }
+    return cuda_err(cudaMemsetAsync(R.P.rec, 0, 256, R.s));
+}
+
+// The enumerative pipeline (plan .. emit) on a prepared run.
+void en_pipeline(const EnRun &R)
+{
     en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
     en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
     en_sum<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
     en_link<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
     en_label<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
     en_emit<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
-    if (c->timing) cudaEventRecord(c->ev[1], R.s);
-    return en_finish(c, R, capacity, n_tokens, consumed);
 }
 
-extern "C" int lx_chunk_contexts(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n,
-                                 uint64_t *d_starts, uint16_t *d_ctx, uint64_t cap, uint64_t *count, void *stream)
+// The speculative pipeline (plan .. copy) on a prepared run; the record's
+// status as en_finish reads it.
+int spec_pipeline(lx_ctx *c, EnRun &R, lx_model *model, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed,
+                  lx_spec_stats *stats)
 {
-    if (!count || (cap && (!d_starts || !d_ctx))) return LX_E_INVAL;
-    *count = 0;
-    EnRun R;
-    int rc = en_setup(c, ts, d_in, n, LX_FULL_EXACT, nullptr, nullptr, 0, stream, R);
-    if (rc != LX_OK || n == 0) return rc;
-    *count = R.P.M;
-    if (cap < R.P.M) return LX_E_CAPACITY;
-    en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
-    en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
-    en_sum<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
-    en_link<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
-    en_label<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
-    ctx_export<<<R.grid, EN_NT, 0, R.s>>>(R.P, d_starts, d_ctx);
-    uint64_t nt, con;
-    rc = en_finish(c, R, ~0ull, &nt, &con);
-    return rc;
-}
-
-extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *model, const uint8_t *d_in,
-                                  uint64_t n, int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity,
-                                  uint64_t *n_tokens, uint64_t *consumed, lx_spec_stats *stats, void *stream)
-{
-    if (!n_tokens || !consumed) return LX_E_INVAL;
-    *n_tokens = 0;
-    *consumed = 0;
-    if (stats) *stats = lx_spec_stats{0, 0, 0, 0};
-    EnRun R;
-    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R, true);
-    if (rc != LX_OK || n == 0) return rc;
-    if (model && model_contexts(model) != ts->scan.S + 1) return LX_E_INVAL;
-    if (c->timing) cudaEventRecord(c->ev[0], R.s);
+    int rc = LX_OK;
     en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
     if (model) {
         rc = model_predict(model, R.P.in, R.P.n, R.P.start, R.P.cinfo, R.P.blob, R.P.cbeg_off, R.P.cand_off,
@@ -1138,4 +1172,82 @@ extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *mo
         stats->judged = judged ? 1u : 0u;
     }
     return rc;
+}
+
+}  // namespace
+
+int lx::lex_enumerative_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+                               uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
+                               uint64_t *consumed, cudaStream_t stream, bool guard)
+{
+    if (!n_tokens || !consumed) return LX_E_INVAL;
+    *n_tokens = 0;
+    *consumed = 0;
+    EnRun R;
+    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R);
+    if (rc != LX_OK || n == 0) return rc;
+    if (c->timing) cudaEventRecord(c->ev[0], R.s);
+    if (guard && (rc = en_guard(c, ts, R)) != LX_OK) return rc;
+    for (;;) {
+        en_pipeline(R);
+        if (c->timing) cudaEventRecord(c->ev[1], R.s);
+        rc = en_finish(c, R, capacity, n_tokens, consumed);
+        if (rc != LX_LOOKAHEAD) return rc;
+        if (R.P.live || R.P.budget == ~0u) return LX_E_CUDA;   // a guarded run never flags it
+        if ((rc = en_guard(c, ts, R)) != LX_OK) return rc;
+    }
+}
+
+extern "C" int lx_lex_enumerative(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+                                  uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
+                                  uint64_t *consumed, void *stream)
+{
+    return lex_enumerative_device(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed,
+                                  static_cast<cudaStream_t>(stream), false);
+}
+
+extern "C" int lx_chunk_contexts(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n,
+                                 uint64_t *d_starts, uint16_t *d_ctx, uint64_t cap, uint64_t *count, void *stream)
+{
+    if (!count || (cap && (!d_starts || !d_ctx))) return LX_E_INVAL;
+    *count = 0;
+    EnRun R;
+    int rc = en_setup(c, ts, d_in, n, LX_FULL_EXACT, nullptr, nullptr, 0, stream, R);
+    if (rc != LX_OK || n == 0) return rc;
+    *count = R.P.M;
+    if (cap < R.P.M) return LX_E_CAPACITY;
+    for (;;) {
+        en_plan<<<R.grid, EN_NT, R.smem, R.s>>>(R.P);
+        en_enumerate<<<R.egrid, EN_NT, R.smem, R.s>>>(R.P);
+        en_sum<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
+        en_link<<<1, RS_NT, R.rs_smem, R.s>>>(R.P);
+        en_label<<<(R.P.nr1 + EN_NT - 1) / EN_NT, EN_NT, R.smem, R.s>>>(R.P);
+        ctx_export<<<R.grid, EN_NT, 0, R.s>>>(R.P, d_starts, d_ctx);
+        uint64_t nt, con;
+        rc = en_finish(c, R, ~0ull, &nt, &con);
+        if (rc != LX_LOOKAHEAD) return rc;
+        if (R.P.live || R.P.budget == ~0u) return LX_E_CUDA;
+        if ((rc = en_guard(c, ts, R)) != LX_OK) return rc;
+    }
+}
+
+extern "C" int lx_lex_speculative(lx_ctx *c, const lx_tokenset *ts, lx_model *model, const uint8_t *d_in,
+                                  uint64_t n, int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity,
+                                  uint64_t *n_tokens, uint64_t *consumed, lx_spec_stats *stats, void *stream)
+{
+    if (!n_tokens || !consumed) return LX_E_INVAL;
+    *n_tokens = 0;
+    *consumed = 0;
+    if (stats) *stats = lx_spec_stats{0, 0, 0, 0};
+    EnRun R;
+    int rc = en_setup(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, stream, R, true);
+    if (rc != LX_OK || n == 0) return rc;
+    if (model && model_contexts(model) != ts->scan.S + 1) return LX_E_INVAL;
+    if (c->timing) cudaEventRecord(c->ev[0], R.s);
+    for (;;) {
+        rc = spec_pipeline(c, R, model, capacity, n_tokens, consumed, stats);
+        if (rc != LX_LOOKAHEAD) return rc;
+        if (R.P.live || R.P.budget == ~0u) return LX_E_CUDA;   // a guarded run never flags it
+        if ((rc = en_guard(c, ts, R)) != LX_OK) return rc;
+    }
 }

@@ -111,12 +111,40 @@ struct WalkTable {
     std::vector<uint8_t> blob;
 };
 
+// ---------------------------------------------------------------------------
+// Liveness automaton: the failed-lookahead guard (Section 9, the quadratic
+// pathology of longest-match scanning).
+//
+// Read from right to left, its state after w[k..n) is the set
+//   live_k = { q in Q+ : delta+*(q, w[k..m)) accepts for some m > k },
+// empty at k = n: the states from which a scan at offset k still has an
+// accepting position ahead.  A scan whose state is not in live_k has already
+// passed its last accepting position, so it may end its token at once; with
+// that test every token costs its own length plus one step -- the table of
+// failed (state, position) pairs that Reps keeps during the scan, computed
+// before it.  Its states are the distinct sets reachable from the empty set;
+// on class c a set X goes to F_c(X) = { q in Q+ : delta+(q, c) accepts or
+// lies in X }.  A class whose F_c is the same for every state resets it.
+// At most LIVE_MAX sets (one-byte ids); otherwise the guard is unavailable.
+// Blob (16-byte aligned parts): byte_class u8[256] | next u8[C * R] (next of
+// set r on class c at c * R + r) | reset u8[C] | member u32[R * W] (bit q of
+// words r * W .. : q in set r).
+// ---------------------------------------------------------------------------
+constexpr uint32_t LIVE_MAX = 255;
+struct LiveTable {
+    int status = LX_E_TOOBIG;
+    uint32_t R = 0, C = 0, S = 0, W = 0;     // sets, classes, DFA states, member words per set
+    uint32_t next_off = 0, reset_off = 0, member_off = 0;
+    std::vector<uint8_t> blob;
+};
+
 struct DeviceTables {
     int device = -1;
     void *d_blob[3] = {nullptr, nullptr, nullptr};
     void *d_blob_cls[3] = {nullptr, nullptr, nullptr};
     void *d_scan = nullptr;
     void *d_walk[3] = {nullptr, nullptr, nullptr};
+    void *d_live = nullptr;
 };
 
 }  // namespace lx
@@ -134,6 +162,8 @@ struct lx_tokenset {
     lx::HostTable tab_cls[3];   // per mode: class-indexed (only when tab[m] is byte-indexed)
     lx::ScanTable scan;
     lx::WalkTable walk[3];      // per mode: event-code walk table (LX_E_TOOBIG when it does not fit)
+    lx::WalkTable walk_cls[3];  // per mode: its class form, when walk[m] is byte-indexed (batches)
+    lx::LiveTable liveness;     // the failed-lookahead guard (LX_E_TOOBIG: unavailable)
     std::mutex mu;
     std::vector<lx::DeviceTables> dev;
 };

@@ -1033,6 +1033,7 @@ int lx::ensure_device_tables(const lx_tokenset *cts, int device, DeviceTables *o
     if (rc == LX_OK && ts->scan.status == LX_OK) rc = upload(ts->scan.blob, &dt.d_scan);
     for (int m = 0; m < 3 && rc == LX_OK; m++)
         if (ts->walk[m].status == LX_OK) rc = upload(ts->walk[m].blob, &dt.d_walk[m]);
+    if (rc == LX_OK && ts->liveness.status == LX_OK) rc = upload(ts->liveness.blob, &dt.d_live);
     if (rc != LX_OK) {
         for (int m = 0; m < 3; m++) {
             if (dt.d_blob[m]) cudaFree(dt.d_blob[m]);
@@ -1040,6 +1041,7 @@ int lx::ensure_device_tables(const lx_tokenset *cts, int device, DeviceTables *o
             if (dt.d_walk[m]) cudaFree(dt.d_walk[m]);
         }
         if (dt.d_scan) cudaFree(dt.d_scan);
+        if (dt.d_live) cudaFree(dt.d_live);
         return rc;
     }
     ts->dev.push_back(dt);
@@ -1060,6 +1062,7 @@ extern "C" void lx_tokenset_free(lx_tokenset *ts)
             if (d.d_walk[m]) cudaFree(d.d_walk[m]);
         }
         if (d.d_scan) cudaFree(d.d_scan);
+        if (d.d_live) cudaFree(d.d_live);
     }
     if (cur >= 0 && !ts->dev.empty()) cudaSetDevice(cur);
     delete ts;
@@ -1096,6 +1099,7 @@ extern "C" void lx_ctx_free(lx_ctx *c)
     if (c->b_stream) cudaStreamDestroy(c->b_stream);
     if (c->b_dev) cudaFree(c->b_dev);
     if (c->e_dev) cudaFree(c->e_dev);
+    if (c->lv_dev) cudaFree(c->lv_dev);
     if (c->b_host) cudaFreeHost(c->b_host);
     if (c->d_in) cudaFree(c->d_in);
     if (c->h_scratch) cudaFreeHost(c->h_scratch);
@@ -1294,8 +1298,9 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     if (!force && c->kernel != LX_KERNEL_TILE && warp_path_ok(ts, mode, d_in)) {
         const int rc = lex_warp_device(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st,
                                        can_enumerate ? SPARSE_LIMIT : 0);
-        if (rc != LX_SPARSE) return rc;
-        return lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st);
+        if (rc != LX_SPARSE && rc != LX_LOOKAHEAD) return rc;
+        return lex_enumerative_device(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st,
+                                      rc == LX_LOOKAHEAD);
     }
     if (!force && c->kernel == LX_KERNEL_WARP && n) return LX_E_INVAL;   // asked for, not available here
     if (ts->tab[mode].status != LX_OK) return ts->tab[mode].status;

@@ -65,6 +65,7 @@ constexpr int MAX_WARPS = 20;                 // warps per CTA at most (as many 
 constexpr unsigned ERR_TIMEOUT = 1u;
 constexpr unsigned ERR_SMEM = 2u;
 constexpr unsigned ERR_SPARSE = 4u;   // a chunk ran past the sparse limit: certified bytes too far apart
+constexpr unsigned ERR_LOOKAHEAD = 8u;   // backtracking past its step budget (failed lookahead)
 
 static_assert(SLICE % BLK == 0 && WAREA % 16 == 0, "geometry");
 
@@ -101,6 +102,8 @@ struct WEnv {
     uint32_t P_start, P_pre, P_slow;
     uint32_t tb_s, acc_s, kmap_s, cmap_s, cut_s, shift;
     uint32_t ev;                 // event buffer: code of position p at ev + p
+    unsigned int *err;           // the result record's error word
+    uint32_t guard;              // 1: backtracking past its step budget stops the call (ERR_LOOKAHEAD)
     const uint8_t *in;           // the tile's first byte
     uint32_t nrel;               // input bytes from the tile start (clamped)
     uint64_t nrel64;
@@ -225,10 +228,16 @@ __device__ void refine_start(const WEnv &E, Lane &L)
 // re-walk falls into SLOW again at or before hi; a SLOW past hi belongs to
 // the next chunk and stops the lane.  No accepting prefix: a failure at the
 // token start (Corollary 1), recorded when it lies inside this chunk.
+// Failed lookahead that repeats at successive token starts makes the repeats
+// quadratic in the chunk length (Section 9); past a budget of steps linear in
+// it the lane stops and flags ERR_LOOKAHEAD (with E.guard), and the caller
+// lexes the input with the failed-lookahead guard instead.
 template <int FORM>
 __device__ void slow_fix(const WEnv &E, Lane &L, uint32_t upto, uint32_t hi)
 {
     refine_start<FORM>(E, L);
+    const uint32_t budget = 16u * (upto - L.s) + 65536u;
+    uint32_t steps = 0;
     for (;;) {
         uint32_t tok = L.s;
         for (uint32_t j = min(upto - 1, hi); j > L.s; j--)
@@ -263,6 +272,12 @@ __device__ void slow_fix(const WEnv &E, Lane &L, uint32_t upto, uint32_t hi)
         L.e = e;
         if (e != E.P_slow) return;
         if (kslow > hi || r > hi) {
+            L.act = false;
+            return;
+        }
+        steps += upto - tok;
+        if (E.guard && steps > budget) {
+            atomicOr(E.err, ERR_LOOKAHEAD);
             L.act = false;
             return;
         }
@@ -348,11 +363,11 @@ struct ByteReader {
 
 template <int FORM>
 __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail, uint16_t *kinds, uint32_t *lens,
-                                  uint64_t cap, uint64_t o, uint64_t limit = 0, bool *over = nullptr)
+                                  uint64_t cap, uint64_t o, uint64_t limit = 0, unsigned *over = nullptr)
 {
     const uint64_t n = E.nrel64;
     ByteReader rd{E.in, n};
-    uint64_t p = start, tok = start, cnt = 0;
+    uint64_t p = start, tok = start, cnt = 0, steps = 0;
     uint32_t e = E.P_start;
     *fail = NONE64;
     const uint64_t stop = limit ? start + limit : ~0ull;
@@ -374,7 +389,7 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
             }
         } else {
             if (p >= stop) {
-                *over = true;
+                *over = ERR_SPARSE;
                 return cnt;
             }
             const uint32_t b = rd.at(p);
@@ -390,7 +405,13 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
                 continue;
             }
         }
-        // longest match with backtracking: replay [tok, p) from q0
+        // longest match with backtracking: replay [tok, p) from q0; repeated
+        // failed lookahead past a budget linear in the chunk stops the call
+        steps += p - tok;
+        if (limit && steps > 4 * limit) {
+            *over = ERR_LOOKAHEAD;
+            return cnt;
+        }
         uint32_t q = E.P_start, rc = 0;
         uint64_t r = NONE64;
         for (uint64_t k = tok; k < p; k++) {
@@ -705,6 +726,8 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
     E.cmap_s = tb_s + P.cmap_off;
     E.cut_s = tb_s + P.cut_off;
     E.shift = P.row_shift;
+    E.err = &P.res->error;
+    E.guard = P.sparse_limit != 0 ? 1u : 0u;
     const uint32_t warea = ((tb_s + P.blob_bytes + 15u) & ~15u) + (uint32_t)wid * WAREA;
     E.ev = warea;
     const uint32_t stage = warea + EV_BYTES;
@@ -846,10 +869,10 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         // the chunk past the halo, counted by lane 0
         uint64_t gen_cnt = 0, gen_fail = NONE64;
         const bool do_long = c0 != NONE && long_s1 != 0 && fail > long_s1 - 1;
-        bool over = false;
+        unsigned over = 0;
         if (do_long && lane == 0) {
             gen_cnt = generic_chunk<FORM>(E, long_s1 - 1, &gen_fail, nullptr, nullptr, 0, 0, P.sparse_limit, &over);
-            if (over) atomicOr(&P.res->error, ERR_SPARSE);   // the caller lexes the input another way
+            if (over) atomicOr(&P.res->error, over);   // the caller lexes the input another way
         }
         if (__shfl_sync(0xffffffffu, over ? 1u : 0u, 0)) {
             publish_tile(P, tile, 0);
@@ -1064,6 +1087,7 @@ int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint6
     if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(st));
     if (rc != LX_OK) return rc;
     const WResult r = *static_cast<const WResult *>(c->h_res);
+    if (r.error & ERR_LOOKAHEAD) return LX_LOOKAHEAD;
     if (r.error & ERR_SPARSE) return LX_SPARSE;
     if (r.error & ERR_TIMEOUT) return LX_E_TIMEOUT;
     if (r.error & ERR_SMEM) return LX_E_TOOBIG;

@@ -53,6 +53,9 @@ struct lx_ctx {
     size_t h_scratch_bytes = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_lex;
+    // the failed-lookahead guard's prepass (liveness.cu): device scratch
+    void *lv_dev = nullptr;
+    size_t lv_dev_bytes = 0;
     // lx_lex kernel choice (lx_ctx_set_kernel): LX_KERNEL_AUTO, _TILE or _WARP
     int kernel = 0;
     // optional kernel timing
@@ -76,13 +79,29 @@ int ensure_device_tables(const lx_tokenset *ts, int device, DeviceTables *out);
 // token set, mode and input pointer (an event-code walk table and a 16-byte
 // aligned input), and the call itself (same contract as lx_lex).  With
 // sparse_limit != 0 a chunk longer than that many bytes (certified bytes too
-// far apart) makes the call stop early and return LX_SPARSE, leaving the
-// input to the enumerative path.
+// far apart) makes the call stop early and return LX_SPARSE, and backtracking
+// steps beyond a budget proportional to n (failed lookahead) make it return
+// LX_LOOKAHEAD, leaving the input to the enumerative path (guarded).
 constexpr int LX_SPARSE = -100;   // internal status, never returned by the C ABI
 bool warp_path_ok(const lx_tokenset *ts, int mode, const uint8_t *d_in);
 int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
                     uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed, cudaStream_t st,
                     uint64_t sparse_limit);
+// Internal status: a scan ran past its step budget (failed lookahead, or a
+// token spanning many chunks); the caller runs the input again with the
+// failed-lookahead guard.  Never returned by the C ABI.
+constexpr int LX_LOOKAHEAD = -101;
+// lx_lex_enumerative (enumerate.cu) with the failed-lookahead guard from the
+// start when `guard` (the caller saw a scan run past its budget already).
+int lex_enumerative_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+                           uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
+                           uint64_t *consumed, cudaStream_t stream, bool guard);
+// The guard's prepass (liveness.cu): the liveness automaton's state at every
+// offset 0..n of the input into d_out[n + 1] (nullptr: the context's scratch);
+// *live receives the array, *member the automaton's member bitsets on the
+// device.  LX_E_TOOBIG when the token set has no liveness automaton.
+int liveness_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, uint8_t *d_out,
+                    cudaStream_t s, const uint8_t **live, const uint32_t **member);
 // The entry-context model (model.cu): number of contexts it scores, and the
 // BF16 prediction of the entry context of every chunk start (0xFFFE =
 // BOUNDARY) into guess[M], restricted to the candidates of the byte before.

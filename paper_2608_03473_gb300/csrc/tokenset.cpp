@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "internal.h"
@@ -263,7 +264,7 @@ void build_table(const lx_tokenset &t, int mode, HostTable &ht, bool class_form)
 
 // Event-code walk table (internal.h).  Same transitions as build_table
 // without E rows: the token end and its kind travel in the entry.
-void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt)
+void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt, bool force_class = false)
 {
     const uint32_t S = t.n_states, C = t.n_classes, q0 = t.q0;
     auto nx = [&](uint32_t c, uint32_t q) { return t.next[(size_t)c * S + q]; };
@@ -290,7 +291,7 @@ void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt)
     wt.n_kept = next_code - 2;
     const uint32_t SLOW = 0, START = S + 1, PRE = S + 2, R = S + 3;
     auto Rq = [](uint32_t q) { return 1 + q; };
-    if ((uint64_t)R * 512 <= lx::MAX_BYTE_FORM_BYTES) {
+    if (!force_class && (uint64_t)R * 512 <= lx::MAX_BYTE_FORM_BYTES) {
         wt.form = lx::FORM_BYTE;
         wt.row_shift = 9;
     } else if (C <= 127 && (uint64_t)R * 256 <= lx::MAX_TABLE_BYTES) {
@@ -420,6 +421,63 @@ void build_scan_table(const lx_tokenset &t, ScanTable &st)
     cb[256] = (uint16_t)o;
 }
 
+// The liveness automaton (internal.h): breadth-first over the reachable live
+// sets from the empty one, at most LIVE_MAX of them.
+void build_liveness(const lx_tokenset &t, lx::LiveTable &lt)
+{
+    const uint32_t S = t.n_states, C = t.n_classes, W = (S + 31) / 32;
+    lt.S = S;
+    lt.C = C;
+    lt.W = W;
+    std::map<std::vector<uint32_t>, uint32_t> ids;
+    std::vector<std::vector<uint32_t>> sets;
+    std::vector<uint8_t> nxt;   // [r * C + c] while building
+    sets.emplace_back(W, 0u);
+    ids[sets[0]] = 0;
+    for (uint32_t r = 0; r < sets.size(); r++) {
+        for (uint32_t c = 0; c < C; c++) {
+            std::vector<uint32_t> y(W, 0u);
+            for (uint32_t q = 0; q < S; q++) {
+                if (!t.live[q]) continue;
+                const uint32_t d = t.next[(size_t)c * S + q];
+                if (d == LX_NONE || !t.live[d]) continue;
+                if (t.accept[d] != LX_NO_KIND || ((sets[r][d >> 5] >> (d & 31)) & 1u)) y[q >> 5] |= 1u << (q & 31);
+            }
+            auto it = ids.find(y);
+            uint32_t id;
+            if (it != ids.end()) {
+                id = it->second;
+            } else {
+                if (sets.size() >= lx::LIVE_MAX) return;   // too many: no guard
+                id = (uint32_t)sets.size();
+                ids.emplace(y, id);
+                sets.push_back(std::move(y));
+            }
+            nxt.push_back((uint8_t)id);
+        }
+    }
+    const uint32_t R = (uint32_t)sets.size();
+    auto al = [](uint32_t x) { return (x + 15u) & ~15u; };
+    lt.R = R;
+    lt.next_off = 256;
+    lt.reset_off = al(lt.next_off + C * R);
+    lt.member_off = al(lt.reset_off + C);
+    lt.blob.assign(al(lt.member_off + 4 * R * W), 0);
+    std::memcpy(lt.blob.data(), t.byte_class.data(), 256);
+    for (uint32_t c = 0; c < C; c++) {
+        bool same = true;
+        for (uint32_t r = 0; r < R; r++) {
+            lt.blob[lt.next_off + c * R + r] = nxt[(size_t)r * C + c];
+            same = same && nxt[(size_t)r * C + c] == nxt[c];
+        }
+        lt.blob[lt.reset_off + c] = same ? 1 : 0;
+    }
+    uint32_t *mem = reinterpret_cast<uint32_t *>(lt.blob.data() + lt.member_off);
+    for (uint32_t r = 0; r < R; r++)
+        for (uint32_t w = 0; w < W; w++) mem[r * W + w] = sets[r][w];
+    lt.status = LX_OK;
+}
+
 }  // namespace
 
 extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
@@ -460,8 +518,12 @@ extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
             // far smaller, so more CTAs fit per SM
             if (t->tab[m].form == lx::FORM_BYTE) build_table(*t, m, t->tab_cls[m], true);
             build_walk_table(*t, m, t->walk[m]);
+            // the class form as well, for batches that hold several tables
+            if (t->walk[m].status == LX_OK && t->walk[m].form == lx::FORM_BYTE)
+                build_walk_table(*t, m, t->walk_cls[m], true);
         }
         build_scan_table(*t, t->scan);
+        build_liveness(*t, t->liveness);
     } catch (const std::bad_alloc &) {
         delete t;
         return LX_E_NOMEM;
@@ -563,6 +625,17 @@ extern "C" int lx_tokenset_walk_table(const lx_tokenset *ts, int mode, void *out
                             w.p_pre, w.acc_off, w.kmap_off, w.cmap_off, w.cut_off};
     if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 10));
     return w.status;
+}
+
+extern "C" int lx_tokenset_liveness(const lx_tokenset *ts, void *out, uint32_t cap, uint32_t *meta,
+                                    uint32_t meta_len)
+{
+    if (!ts) return LX_E_INVAL;
+    const lx::LiveTable &lt = ts->liveness;
+    if (out && cap) std::memcpy(out, lt.blob.data(), std::min<size_t>(cap, lt.blob.size()));
+    const uint32_t m[8] = {(uint32_t)lt.blob.size(), lt.R, lt.C, lt.S, lt.W, lt.next_off, lt.reset_off, lt.member_off};
+    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 8));
+    return lt.status;
 }
 
 extern "C" int lx_tokenset_scan_table(const lx_tokenset *ts, void *out, uint32_t cap, uint32_t *meta,
