@@ -237,12 +237,23 @@ int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
  *   LX_KERNEL_WARP: always the warp-tile kernel; lx_lex returns LX_E_INVAL
  *     for a call it cannot serve.
  * Both produce the same stream (tests compare them).  Returns LX_E_INVAL
- * for another value.  lx_lex_host and lx_lex_batch always use the tile kernel.
+ * for another value.  lx_lex_host always uses the tile kernel; lx_lex_batch
+ * takes the one-launch warp-tile batch unless LX_KERNEL_TILE is set.
  */
 #define LX_KERNEL_AUTO 0
 #define LX_KERNEL_TILE 1
 #define LX_KERNEL_WARP 2
 int lx_ctx_set_kernel(lx_ctx *ctx, int kernel);
+
+/*
+ * lx_ctx_set_warps -- warps per CTA of the warp-tile kernel on this context
+ * (1..20; 0 = as many as the shared-memory budget holds next to the table,
+ * the default).  Each warp owns one 4096-byte tile at a time, so the setting
+ * trades resident warps (latency hiding) against L1 left beside shared
+ * memory.  Same tokens either way; lx_autotune chooses it.  LX_E_INVAL for a
+ * value above 20.
+ */
+int lx_ctx_set_warps(lx_ctx *ctx, uint32_t warps);
 
 /*
  * lx_ctx_debug_withhold -- failure-detection test hook.  In later lx_lex
@@ -289,6 +300,28 @@ int lx_lex(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, 
            uint64_t *consumed, void *stream);
 
 /*
+ * lx_lex_async -- lx_lex without a host round trip: the warp-tile kernel, then
+ * a one-thread kernel that writes the call's result record to *d_result
+ * (device memory, caller-owned) in stream order.  Nothing synchronizes and
+ * nothing falls back: chunks whose certified bytes lie far apart are walked
+ * byte by byte, and backtracking carries no step budget (same tokens as
+ * lx_lex, possibly slower on such inputs).  Needs the warp-tile kernel
+ * (an event-code walk table for the mode and a 16-byte aligned d_in):
+ * LX_E_INVAL otherwise, returned at once, like every argument error.
+ * d_result->status is LX_OK, LX_E_CAPACITY, LX_E_TIMEOUT or LX_E_TOOBIG;
+ * n_tokens and consumed as in lx_lex.  Calls on one context must share one
+ * stream (they reuse the context's scratch in order).
+ */
+typedef struct {
+    int32_t status;
+    uint32_t reserved;
+    uint64_t n_tokens;
+    uint64_t consumed;
+} lx_async_result;
+int lx_lex_async(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+                 uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, lx_async_result *d_result, void *stream);
+
+/*
  * lx_lex_host -- lx_lex on HOST buffers: copies h_in to the device, lexes it
  * and copies the tokens back into h_kinds / h_lens (host, capacity entries),
  * using device buffers owned by the context.  Same results and errors as
@@ -320,9 +353,13 @@ int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_
  * lx_autotune measured for it, 0 if set by hand or default).
  * lx_autotune times every ks in {24, 32, 36, 40, 48, 56, 64} on each table form,
  * with the largest and the smallest CTA count, on `d_sample` (a device buffer representative
- * of the inputs to come, n bytes; outputs go to d_kinds / d_lens), checks that
- * all give the same result, and keeps the fastest.  Synchronizes `stream`.
- * The configuration also applies to lx_lex_batch groups of that token set.
+ * of the inputs to come, n bytes; outputs go to d_kinds / d_lens), then the
+ * warp-tile kernel (where it applies to the sample) at 4, 8, 12, 16 and 20
+ * warps per CTA; checks that all give the same result, keeps the fastest
+ * tile configuration and, for lx_lex on LX_KERNEL_AUTO, the faster kernel
+ * with its warps per CTA (lx_ctx_set_warps overrides the latter; setting a
+ * configuration by hand clears the choice).  Synchronizes `stream`.
+ * The tile configuration also applies to lx_lex_batch groups of that token set.
  */
 #define LX_KS_MIN 16u
 #define LX_KS_MAX 96u
@@ -463,11 +500,20 @@ int lx_lex_speculative(lx_ctx *ctx, const lx_tokenset *ts, lx_model *model, cons
  * docs[i] names a device buffer of docs[i].n bytes and the index of its
  * token set in sets[0 .. n_sets).  Every document is lexed exactly as
  * lx_lex would lex it alone (cuts at the mode's certificates of its own
- * token set, Theorems 1 and 3; failures per Corollary 1).  Documents are
- * grouped by token set: one persistent kernel per set runs over the tiles of
- * all that set's documents, and the groups follow each other in set order.
- * The output stream d_kinds / d_lens (capacity entries) holds the groups in
- * set order and, within a group, the documents in their order in docs[].
+ * token set, Theorems 1 and 3; failures per Corollary 1).
+ * One launch (the default): the warp-tile kernel runs over the tiles of all
+ * documents in their order in docs[], the class-form walk tables of all the
+ * sets side by side in shared memory (their rows must share the 16-bit
+ * shared-address window, about 250 rows of 256 bytes in all), each tile
+ * taking its document's table; the output stream d_kinds / d_lens (capacity
+ * entries) holds the documents in their order in docs[].  Long chunks are
+ * walked byte by byte inside the launch (no document leaves it).  When that
+ * does not apply (a set without a class-form walk table, rows beyond the
+ * window, a document not 16-byte aligned, or LX_KERNEL_TILE set), documents
+ * are grouped by token set: one persistent tile kernel per set runs over the
+ * tiles of all that set's documents, and the stream holds the groups in set
+ * order and, within a group, the documents in their order in docs[].  Either
+ * way document i's tokens start at results[i].out_off.
  * results[i] (host array of n_docs) receives the output index of document
  * i's first token (out_off), its kept-token count n_tokens (tokens before
  * its first lexing error) and consumed = con(w) of the document; when

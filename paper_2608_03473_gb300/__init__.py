@@ -58,6 +58,7 @@ EXPORTED = (
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
     "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold", "lx_ctx_set_kernel",
+    "lx_ctx_set_warps", "lx_lex_async",
     "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative", "lx_chunk_contexts",
     "lx_lex_speculative", "lx_model_create", "lx_model_free", "lx_model_info", "lx_model_get_params",
     "lx_model_set_params", "lx_model_windows", "lx_model_forward", "lx_model_gradient", "lx_model_train_step",
@@ -123,6 +124,8 @@ def load_library(path: Optional[str] = None):
             "lx_ctx_set_config": (i32, [vp, vp, i32, u32, u32, u32]),
             "lx_ctx_debug_withhold": (i32, [vp, u32]),
             "lx_ctx_set_kernel": (i32, [vp, i32]),
+            "lx_ctx_set_warps": (i32, [vp, u32]),
+            "lx_lex_async": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp]),
             "lx_ctx_get_config": (i32, [vp, vp, i32, vp, vp, vp, vp]),
             "lx_autotune": (i32, [vp, vp, i32, vp, u64, vp, vp, u64, vp]),
             "lx_lex": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp, vp]),
@@ -300,6 +303,39 @@ def lx_ctx_set_kernel(ctx: Ctx, kernel: int) -> int:
     """Which kernel lx_lex uses: LX_KERNEL_AUTO (warp-tile kernel where it
     applies), LX_KERNEL_TILE or LX_KERNEL_WARP."""
     return load_library().lx_ctx_set_kernel(ctx.handle, int(kernel))
+
+
+def lx_ctx_set_warps(ctx: Ctx, warps: int) -> int:
+    """Warps per CTA of the warp-tile kernel (0: as many as fit)."""
+    return load_library().lx_ctx_set_warps(ctx.handle, int(warps))
+
+
+class AsyncResult(ctypes.Structure):
+    """lx_async_result: the record lx_lex_async writes to device memory."""
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_uint32), ("n_tokens", ctypes.c_uint64),
+                ("consumed", ctypes.c_uint64)]
+
+
+def lx_lex_async(ctx: Ctx, ts: Tokenset, d_in, mode: int, d_kinds, d_lens, d_result, n: Optional[int] = None,
+                 capacity: Optional[int] = None, stream=None) -> int:
+    """Launch lx_lex without a host round trip; the result record (24 bytes:
+    status, reserved, n_tokens, consumed) lands in the device buffer
+    ``d_result`` in stream order.  Returns the launch status."""
+    lib = load_library()
+    n = d_in.numel() if n is None else int(n)
+    cap = min(d_kinds.numel(), d_lens.numel()) if capacity is None else int(capacity)
+    if d_result.numel() * d_result.element_size() < ctypes.sizeof(AsyncResult):
+        raise ValueError("d_result needs 24 bytes")
+    return lib.lx_lex_async(ctx.handle, ts.handle, d_in.data_ptr(), n, int(mode), d_kinds.data_ptr(),
+                            d_lens.data_ptr(), cap, d_result.data_ptr(), _stream_handle(stream))
+
+
+def async_result(buf) -> Tuple[int, int, int]:
+    """(status, n_tokens, consumed) from the bytes of an lx_async_result."""
+    a = np.asarray(buf).view(np.uint8)
+    st = int(a[:4].view(np.int32)[0])
+    nt, con = a[8:24].view(np.uint64).tolist()
+    return st, int(nt), int(con)
 
 
 def lx_ctx_enable_timing(ctx: Ctx, on: bool = True) -> int:

@@ -150,6 +150,7 @@ struct DeviceTables {
 }  // namespace lx
 
 struct lx_tokenset {
+    uint64_t serial = 0;        // unique per compiled token set (cache keys)
     uint32_t n_states = 0, n_classes = 0, q0 = 0, n_kinds = 0;
     std::vector<uint8_t> byte_class;
     std::vector<uint32_t> next;       // [c * S + q]

@@ -1100,6 +1100,7 @@ extern "C" void lx_ctx_free(lx_ctx *c)
     if (c->b_dev) cudaFree(c->b_dev);
     if (c->e_dev) cudaFree(c->e_dev);
     if (c->lv_dev) cudaFree(c->lv_dev);
+    if (c->wb_dev) cudaFree(c->wb_dev);
     if (c->b_host) cudaFreeHost(c->b_host);
     if (c->d_in) cudaFree(c->d_in);
     if (c->h_scratch) cudaFreeHost(c->h_scratch);
@@ -1135,6 +1136,25 @@ extern "C" int lx_ctx_set_kernel(lx_ctx *c, int kernel)
     if (!c || kernel < LX_KERNEL_AUTO || kernel > LX_KERNEL_WARP) return LX_E_INVAL;
     c->kernel = kernel;
     return LX_OK;
+}
+
+extern "C" int lx_ctx_set_warps(lx_ctx *c, uint32_t warps)
+{
+    if (!c || warps > 20) return LX_E_INVAL;
+    c->warps = warps;
+    return LX_OK;
+}
+
+extern "C" int lx_lex_async(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
+                            uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, lx_async_result *d_result,
+                            void *stream)
+{
+    if (!c || !ts || !d_result || (n && !d_in)) return LX_E_INVAL;
+    if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
+    if (capacity && (!d_kinds || !d_lens)) return LX_E_INVAL;
+    if (!warp_path_ok(ts, mode, d_in)) return LX_E_INVAL;
+    return lex_warp_async(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, d_result,
+                          static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int lx_ctx_debug_withhold(lx_ctx *c, uint32_t tile)
@@ -1227,6 +1247,20 @@ static const HostTable &table_for(const lx_tokenset *ts, int mode, const LaunchC
     return g.cls && has_class_table(ts, mode) ? ts->tab_cls[mode] : ts->tab[mode];
 }
 
+static const lx_tuned *tuned_for(const lx_ctx *c, const lx_tokenset *ts, int mode)
+{
+    for (const lx_tuned &t : c->tuned)
+        if (t.ts == ts && t.mode == mode) return &t;
+    return nullptr;
+}
+
+uint32_t lx::warps_setting(const lx_ctx *c, const lx_tokenset *ts, int mode)
+{
+    if (c->warps) return c->warps;
+    const lx_tuned *t = tuned_for(c, ts, mode);
+    return t ? t->warps : 0u;
+}
+
 static LaunchCfg config_for(lx_ctx *c, const lx_tokenset *ts, int mode)
 {
     LaunchCfg g;
@@ -1295,7 +1329,9 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     const bool can_enumerate = !force && c->kernel == LX_KERNEL_AUTO && ts->scan.status == LX_OK;
     if (can_enumerate && !mode_has_cuts(ts, mode))
         return lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st);
-    if (!force && c->kernel != LX_KERNEL_TILE && warp_path_ok(ts, mode, d_in)) {
+    const lx_tuned *tu = tuned_for(c, ts, mode);
+    const bool tuned_tile = c->kernel == LX_KERNEL_AUTO && tu && tu->kernel == LX_KERNEL_TILE;
+    if (!force && c->kernel != LX_KERNEL_TILE && !tuned_tile && warp_path_ok(ts, mode, d_in)) {
         const int rc = lex_warp_device(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st,
                                        can_enumerate ? SPARSE_LIMIT : 0);
         if (rc != LX_SPARSE && rc != LX_LOOKAHEAD) return rc;
@@ -1663,10 +1699,8 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
     if (!c || !n_total || (n_docs && (!docs || !results)) || (n_sets && !sets)) return LX_E_INVAL;
     if (mode < LX_FULL_EXACT || mode > LX_FILTERED_MODULO) return LX_E_MODE;
     if (capacity && (!d_kinds || !d_lens)) return LX_E_INVAL;
-    for (uint32_t s = 0; s < n_sets; s++) {
+    for (uint32_t s = 0; s < n_sets; s++)
         if (!sets[s]) return LX_E_INVAL;
-        if (sets[s]->tab[mode].status != LX_OK) return sets[s]->tab[mode].status;
-    }
     for (uint32_t i = 0; i < n_docs; i++) {
         if (docs[i].set >= n_sets || docs[i].reserved != 0) return LX_E_INVAL;
         if (docs[i].n && !docs[i].data) return LX_E_INVAL;
@@ -1676,6 +1710,15 @@ extern "C" int lx_lex_batch(lx_ctx *c, const lx_tokenset *const *sets, uint32_t 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
+    if (c->kernel != LX_KERNEL_TILE) {   // one launch for every document of every set
+        const int rc = lex_batch_warp(c, sets, n_sets, docs, n_docs, mode, d_kinds, d_lens, capacity, results,
+                                      n_total, st);
+        if (rc != LX_SPARSE) return rc;
+        for (uint32_t i = 0; i < n_docs; i++) results[i] = lx_doc_result{0, 0, 0};
+        *n_total = 0;
+    }
+    for (uint32_t s = 0; s < n_sets; s++)
+        if (sets[s]->tab[mode].status != LX_OK) return sets[s]->tab[mode].status;
 
     // group the non-empty documents by token set, keeping their order
     std::vector<uint32_t> order;
@@ -1847,9 +1890,11 @@ static void store_config(lx_ctx *c, const lx_tokenset *ts, int mode, const Launc
             t.ctas = g.ctas;
             t.cls = g.cls;
             t.ms = ms;
+            t.kernel = 0;   // a configuration set by hand: the default kernel choice again
+            t.warps = 0;
             found = true;
         }
-    if (!found) c->tuned.push_back(lx_tuned{ts, mode, g.ks, g.ctas, g.cls, ms});
+    if (!found) c->tuned.push_back(lx_tuned{ts, mode, g.ks, g.ctas, g.cls, ms, 0, 0});
     if (c->b_exec) {   // a cached batch graph may hold the old configuration
         cudaGraphExecDestroy(c->b_exec);
         c->b_exec = nullptr;
@@ -1951,11 +1996,52 @@ extern "C" int lx_autotune(lx_ctx *c, const lx_tokenset *ts, int mode, const uin
             if (rc != LX_OK) break;
         }
     }
+    // the warp-tile kernel at several warps per CTA, when it applies
+    float best_w = 1e30f;
+    uint32_t best_nw = 0;
+    const uint32_t saved_warps = c->warps;
+    if (rc == LX_OK && warp_path_ok(ts, mode, d_sample)) {
+        for (uint32_t nw : {4u, 8u, 12u, 16u, 20u}) {
+            c->warps = nw;
+            uint64_t nt = 0, con = 0;
+            float total = 0.0f;
+            for (int rep = 0; rep < 4 && rc == LX_OK; rep++) {
+                cudaEventRecord(e0, st);
+                rc = lex_warp_device(c, ts, d_sample, n, mode, d_kinds, d_lens, capacity, &nt, &con, st, 0);
+                cudaEventRecord(e1, st);
+                if (rc == LX_E_CAPACITY) rc = LX_OK;
+                if (rc != LX_OK) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep) total += ms;
+            }
+            if (rc != LX_OK) break;
+            if (ref_tokens == ~0ull) {
+                ref_tokens = nt;
+                ref_con = con;
+            } else if (nt != ref_tokens || con != ref_con) {
+                rc = LX_E_CUDA;
+                break;
+            }
+            if (total / 3 < best_w) {
+                best_w = total / 3;
+                best_nw = nw;
+            }
+        }
+    }
+    c->warps = saved_warps;
     c->timing = timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LX_OK) return rc;
     store_config(c, ts, mode, best_g, best);
+    for (lx_tuned &t : c->tuned)
+        if (t.ts == ts && t.mode == mode) {
+            t.kernel = best_nw && best_w < best ? LX_KERNEL_WARP : LX_KERNEL_TILE;
+            t.warps = best_nw;
+            if (t.kernel == LX_KERNEL_WARP) t.ms = best_w;
+        }
     return LX_OK;
 }
 

@@ -37,6 +37,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <vector>
 
 #include "devutil.cuh"
 #include "internal.h"
@@ -77,6 +79,28 @@ struct WResult {
     unsigned int pad;
 };
 
+// Batches: a document's tiles are consecutive in the launch's tile sequence
+// from first_tile; `set` indexes the WSet array staged with the tables.
+struct WDoc {
+    const uint8_t *in;
+    uint64_t n;
+    uint32_t first_tile;
+    uint32_t set;
+};
+
+// One token set's rows and maps in a batch's combined table (offsets from
+// the table's start; the rows of all sets lie in one 16-bit address window).
+struct WSet {
+    uint32_t p_start, p_pre, p_slow, kmap_off, cmap_off, cut_off;
+};
+
+struct WDocRes {
+    unsigned long long total;          // kept tokens of the document's tiles (any after a failure included)
+    unsigned long long inv_fail_pos;   // ~min failure offset within the document, 0 = none
+    unsigned long long inv_fail_tok;   // ~output index at that failure
+    unsigned long long out_off1;       // output index of its first token + 1 (0: not yet resolved)
+};
+
 struct WParams {
     const uint8_t *in;
     uint64_t n;
@@ -95,6 +119,11 @@ struct WParams {
     uint64_t timeout_ns;
     uint32_t withhold;
     uint64_t sparse_limit;   // longest chunk walked byte by byte before giving up (0: no limit)
+    // batches
+    const WDoc *docs;
+    const uint32_t *tile_doc;   // document of every tile
+    WDocRes *dres;
+    uint32_t sets_off;          // WSet array in the table blob
 };
 
 // Shared addresses of the tables and of this warp's buffers, and the tile.
@@ -507,11 +536,14 @@ __device__ void publish_tile(const WParams &P, uint32_t tile, uint64_t agg)
     if (lane == 0 && agg) atomicAdd(&P.res->total, agg);
     if (lane == 0 && tile != P.withhold) {
         st_status(&P.status[tile], ST_AGG | agg);
-        __threadfence();
-        last = atomicAdd(&P.gdone[g], 1u) + 1 == gsize ? 1u : 0u;
-        if (last) __threadfence();
+        // release: the status store before the count; acquire: the group's
+        // other status stores visible to the warp that completes it
+        uint32_t old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&P.gdone[g]) : "memory");
+        last = old + 1 == gsize ? 1u : 0u;
     }
     if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    __threadfence();   // every lane reads the statuses lane 0's acquire made visible
     // every tile of the group has published: its aggregate
     unsigned long long x = 0;
     for (uint32_t j = lane; j < gsize; j += 32) x += ld_status(&P.status[f + j]) & ST_VAL;
@@ -607,24 +639,39 @@ struct Pending {
     uint32_t staged;    // tokens in the stage (all of the tile's kept tokens)
     uint64_t fail;      // failure offset within the tile, or NONE64
     uint64_t agg;
+    uint32_t doc, dtile;   // batches: its document and its index there
+    uint32_t kmap_s;       // the kind map of its token set
 };
 
-__device__ void report_failure(const WParams &P, uint32_t tile, uint64_t fail, uint64_t G, uint64_t agg)
+// After a tile's output offset G is known: its failure (the first of the
+// input, or of its document in a batch) and, for a document's first tile,
+// the document's output offset.
+template <bool BATCH>
+__device__ void report_failure(const WParams &P, uint32_t tile, uint64_t fail, uint64_t G, uint64_t agg,
+                               uint32_t doc, uint32_t dtile)
 {
-    if ((threadIdx.x & 31) == 0 && fail != NONE64) {
+    if ((threadIdx.x & 31) != 0) return;
+    if (BATCH) {
+        if (dtile == 0) P.dres[doc].out_off1 = G + 1;
+        if (fail != NONE64) {
+            atomicMax(&P.dres[doc].inv_fail_pos, ~(unsigned long long)((uint64_t)dtile * WT + fail));
+            atomicMax(&P.dres[doc].inv_fail_tok, ~(unsigned long long)(G + agg));
+        }
+    } else if (fail != NONE64) {
         atomicMax(&P.res->inv_fail_pos, ~(unsigned long long)((uint64_t)tile * WT + fail));
         atomicMax(&P.res->inv_fail_tok, ~(unsigned long long)(G + agg));
     }
 }
 
-// The staged tokens of a tile to the output from index G, coalesced.
-__device__ void copy_stage(const WParams &P, const WEnv &E, uint32_t stage, uint32_t staged, uint64_t G)
+// The staged tokens of a tile to the output from index G, coalesced; kmap_s:
+// the kind map of the tile's token set.
+__device__ void copy_stage(const WParams &P, uint32_t kmap_s, uint32_t stage, uint32_t staged, uint64_t G)
 {
     for (uint32_t i = threadIdx.x & 31; i < staged; i += 32) {
         const uint64_t o = G + i;
         if (o < P.cap) {
             const uint32_t v = lds_u32(stage + 4 * i);
-            P.out_kinds[o] = (uint16_t)lds_u16(E.kmap_s + (v >> 16));
+            P.out_kinds[o] = (uint16_t)lds_u16(kmap_s + (v >> 16));
             P.out_lens[o] = v & 0xFFFFu;
         }
     }
@@ -696,7 +743,7 @@ __device__ __forceinline__ void phase2_step(const WEnv &E, Lane &L, const uint4 
     }
 }
 
-template <int FORM>
+template <int FORM, bool BATCH>
 __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -735,7 +782,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
     __syncthreads();
     const uint32_t ahead = gridDim.x * (blockDim.x / 32);   // tiles the other warps take meanwhile
 
-    Pending pend{NONE, 0, NONE64, 0};
+    Pending pend{NONE, 0, NONE64, 0, 0, 0, 0};
     for (;;) {
         uint32_t tile = 0;
         if (lane == 0) {
@@ -744,12 +791,27 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         }
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= P.n_tiles) break;
-        const uint64_t tb = (uint64_t)tile * WT;
-        E.in = P.in + tb;
-        E.nrel64 = P.n - tb;
+        uint32_t doc = 0, dtile = tile;
+        if (BATCH) {   // the tile's document and its token set's rows and maps
+            doc = __ldg(P.tile_doc + tile);
+            const WDoc D = P.docs[doc];
+            dtile = tile - D.first_tile;
+            E.in = D.in + (uint64_t)dtile * WT;
+            E.nrel64 = D.n - (uint64_t)dtile * WT;
+            const uint32_t ws = tb_s + P.sets_off + D.set * (uint32_t)sizeof(WSet);
+            E.P_start = tb_s + lds_u32(ws);
+            E.P_pre = tb_s + lds_u32(ws + 4);
+            E.P_slow = tb_s + lds_u32(ws + 8);
+            E.kmap_s = tb_s + lds_u32(ws + 12);
+            E.cmap_s = tb_s + lds_u32(ws + 16);
+            E.cut_s = tb_s + lds_u32(ws + 20);
+        } else {
+            E.in = P.in + (uint64_t)tile * WT;
+            E.nrel64 = P.n - (uint64_t)tile * WT;
+        }
         E.nrel = E.nrel64 < BIG ? (uint32_t)E.nrel64 : BIG;
         const uint32_t nrel = E.nrel;
-        if (lane == 0 && tile + ahead < P.n_tiles) {   // a tile some warp takes about one tile from now, into L2
+        if (!BATCH && lane == 0 && tile + ahead < P.n_tiles) {   // a tile some warp takes about one tile from now, into L2
             const uint64_t fb = (uint64_t)(tile + ahead) * WT;
             const uint64_t left = P.n - fb;
             const uint32_t bytes = (uint32_t)(left < EVB ? left : EVB) & ~15u;
@@ -788,7 +850,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
 
         // (b) phase 1: every lane walks its slice from the PRE row
         const uint32_t t0 = (uint32_t)lane * SLICE;
-        const bool first = tile == 0 && lane == 0;
+        const bool first = dtile == 0 && lane == 0;   // the input's (document's) first chunk starts at 0
         Lane L;
         L.e = first ? E.P_start : E.P_pre;
         L.s = first ? 0u : NONE;
@@ -882,14 +944,15 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         gen_fail = __shfl_sync(0xffffffffu, gen_fail, 0);
         const uint64_t agg = fast_total + gen_cnt;
         const uint64_t fpos = fail != NONE ? (uint64_t)fail : gen_fail;
+        if (BATCH && lane == 0 && agg) atomicAdd(&P.dres[doc].total, agg);
         publish_tile(P, tile, agg);
 
         // the previous tile's output: its predecessors have had a whole tile to publish
         if (pend.tile != NONE) {
             uint64_t G = 0;
             if (!resolve_tile(P, pend.tile, G)) break;
-            report_failure(P, pend.tile, pend.fail, G, pend.agg);
-            copy_stage(P, E, stage, pend.staged, G);
+            report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
+            copy_stage(P, pend.kmap_s, stage, pend.staged, G);
             pend.tile = NONE;
             __syncwarp();
         }
@@ -899,7 +962,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         uint64_t G = 0;
         if (!defer) {   // rare: tokens beyond the stage or a chunk past the halo are written at once
             if (!resolve_tile(P, tile, G)) break;
-            report_failure(P, tile, fpos, G, agg);
+            report_failure<BATCH>(P, tile, fpos, G, agg, doc, dtile);
         }
         if (c0 != NONE) {
             uint32_t prev = last;
@@ -958,8 +1021,11 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             pend.staged = fast_total;
             pend.fail = fpos;
             pend.agg = agg;
+            pend.doc = doc;
+            pend.dtile = dtile;
+            pend.kmap_s = E.kmap_s;
         } else {
-            copy_stage(P, E, stage, fast_total < STAGE_CAP ? fast_total : STAGE_CAP, G);
+            copy_stage(P, E.kmap_s, stage, fast_total < STAGE_CAP ? fast_total : STAGE_CAP, G);
             if (do_long && lane == 0) {
                 uint64_t f2;
                 generic_chunk<FORM>(E, long_s1 - 1, &f2, P.out_kinds, P.out_lens, P.cap, G + fast_total);
@@ -970,8 +1036,8 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
     if (pend.tile != NONE) {
         uint64_t G = 0;
         if (resolve_tile(P, pend.tile, G)) {
-            report_failure(P, pend.tile, pend.fail, G, pend.agg);
-            copy_stage(P, E, stage, pend.staged, G);
+            report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
+            copy_stage(P, pend.kmap_s, stage, pend.staged, G);
         }
     }
 }
@@ -981,29 +1047,72 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
 // ---------------------------------------------------------------------------
 constexpr uint32_t SMEM_BUDGET = 227 * 1024;   // dynamic shared memory one CTA may use
 
-int warp_occupancy(lx_ctx *c, int form, uint32_t threads, uint32_t smem, int *occ)
+template <int FORM, bool BATCH>
+int occupancy_of(uint32_t threads, uint32_t smem, int *o)
 {
-    const uint64_t key = (3ull << 40) | ((uint64_t)threads << 33) | ((uint64_t)form << 32) | smem;
+    cudaError_t e = cudaFuncSetAttribute(lex_warps<FORM, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BUDGET);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(o, lex_warps<FORM, BATCH>, threads, smem);
+    return e == cudaSuccess ? LX_OK : LX_E_CUDA;
+}
+
+int warp_occupancy(lx_ctx *c, int form, bool batch, uint32_t threads, uint32_t smem, int *occ)
+{
+    const uint64_t key = (3ull << 40) | ((uint64_t)batch << 39) | ((uint64_t)threads << 33) | ((uint64_t)form << 32) |
+                         smem;
     for (auto &kv : c->occupancy)
         if (kv.first == key) {
             *occ = kv.second;
             return LX_OK;
         }
-    cudaError_t e;
-    int o = 0;
-    if (form == FORM_BYTE) {
-        e = cudaFuncSetAttribute(lex_warps<FORM_BYTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_BYTE>, threads, smem);
-    } else {
-        e = cudaFuncSetAttribute(lex_warps<FORM_CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lex_warps<FORM_CLASS>, threads, smem);
-    }
-    if (e != cudaSuccess) return LX_E_CUDA;
+    int o = 0, rc;
+    if (batch) rc = occupancy_of<FORM_CLASS, true>(threads, smem, &o);
+    else if (form == FORM_BYTE) rc = occupancy_of<FORM_BYTE, false>(threads, smem, &o);
+    else rc = occupancy_of<FORM_CLASS, false>(threads, smem, &o);
+    if (rc != LX_OK) return rc;
     if (o < 1) return LX_E_TOOBIG;
     c->occupancy.emplace_back(key, o);
     *occ = o;
     return LX_OK;
+}
+
+// Warps per CTA next to a table blob of `blob_bytes`: as many as the shared
+// memory budget holds, at most MAX_WARPS (or the context's setting).
+uint32_t warps_for(uint32_t want, uint32_t blob_bytes, uint32_t *smem)
+{
+    const uint32_t fixed = 512 + blob_bytes + 16;
+    if (fixed + WAREA > SMEM_BUDGET) return 0;
+    uint32_t nw = std::min<uint32_t>(MAX_WARPS, (SMEM_BUDGET - fixed) / WAREA);
+    if (want) nw = std::min<uint32_t>(nw, want);
+    *smem = fixed + nw * WAREA;
+    return nw;
+}
+
+// One warp per document writes the document's index over its tiles.
+__global__ void bt_tile_docs(const WDoc *docs, uint32_t n_docs, uint32_t *tile_doc)
+{
+    const uint32_t lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x / 32u);
+    for (uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) / 32u; d < n_docs; d += nw) {
+        const WDoc D = docs[d];
+        const uint32_t nt = (uint32_t)((D.n + WT - 1) / WT);
+        for (uint32_t k = lane; k < nt; k += 32) tile_doc[D.first_tile + k] = d;
+    }
+}
+
+// The async variant's status from the launch record.
+__global__ void as_finish(const WResult *r, uint64_t n, uint64_t cap, lx_async_result *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    lx_async_result o{LX_OK, 0, r->total, n};
+    if (r->inv_fail_pos) {
+        o.consumed = ~r->inv_fail_pos;
+        o.n_tokens = ~r->inv_fail_tok;
+    }
+    if (r->error & ERR_TIMEOUT) o.status = LX_E_TIMEOUT;
+    else if (r->error & ERR_SMEM) o.status = LX_E_TOOBIG;
+    else if (r->error) o.status = LX_E_CUDA;
+    else if (o.n_tokens > cap) o.status = LX_E_CAPACITY;
+    *out = o;
 }
 
 }  // namespace
@@ -1014,16 +1123,20 @@ bool warp_path_ok(const lx_tokenset *ts, int mode, const uint8_t *d_in)
     return ts->walk[mode].status == LX_OK && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
 }
 
-int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
-                    uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed, cudaStream_t st,
-                    uint64_t sparse_limit)
+namespace {
+
+// One input's launch: parameters, zeroed scratch size and shape.
+struct WarpLaunch {
+    WParams P;
+    uint32_t grid = 0, nwarps = 0, smem = 0;
+    size_t need = 0;
+    int form = FORM_BYTE;
+};
+
+int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                 uint32_t *d_lens, uint64_t capacity, uint64_t sparse_limit, WarpLaunch &L)
 {
     const WalkTable &w = ts->walk[mode];
-    if (n == 0) {
-        *n_tokens = 0;
-        *consumed = 0;
-        return LX_OK;
-    }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return LX_E_INVAL;
     DeviceTables dt;
@@ -1032,23 +1145,22 @@ int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint6
     const uint64_t n_tiles64 = (n + WT - 1) / WT;
     if (n_tiles64 > 0xFFFFFFF0ull) return LX_E_INVAL;
     const uint32_t n_tiles = (uint32_t)n_tiles64;
-    // as many warps per CTA as one SM's shared memory holds next to the table
-    const uint32_t fixed = 512 + (uint32_t)w.blob.size() + 16;
-    const uint32_t nwarps = std::min<uint32_t>(MAX_WARPS, (SMEM_BUDGET - fixed) / WAREA);
-    if (nwarps < 1) return LX_E_TOOBIG;
-    const uint32_t smem = fixed + nwarps * WAREA;
+    L.nwarps = warps_for(warps_setting(c, ts, mode), (uint32_t)w.blob.size(), &L.smem);
+    if (L.nwarps < 1) return LX_E_TOOBIG;
+    L.form = w.form;
     int occ = 0;
-    rc = warp_occupancy(c, w.form, 32 * nwarps, smem, &occ);
+    rc = warp_occupancy(c, w.form, false, 32 * L.nwarps, L.smem, &occ);
     if (rc != LX_OK) return rc;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * c->num_sms, (n_tiles + nwarps - 1) / nwarps);
+    L.grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * c->num_sms, (n_tiles + L.nwarps - 1) / L.nwarps);
 
     const uint32_t n_groups = (n_tiles + GS - 1) / GS;
     const size_t o_gstatus = 64 + 8 * (size_t)n_tiles, o_gdone = o_gstatus + 8 * (size_t)n_groups;
-    const size_t need = o_gdone + 4 * (size_t)n_groups;   // zeroed per call
-    rc = grow(&c->scratch, &c->scratch_bytes, need);
+    L.need = o_gdone + 4 * (size_t)n_groups;   // zeroed per call
+    rc = grow(&c->scratch, &c->scratch_bytes, L.need);
     if (rc != LX_OK) return rc;
     uint8_t *scr = static_cast<uint8_t *>(c->scratch);
-    WParams P;
+    WParams &P = L.P;
+    P = WParams{};
     P.in = d_in;
     P.n = n;
     P.blob = static_cast<const uint8_t *>(dt.d_walk[mode]);
@@ -1074,16 +1186,37 @@ int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint6
     P.withhold = c->withhold;
     P.sparse_limit = sparse_limit;
     static_assert(sizeof(WResult) == 32, "record layout");
+    return LX_OK;
+}
 
-    rc = cuda_err(cudaMemsetAsync(c->scratch, 0, need, st));
+void warp_launch(const WarpLaunch &L, cudaStream_t st)
+{
+    if (L.form == FORM_BYTE) lex_warps<FORM_BYTE, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P);
+    else lex_warps<FORM_CLASS, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P);
+}
+
+}  // namespace
+
+int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                    uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed, cudaStream_t st,
+                    uint64_t sparse_limit)
+{
+    if (n == 0) {
+        *n_tokens = 0;
+        *consumed = 0;
+        return LX_OK;
+    }
+    WarpLaunch L;
+    int rc = warp_prepare(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, sparse_limit, L);
+    if (rc != LX_OK) return rc;
+    rc = cuda_err(cudaMemsetAsync(c->scratch, 0, L.need, st));
     if (rc != LX_OK) return rc;
     if (c->timing) cudaEventRecord(c->ev[0], st);
-    if (w.form == FORM_BYTE) lex_warps<FORM_BYTE><<<grid, 32 * nwarps, smem, st>>>(P);
-    else lex_warps<FORM_CLASS><<<grid, 32 * nwarps, smem, st>>>(P);
+    warp_launch(L, st);
     rc = cuda_err(cudaGetLastError());
     if (c->timing) cudaEventRecord(c->ev[1], st);
     if (rc != LX_OK) return rc;
-    rc = cuda_err(cudaMemcpyAsync(c->h_res, P.res, sizeof(WResult), cudaMemcpyDeviceToHost, st));
+    rc = cuda_err(cudaMemcpyAsync(c->h_res, L.P.res, sizeof(WResult), cudaMemcpyDeviceToHost, st));
     if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(st));
     if (rc != LX_OK) return rc;
     const WResult r = *static_cast<const WResult *>(c->h_res);
@@ -1099,6 +1232,243 @@ int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint6
     *n_tokens = tokens;
     *consumed = con;
     return tokens > capacity ? LX_E_CAPACITY : LX_OK;
+}
+
+int lex_warp_async(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                   uint32_t *d_lens, uint64_t capacity, lx_async_result *d_result, cudaStream_t st)
+{
+    if (n == 0) {
+        const lx_async_result z{LX_OK, 0, 0, 0};
+        return cuda_err(cudaMemcpyAsync(d_result, &z, sizeof z, cudaMemcpyHostToDevice, st));
+    }
+    WarpLaunch L;
+    int rc = warp_prepare(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, 0, L);
+    if (rc != LX_OK) return rc;
+    rc = cuda_err(cudaMemsetAsync(c->scratch, 0, L.need, st));
+    if (rc != LX_OK) return rc;
+    warp_launch(L, st);
+    as_finish<<<1, 32, 0, st>>>(L.P.res, n, capacity, d_result);
+    return cuda_err(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// batches: every document of every token set in one launch
+// ---------------------------------------------------------------------------
+namespace {
+
+// The combined table of a batch's token sets (class form): all rows first,
+// each set's entries moved by its row offset, then one acceptance byte per
+// row, then per set its kind map, class map (256-aligned) and cut map, then
+// the WSet array.
+struct Combined {
+    std::vector<uint8_t> blob;
+    uint32_t rows_bytes = 0, acc_off = 0, sets_off = 0;
+};
+
+const WalkTable *class_walk(const lx_tokenset *ts, int mode)
+{
+    const WalkTable &w = ts->walk[mode];
+    if (w.status == LX_OK && w.form == FORM_CLASS) return &w;
+    const WalkTable &wc = ts->walk_cls[mode];
+    return wc.status == LX_OK ? &wc : nullptr;
+}
+
+// Rows of all sets must share one 16-bit shared-address window; the first
+// kilobyte of the window may be reserved.
+constexpr uint32_t BATCH_ROWS_MAX = 65536 - 1024;
+
+int combine(const lx_tokenset *const *sets, uint32_t n_sets, int mode, Combined &out)
+{
+    auto al = [](uint32_t x, uint32_t a) { return (x + a - 1) / a * a; };
+    std::vector<const WalkTable *> w(n_sets);
+    uint32_t rows = 0;
+    for (uint32_t s = 0; s < n_sets; s++) {
+        w[s] = class_walk(sets[s], mode);
+        if (!w[s]) return LX_E_TOOBIG;
+        rows += w[s]->rows_bytes;
+    }
+    if (rows > BATCH_ROWS_MAX) return LX_E_TOOBIG;
+    const uint32_t n_rows = rows >> 8;
+    out.rows_bytes = rows;
+    out.acc_off = rows;
+    uint32_t o = al(rows + n_rows, 256);
+    std::vector<uint32_t> base(n_sets), maps(n_sets);
+    uint32_t rb = 0;
+    for (uint32_t s = 0; s < n_sets; s++) {
+        base[s] = rb;
+        rb += w[s]->rows_bytes;
+        maps[s] = o;   // kmap (256 B), cmap (256 B, 256-aligned), cut (256 B)
+        o += 768;
+    }
+    out.sets_off = o;
+    out.blob.assign(al(o + (uint32_t)sizeof(WSet) * n_sets, 16), 0);
+    std::vector<WSet> ws(n_sets);
+    for (uint32_t s = 0; s < n_sets; s++) {
+        const WalkTable &t = *w[s];
+        const uint16_t *src = reinterpret_cast<const uint16_t *>(t.blob.data());
+        uint16_t *dst = reinterpret_cast<uint16_t *>(out.blob.data() + base[s]);
+        for (uint32_t k = 0; k < t.rows_bytes / 2; k++) dst[k] = (uint16_t)(src[k] + base[s]);   // rows move by base
+        std::memcpy(out.blob.data() + out.acc_off + (base[s] >> 8), t.blob.data() + t.acc_off, t.n_rows);
+        std::memcpy(out.blob.data() + maps[s], t.blob.data() + t.kmap_off, 256);
+        std::memcpy(out.blob.data() + maps[s] + 256, t.blob.data() + t.cmap_off, 256);
+        std::memcpy(out.blob.data() + maps[s] + 512, t.blob.data() + t.cut_off, 256);
+        ws[s] = WSet{base[s] + t.p_start, base[s] + t.p_pre, base[s], maps[s], maps[s] + 256, maps[s] + 512};
+    }
+    std::memcpy(out.blob.data() + out.sets_off, ws.data(), sizeof(WSet) * n_sets);
+    return LX_OK;
+}
+
+}  // namespace
+
+int lex_batch_warp(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, const lx_doc *docs, uint32_t n_docs,
+                   int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, lx_doc_result *results,
+                   uint64_t *n_total, cudaStream_t st)
+{
+    // applicable: class-form tables that share the address window, aligned documents
+    if (n_sets == 0 || n_sets > 16) return LX_SPARSE;
+    for (uint32_t i = 0; i < n_docs; i++)
+        if (docs[i].n && (reinterpret_cast<uintptr_t>(docs[i].data) & 15u)) return LX_SPARSE;
+    std::vector<uint64_t> key = {0xB47C4ull, (uint64_t)mode, n_sets};
+    for (uint32_t s = 0; s < n_sets; s++) key.push_back(sets[s]->serial);
+    if (key != c->wb_key) {
+        Combined cb;
+        const int rc = combine(sets, n_sets, mode, cb);
+        if (rc == LX_E_TOOBIG) return LX_SPARSE;
+        if (rc != LX_OK) return rc;
+        int r2 = grow(&c->wb_dev, &c->wb_dev_bytes, cb.blob.size());
+        if (r2 != LX_OK) return r2;
+        r2 = cuda_err(cudaMemcpy(c->wb_dev, cb.blob.data(), cb.blob.size(), cudaMemcpyHostToDevice));
+        if (r2 != LX_OK) return r2;
+        c->wb_key = key;
+        c->wb_blob_bytes = (uint32_t)cb.blob.size();
+        c->wb_rows = cb.rows_bytes;
+        c->wb_acc_off = cb.acc_off;
+        c->wb_sets_off = cb.sets_off;
+    }
+
+    // documents in their order; empty ones take no tile
+    std::vector<WDoc> hd;
+    std::vector<uint32_t> idx;
+    uint64_t TT = 0;
+    for (uint32_t i = 0; i < n_docs; i++) {
+        if (!docs[i].n) continue;
+        hd.push_back(WDoc{docs[i].data, docs[i].n, (uint32_t)TT, docs[i].set});
+        idx.push_back(i);
+        TT += (docs[i].n + WT - 1) / WT;
+        if (TT > 0xFFFFFFF0ull) return LX_E_INVAL;
+    }
+    if (hd.empty()) return LX_OK;
+    const uint32_t D = (uint32_t)hd.size(), n_tiles = (uint32_t)TT, n_groups = (n_tiles + GS - 1) / GS;
+
+    uint32_t smem = 0;
+    const uint32_t nwarps = warps_for(c->warps, c->wb_blob_bytes, &smem);
+    if (nwarps < 1) return LX_SPARSE;
+    int occ = 0;
+    int rc = warp_occupancy(c, FORM_CLASS, true, 32 * nwarps, smem, &occ);
+    if (rc == LX_E_TOOBIG) return LX_SPARSE;
+    if (rc != LX_OK) return rc;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * c->num_sms, (n_tiles + nwarps - 1) / nwarps);
+
+    // device scratch: [zeroed: record, counter, statuses, group words, document records][documents][tile map]
+    auto al = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
+    const size_t o_status = 64, o_gstatus = al(o_status + 8 * (size_t)n_tiles, 64);
+    const size_t o_gdone = al(o_gstatus + 8 * (size_t)n_groups, 64), o_dres = al(o_gdone + 4 * (size_t)n_groups, 64);
+    const size_t zero_end = o_dres + sizeof(WDocRes) * D;
+    const size_t o_docs = al(zero_end, 256), o_tdoc = al(o_docs + sizeof(WDoc) * D, 256);
+    const size_t dev_total = o_tdoc + 4 * (size_t)n_tiles;
+    // pinned staging: documents up, then the record and the document records down
+    const size_t h_down = al(sizeof(WDoc) * D, 64), host_total = h_down + zero_end;
+    bool moved = false;
+    {
+        void *od = c->b_dev, *oh = c->b_host;
+        rc = grow(&c->b_dev, &c->b_dev_bytes, dev_total);
+        if (rc == LX_OK) rc = grow_host(&c->b_host, &c->b_host_bytes, host_total);
+        if (rc != LX_OK) return rc;
+        moved = od != c->b_dev || oh != c->b_host;
+    }
+    uint8_t *dv = static_cast<uint8_t *>(c->b_dev);
+    uint8_t *hs = static_cast<uint8_t *>(c->b_host);
+    std::memcpy(hs, hd.data(), sizeof(WDoc) * D);
+
+    std::vector<uint64_t> gkey = {0xB47C5ull, D, TT, (uint64_t)mode, (uint64_t)(uintptr_t)d_kinds,
+                                  (uint64_t)(uintptr_t)d_lens, capacity, (uint64_t)(uintptr_t)dv,
+                                  (uint64_t)(uintptr_t)hs, c->timeout_ns, grid, nwarps,
+                                  (uint64_t)(uintptr_t)c->wb_dev};
+    gkey.insert(gkey.end(), key.begin(), key.end());
+    if (moved || gkey != c->b_key || !c->b_exec) {
+        if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+        c->b_exec = nullptr;
+        c->b_key.clear();
+        if (!c->b_stream && cudaStreamCreateWithFlags(&c->b_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return LX_E_CUDA;
+        cudaStream_t cs = c->b_stream;
+        WParams P{};
+        P.in = nullptr;
+        P.n = 0;
+        P.blob = static_cast<const uint8_t *>(c->wb_dev);
+        P.blob_bytes = c->wb_blob_bytes;
+        P.rows_bytes = c->wb_rows;
+        P.row_shift = 8;
+        P.acc_off = c->wb_acc_off;
+        P.out_kinds = d_kinds;
+        P.out_lens = d_lens;
+        P.cap = capacity;
+        P.res = reinterpret_cast<WResult *>(dv);
+        P.tile_counter = reinterpret_cast<unsigned int *>(dv + 32);
+        P.status = reinterpret_cast<unsigned long long *>(dv + o_status);
+        P.gstatus = reinterpret_cast<unsigned long long *>(dv + o_gstatus);
+        P.gdone = reinterpret_cast<unsigned int *>(dv + o_gdone);
+        P.n_tiles = n_tiles;
+        P.timeout_ns = c->timeout_ns;
+        P.withhold = NONE;
+        P.sparse_limit = 0;   // long chunks are walked byte by byte: no document leaves the launch
+        P.docs = reinterpret_cast<const WDoc *>(dv + o_docs);
+        P.tile_doc = reinterpret_cast<const uint32_t *>(dv + o_tdoc);
+        P.dres = reinterpret_cast<WDocRes *>(dv + o_dres);
+        P.sets_off = c->wb_sets_off;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LX_E_CUDA;
+        cudaMemsetAsync(dv, 0, zero_end, cs);
+        cudaMemcpyAsync(dv + o_docs, hs, sizeof(WDoc) * D, cudaMemcpyHostToDevice, cs);
+        bt_tile_docs<<<(D + 7) / 8, 256, 0, cs>>>(P.docs, D, const_cast<uint32_t *>(P.tile_doc));
+        lex_warps<FORM_CLASS, true><<<grid, 32 * nwarps, smem, cs>>>(P);
+        cudaMemcpyAsync(hs + h_down, dv, zero_end, cudaMemcpyDeviceToHost, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->b_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->b_exec = nullptr;
+            cudaGetLastError();
+            return LX_E_CUDA;
+        }
+        c->b_key = gkey;
+    }
+    if (c->timing) cudaEventRecord(c->ev[0], st);
+    rc = cuda_err(cudaGraphLaunch(c->b_exec, st));
+    if (c->timing) cudaEventRecord(c->ev[1], st);
+    if (rc == LX_OK) rc = cuda_err(cudaStreamSynchronize(st));
+    if (rc != LX_OK) return rc;
+
+    const WResult r = *reinterpret_cast<const WResult *>(hs + h_down);
+    if (r.error & ERR_TIMEOUT) return LX_E_TIMEOUT;
+    if (r.error & ERR_SMEM) return LX_SPARSE;   // the rows did not fit the window after all
+    if (r.error) return LX_E_CUDA;
+    const WDocRes *dres = reinterpret_cast<const WDocRes *>(hs + h_down + o_dres);
+    for (uint32_t j = 0; j < D; j++) {
+        const WDocRes &x = dres[j];
+        lx_doc_result &o = results[idx[j]];
+        if (x.out_off1 == 0) return LX_E_CUDA;   // every document's first tile reports its offset
+        o.out_off = x.out_off1 - 1;
+        if (x.inv_fail_pos) {
+            o.consumed = ~x.inv_fail_pos;
+            o.n_tokens = ~x.inv_fail_tok - o.out_off;
+        } else {
+            o.consumed = hd[j].n;
+            o.n_tokens = x.total;
+        }
+    }
+    *n_total = r.total;
+    return r.total > capacity ? LX_E_CAPACITY : LX_OK;
 }
 
 }  // namespace lx

@@ -19,6 +19,8 @@ struct lx_tuned {
     int mode;
     uint32_t ks, ctas, cls;   // cls: class-indexed table
     float ms;   // measured by lx_autotune (0 when set by hand)
+    int kernel = 0;           // LX_KERNEL_TILE or _WARP when lx_autotune chose one (0: not chosen)
+    uint32_t warps = 0;       // warps per CTA it chose for the warp-tile kernel (0: as many as fit)
 };
 
 struct lx_ctx {
@@ -58,6 +60,14 @@ struct lx_ctx {
     size_t lv_dev_bytes = 0;
     // lx_lex kernel choice (lx_ctx_set_kernel): LX_KERNEL_AUTO, _TILE or _WARP
     int kernel = 0;
+    // warps per CTA of the warp-tile kernel (0: as many as shared memory holds)
+    uint32_t warps = 0;
+    // lx_lex_batch on the warp-tile kernel: the combined table of the last
+    // batch's token sets (key: mode and the sets' serial numbers)
+    void *wb_dev = nullptr;
+    size_t wb_dev_bytes = 0;
+    std::vector<uint64_t> wb_key;
+    uint32_t wb_blob_bytes = 0, wb_rows = 0, wb_acc_off = 0, wb_sets_off = 0;
     // optional kernel timing
     bool timing = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -84,6 +94,21 @@ int ensure_device_tables(const lx_tokenset *ts, int device, DeviceTables *out);
 // LX_LOOKAHEAD, leaving the input to the enumerative path (guarded).
 constexpr int LX_SPARSE = -100;   // internal status, never returned by the C ABI
 bool warp_path_ok(const lx_tokenset *ts, int mode, const uint8_t *d_in);
+// Warps per CTA for the warp-tile kernel on (ts, mode): the context's
+// setting, else lx_autotune's choice, else 0 (as many as fit).
+uint32_t warps_setting(const lx_ctx *c, const lx_tokenset *ts, int mode);
+// lx_lex_async (lexwarp.cu): the warp-tile kernel and a status kernel that
+// writes the result record to device memory; no synchronization, no fallback.
+int lex_warp_async(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
+                   uint32_t *d_lens, uint64_t capacity, lx_async_result *d_result, cudaStream_t st);
+// lx_lex_batch in one launch of the warp-tile kernel (lexwarp.cu): every
+// document of every token set, the sets' class-form tables side by side in
+// shared memory, the output in document order.  LX_SPARSE when not
+// applicable (a table without a class form, rows beyond the 16-bit window,
+// an unaligned document): the caller takes the per-set tile kernels.
+int lex_batch_warp(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, const lx_doc *docs, uint32_t n_docs,
+                   int mode, uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, lx_doc_result *results,
+                   uint64_t *n_total, cudaStream_t st);
 int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
                     uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens, uint64_t *consumed, cudaStream_t st,
                     uint64_t sparse_limit);

@@ -3,6 +3,7 @@
 // Pure host code.
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <new>
@@ -501,6 +502,8 @@ extern "C" int lx_compile_tokenset(const lx_dfa *dfa, const uint16_t *discarded,
 
     lx_tokenset *t = new (std::nothrow) lx_tokenset();
     if (!t) return LX_E_NOMEM;
+    static std::atomic<uint64_t> next_serial{1};
+    t->serial = next_serial++;
     try {
         t->n_states = S;
         t->n_classes = C;
