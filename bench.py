@@ -715,11 +715,12 @@ def main():
         line["config"]["certified"] = {"exact": fmt(ex_mask), "modulo": fmt(mo_mask)}
         if not full:
             # the same filtered stream under exact cuts: with no exact-certified
-            # byte the certified path is one chunk, so it runs through the
-            # enumerative path, which needs no certified byte; its output must
-            # equal the modulo-cut output (both are pi_I(tok(w)))
+            # byte, lx_lex cuts at certified two-byte windows (warp-tile kernel)
+            # where the token set has them, else enumerates entry contexts; its
+            # output must equal the modulo-cut output (both are pi_I(tok(w)))
             x_k = torch.empty_like(d_k)
             x_l = torch.empty_like(d_l)
+            win_ctx = lg.lx_tokenset_walk_table(ts, lg.LX_FILTERED_EXACT)[2].get("n_ctx", 0)
             x_ms = []
             for i in range(5):
                 rcx, ntx, conx = lg.lx_lex(ctx, ts, d_in, lg.LX_FILTERED_EXACT, x_k, x_l, stream=stream)
@@ -731,7 +732,9 @@ def main():
             line["exact_certificate"] = {
                 "mode": "LX_FILTERED_EXACT",
                 "path": "lx_lex (certified cuts)" if ex_mask.any() else
-                        "lx_lex: no exact-certified byte, so the hybrid plan enumerates entry contexts",
+                        ("lx_lex: no exact-certified byte; cuts at certified two-byte windows (warp-tile kernel)"
+                         if win_ctx else "lx_lex: no exact-certified byte, so the hybrid plan enumerates entry contexts"),
+                "window_contexts": win_ctx,
                 "kernel_ms": statistics.median(x_ms), "value": n / (statistics.median(x_ms) / 1e3) / 1e9,
                 "unit": "GB/s", "same_output_as_modulo": bool(same)}
             del x_k, x_l

@@ -149,9 +149,10 @@ int lx_tokenset_class_table(const lx_tokenset *ts, int mode, void *out, uint32_t
  * lx_tokenset_walk_table -- the event-code walk table of `mode` that the
  * warp-tile kernel of lx_lex stages in shared memory (for inspection and
  * host-side tests).  Copies min(cap, size) bytes of the blob to `out` (host,
- * may be NULL) and fills the first meta_len (<= 10) entries of meta:
+ * may be NULL) and fills the first meta_len (<= 12) entries of meta:
  *   { blob bytes, table_form, n_rows, row_shift, p_start, p_pre,
- *     acc_off, kmap_off, cmap_off, cut_off }.
+ *     acc_off, kmap_off, cmap_off, cut_off, n_ctx, ctx_off }
+ * (n_ctx, ctx_off: the split-window context classes, lx_window_certificates).
  * Entries are u16: target row offset (from the blob start) | event code << 1
  * (code 0: no token ended before the byte; 1: a discarded token ended;
  * c >= 2: a kept token of kind kind_map[c] ended).  Byte form: row r holds
@@ -162,6 +163,27 @@ int lx_tokenset_class_table(const lx_tokenset *ts, int mode, void *out, uint32_t
  */
 int lx_tokenset_walk_table(const lx_tokenset *ts, int mode, void *out, uint32_t cap, uint32_t *meta,
                            uint32_t meta_len);
+
+/*
+ * lx_window_certificates -- two-byte split windows, the generalisation of the
+ * exact certificate (Definition 2) to a byte in one byte of left context that
+ * Sections 1 and 9 mention (the paper defines no window certificate; this is
+ * the library's, written in the header so that it can be checked):
+ *   Z(a)      = { delta+(q, a) : q in Q+ }   (the states right after reading a)
+ *   cert(a,b) = q0 not re-entrant, delta+(q0, b) defined, and no state of Z(a)
+ *               has a transition on b into Q+.
+ * With q0 not re-entrant no token can read a and then b, so every occurrence
+ * of a b has a token boundary between the bytes: a cut before b is exact
+ * (Theorem 1's argument applies unchanged).  b is exact-certified iff (a, b)
+ * is certified for every a.  Fills pairs[a * 8 + (b >> 5)] bit (b & 31) for
+ * every pair (256 x 8 words, host).  In the exact modes the warp-tile kernel
+ * also cuts at certified windows: its walk table gains PRE_k rows (PRE in the
+ * context class k of the byte before), meta[10] = number of context classes K
+ * and meta[11] = offset of the u8[256] context map; the cut table at cut_off
+ * then has K + 1 rows of 256 bytes (row k: a chunk may start at byte b after a
+ * byte of context k).  Returns LX_OK.
+ */
+int lx_window_certificates(const lx_tokenset *ts, uint32_t *pairs);
 
 /*
  * lx_tokenset_liveness -- the liveness automaton of the failed-lookahead guard

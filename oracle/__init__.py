@@ -21,11 +21,17 @@ reference run used by the tests:
 * ``contexts``       -- (submodule) entry contexts of the serial scan, their
                         candidate sets and chunk runs entered in a context:
                         splitting a token set with no certified byte.
+* ``live``           -- (submodule) the live sets behind the failed-lookahead
+                        guard and the guarded serial scan.
+* ``windows``        -- (submodule) certified two-byte split windows.
+* ``model``          -- (submodule) FP64 reference of the entry-context model.
 
 Parity pins: tests/test_oracle_pins.py (worked examples of the paper),
 tests/test_oracle_contexts.py (exhaustive checks of the entry contexts),
 tests/test_oracle_bruteforce.py (exhaustive checks on tiny token sets),
-tests/test_oracle_re.py (Python ``re.fullmatch`` cross-check of the scanner).
+tests/test_oracle_re.py (Python ``re.fullmatch`` cross-check of the scanner),
+tests/test_oracle_discard_plan.py (hand-written pi_I streams and plans),
+tests/test_oracle_live.py, tests/test_oracle_windows.py, tests/test_oracle_model.py.
 """
 
 from __future__ import annotations

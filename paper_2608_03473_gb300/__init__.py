@@ -54,7 +54,8 @@ LX_FILTERED_MODULO = 2
 # every function declared in include/lexgpu.h
 EXPORTED = (
     "lx_compile_tokenset", "lx_compile_tokenset_framed", "lx_certificates", "lx_tokenset_info", "lx_tokenset_table", "lx_tokenset_class_table",
-    "lx_tokenset_walk_table", "lx_tokenset_scan_table", "lx_tokenset_liveness", "lx_liveness",
+    "lx_tokenset_walk_table", "lx_window_certificates", "lx_tokenset_scan_table", "lx_tokenset_liveness",
+    "lx_liveness",
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
     "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold", "lx_ctx_set_kernel",
@@ -112,6 +113,7 @@ def load_library(path: Optional[str] = None):
             "lx_tokenset_table": (i32, [vp, i32, vp, u32, vp, u32]),
             "lx_tokenset_class_table": (i32, [vp, i32, vp, u32, vp, u32]),
             "lx_tokenset_walk_table": (i32, [vp, i32, vp, u32, vp, u32]),
+            "lx_window_certificates": (i32, [vp, vp]),
             "lx_tokenset_scan_table": (i32, [vp, vp, u32, vp, u32]),
             "lx_tokenset_liveness": (i32, [vp, vp, u32, vp, u32]),
             "lx_liveness": (i32, [vp, vp, vp, u64, vp, vp]),
@@ -275,12 +277,22 @@ def lx_tokenset_table(ts: Tokenset, mode: int, class_table: bool = False) -> Tup
 def lx_tokenset_walk_table(ts: Tokenset, mode: int) -> Tuple[int, np.ndarray, dict]:
     """The event-code walk table of ``mode`` (status, blob, layout)."""
     lib = load_library()
-    meta = (ctypes.c_uint32 * 10)()
-    lib.lx_tokenset_walk_table(ts.handle, int(mode), None, 0, meta, 10)
+    meta = (ctypes.c_uint32 * 12)()
+    lib.lx_tokenset_walk_table(ts.handle, int(mode), None, 0, meta, 12)
     blob = np.zeros(max(int(meta[0]), 1), np.uint8)
-    rc = lib.lx_tokenset_walk_table(ts.handle, int(mode), blob.ctypes.data, int(blob.size), meta, 10)
-    keys = ("bytes", "form", "n_rows", "row_shift", "p_start", "p_pre", "acc_off", "kmap_off", "cmap_off", "cut_off")
+    rc = lib.lx_tokenset_walk_table(ts.handle, int(mode), blob.ctypes.data, int(blob.size), meta, 12)
+    keys = ("bytes", "form", "n_rows", "row_shift", "p_start", "p_pre", "acc_off", "kmap_off", "cmap_off", "cut_off",
+            "n_ctx", "ctx_off")
     return rc, blob[:int(meta[0])], dict(zip(keys, [int(x) for x in meta]))
+
+
+def lx_window_certificates(ts: Tokenset) -> Tuple[int, np.ndarray]:
+    """(status, bool[256, 256]): [a, b] when a cut before b is certified after a."""
+    lib = load_library()
+    words = np.zeros(256 * 8, np.uint32)
+    rc = lib.lx_window_certificates(ts.handle, words.ctypes.data)
+    bits = np.unpackbits(words.view(np.uint8).reshape(256, 32), axis=1, bitorder="little")
+    return rc, bits.astype(bool)
 
 
 def lx_ctx_create() -> Ctx:

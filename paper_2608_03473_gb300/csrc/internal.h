@@ -97,10 +97,11 @@ constexpr uint16_t SCAN_ACCEPT = 0x8000u;   // next-state flag: the target state
 //                  with a 256-byte map cmap2[b] = 2 class(b) on a 256-byte
 //                  boundary, so the map address is one PRMT and the next
 //                  address (entry & ~0xFF) | cmap2[b]: one LOP3.
-// Blob: [rows][acc u8 per row][kind_map u16 x 128][cmap2 u8 x 256][cut u8 x 256].
+// Blob: [rows][acc u8 per row][kind_map u16 x 128][cmap2 u8 x 256][cut u8 x 256 x (K+1)][ctx u8 x 256].
 // acc[r] is 2 * the code of the kind row r accepts (0: not accepting).
 // ---------------------------------------------------------------------------
 constexpr uint32_t WALK_CODES = 128;   // codes 0..127: at most 126 kept kinds
+constexpr uint32_t WALK_MAX_CTX = 15;  // split-window context classes (PRE_k rows) at most
 struct WalkTable {
     int status = LX_E_TOOBIG;
     int form = FORM_BYTE;
@@ -108,6 +109,11 @@ struct WalkTable {
     uint32_t p_start = 0, p_pre = 0;      // relative row addresses (SLOW is 0)
     uint32_t acc_off = 0, kmap_off = 0, cmap_off = 0, cut_off = 0;
     uint32_t n_kept = 0;                  // kept kinds (codes 2 .. n_kept + 1)
+    // split windows (exact modes): K context classes; PRE_k rows follow PRE;
+    // ctx map u8[256] at ctx_off (context class of a byte, 0: none); the cut
+    // table at cut_off holds K + 1 rows of 256 bytes (row k: a chunk may start
+    // at byte b when the byte before has context k; row 0: single bytes)
+    uint32_t n_ctx = 0, ctx_off = 0;
     std::vector<uint8_t> blob;
 };
 
@@ -159,6 +165,10 @@ struct lx_tokenset {
     std::vector<uint8_t> live;        // [q], Q+
     bool reentrant = false;
     uint32_t exact[8] = {0}, modulo[8] = {0};
+    // two-byte split windows: win[a * 8 + (b >> 5)] bit b: a cut before b is
+    // certified after a (q0 not re-entrant, delta+(q0, b) defined, and no
+    // state of delta+(Q+, a) has a live transition on b)
+    std::vector<uint32_t> win;
     lx::HostTable tab[3];       // per mode: byte-indexed when it fits, else class-indexed
     lx::HostTable tab_cls[3];   // per mode: class-indexed (only when tab[m] is byte-indexed)
     lx::ScanTable scan;

@@ -1317,6 +1317,13 @@ static bool mode_has_cuts(const lx_tokenset *ts, int mode)
     return false;
 }
 
+// The same for the warp-tile kernel, whose walk table also cuts at certified
+// two-byte windows in the exact modes.
+static bool warp_has_cuts(const lx_tokenset *ts, int mode)
+{
+    return mode_has_cuts(ts, mode) || (ts->walk[mode].status == LX_OK && ts->walk[mode].n_ctx > 0);
+}
+
 // Launch the tile kernel and read back its result record.
 static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode,
                       uint16_t *d_kinds, uint32_t *d_lens, uint64_t capacity, uint64_t *n_tokens,
@@ -1327,11 +1334,14 @@ static int lex_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uin
     // apart, entry contexts are enumerated instead (lx_lex_enumerative), so
     // no call degenerates to one lane walking the input.
     const bool can_enumerate = !force && c->kernel == LX_KERNEL_AUTO && ts->scan.status == LX_OK;
-    if (can_enumerate && !mode_has_cuts(ts, mode))
-        return lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st);
     const lx_tuned *tu = tuned_for(c, ts, mode);
     const bool tuned_tile = c->kernel == LX_KERNEL_AUTO && tu && tu->kernel == LX_KERNEL_TILE;
-    if (!force && c->kernel != LX_KERNEL_TILE && !tuned_tile && warp_path_ok(ts, mode, d_in)) {
+    const bool warp_ok = !force && c->kernel != LX_KERNEL_TILE && warp_path_ok(ts, mode, d_in);
+    // the tile kernel cuts at single certified bytes only; the warp kernel also at windows
+    const bool warp_windows = warp_ok && !mode_has_cuts(ts, mode) && warp_has_cuts(ts, mode);
+    if (can_enumerate && !mode_has_cuts(ts, mode) && !warp_windows)
+        return lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st);
+    if (warp_ok && (!tuned_tile || warp_windows)) {
         const int rc = lex_warp_device(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, n_tokens, consumed, st,
                                        can_enumerate ? SPARSE_LIMIT : 0);
         if (rc != LX_SPARSE && rc != LX_LOOKAHEAD) return rc;

@@ -91,7 +91,7 @@ struct WDoc {
 // One token set's rows and maps in a batch's combined table (offsets from
 // the table's start; the rows of all sets lie in one 16-bit address window).
 struct WSet {
-    uint32_t p_start, p_pre, p_slow, kmap_off, cmap_off, cut_off;
+    uint32_t p_start, p_pre, p_slow, kmap_off, cmap_off, cut_off, ctx_off, pad;
 };
 
 struct WDocRes {
@@ -106,7 +106,7 @@ struct WParams {
     uint64_t n;
     const uint8_t *blob;
     uint32_t blob_bytes, rows_bytes, row_shift;
-    uint32_t p_start, p_pre, acc_off, kmap_off, cmap_off, cut_off;
+    uint32_t p_start, p_pre, acc_off, kmap_off, cmap_off, cut_off, ctx_off;
     uint16_t *out_kinds;
     uint32_t *out_lens;
     uint64_t cap;
@@ -124,13 +124,15 @@ struct WParams {
     const uint32_t *tile_doc;   // document of every tile
     WDocRes *dres;
     uint32_t sets_off;          // WSet array in the table blob
+    uint32_t n_ctx;             // split-window context classes of the table (0: none)
 };
 
 // Shared addresses of the tables and of this warp's buffers, and the tile.
 struct WEnv {
     uint32_t P_start, P_pre, P_slow;
-    uint32_t tb_s, acc_s, kmap_s, cmap_s, cut_s, shift;
+    uint32_t tb_s, acc_s, kmap_s, cmap_s, cut_s, ctx_s, shift;   // P_pre: the first PRE row (PRE_k follow)
     uint32_t ev;                 // event buffer: code of position p at ev + p
+    uint32_t windows;            // the table has split-window contexts (PRE_k rows)
     unsigned int *err;           // the result record's error word
     uint32_t guard;              // 1: backtracking past its step budget stops the call (ERR_LOOKAHEAD)
     const uint8_t *in;           // the tile's first byte
@@ -158,14 +160,21 @@ __device__ __forceinline__ uint32_t acc_code(const WEnv &E, uint32_t e)
     return lds_u8(E.acc_s + ((e - E.tb_s) >> E.shift));
 }
 
+// Whether a chunk may start at byte b after byte a: a certified byte, or a
+// certified two-byte window (the cut table's row of a's context class).
+__device__ __forceinline__ bool is_cut(const WEnv &E, uint32_t a, uint32_t b)
+{
+    return lds_u8(E.cut_s + (lds_u8(E.ctx_s + a) << 8) + b) != 0;
+}
+
 // Four byte steps over the little-endian word w as branch-free PTX; the
 // dependent chain per byte is one LOP3 and the table load (the class form
 // adds an independent PRMT and class-map load per byte).  The four event
 // codes (the low byte of each entry) are packed into one word and stored at
 // `ev` when the predicate holds: phase 1 (PH 1) stores a word that did not
-// begin in PRE (x = P_pre); phase 2 (PH 2) a word whose last byte y lies at
+// begin in a PRE row (x = P_pre, the first of them); phase 2 (PH 2) a word whose last byte y lies at
 // or before the chunk end x.  cm: the class map's shared address.
-#define LXW_PRED1 "setp.ne.u32 ps, %0, %3;\n\t"
+#define LXW_PRED1 "setp.lo.u32 ps, %0, %3;\n\t"
 #define LXW_PRED2 "setp.le.u32 ps, %4, %3;\n\t"
 #define LXW_B(XOP, VIN, VOUT)                                                  \
     XOP "lop3.b32 a, " VIN ", t, %7, 0xD8;\n\t"                                \
@@ -228,25 +237,35 @@ struct Lane {
     uint32_t own;     // positions below this may record a failure (the chunk end)
     bool act;
     bool coarse;      // s is the start of the block in which PRE was left, not yet the byte
+    uint4 blk;        // that block's bytes
+    uint32_t pe;      // the PRE row at that block's start
 };
 
-// The block walk only notes the 16-byte block in which a lane left PRE; this
-// finds the byte (the first certified byte of the block) and stores the event
-// codes after it in its word, which the block step did not store (the word
-// began in PRE): the state after the certified byte is PRE's step on it.
+// The block walk only notes the 16-byte block in which a lane left PRE (and
+// keeps its bytes and its PRE row at the block start in registers); this
+// finds the byte (the first certified byte or window of the block, where the
+// PRE rows are left) and stores the event codes after it in its word, which
+// the block step did not store (the word began in PRE): the state after the
+// chunk's first byte is q0's step on it.
 template <int FORM>
 __device__ void refine_start(const WEnv &E, Lane &L)
 {
     if (!L.coarse) return;
     L.coarse = false;
     const uint32_t pb = L.s;
-    uint32_t j = 0;
-    while (j < BLK && !lds_u8(E.cut_s + __ldg(E.in + pb + j))) j++;
+    const uint4 c = L.blk;
+    // replay the PRE rows over the block: the byte where they are left
+    uint32_t j = 0, e = L.pe;
+    for (; j < BLK; j++) {
+        const uint32_t v = wstep<FORM>(E, e, byte_of(pick4(j >> 2, c.x, c.y, c.z, c.w), j & 3u));
+        e = v;
+        if (v < E.P_pre) break;
+    }
+    if (j == BLK) j = BLK - 1;   // unreachable: the block leaves PRE
     L.s = pb + j;
-    uint32_t e = wstep<FORM>(E, E.P_pre, __ldg(E.in + L.s));
-    for (uint32_t k = L.s + 1; k < ((L.s + 4) & ~3u); k++) {
-        e = wstep<FORM>(E, e, __ldg(E.in + k));
-        sts_u8(eva(E, k), e & 0xFFu);
+    for (uint32_t k = j + 1; k < ((j + 4) & ~3u); k++) {
+        e = wstep<FORM>(E, e, byte_of(pick4(k >> 2, c.x, c.y, c.z, c.w), k & 3u));
+        sts_u8(eva(E, pb + k), e & 0xFFu);
     }
 }
 
@@ -320,8 +339,8 @@ __device__ void scalar_steps(const WEnv &E, Lane &L, uint32_t upto, uint32_t hi)
     while (L.p < upto && L.act) {
         const uint32_t k = L.p, e0 = L.e;
         const uint32_t v = wstep<FORM>(E, e0, __ldg(E.in + k));
-        if (e0 == E.P_pre && v != E.P_pre && L.s == NONE) L.s = k;
-        if (e0 != E.P_pre && k <= hi) sts_u8(eva(E, k), v & 0xFFu);
+        if (e0 >= E.P_pre && v < E.P_pre && L.s == NONE) L.s = k;
+        if (e0 < E.P_pre && k <= hi) sts_u8(eva(E, k), v & 0xFFu);
         L.e = v;
         L.p = k + 1;
         if (v == E.P_slow) {
@@ -345,7 +364,7 @@ __device__ void finalize(const WEnv &E, Lane &L, uint32_t hi)
     }
     while (L.act) {
         const uint32_t e = L.e;
-        if (e == E.P_start || e == E.P_pre) return;
+        if (e == E.P_start || e >= E.P_pre) return;
         if (e != E.P_slow) {
             const uint32_t ac = acc_code(E, e);
             if (ac) {
@@ -427,7 +446,7 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
                 if (v & 0xFFu) {
                     emit(v & 0xFFu, p - tok);
                     tok = p;
-                    if (p >= WT && lds_u8(E.cut_s + b)) return cnt;
+                    if (p >= WT && is_cut(E, rd.at(p - 1), b)) return cnt;
                 }
                 e = v;
                 p++;
@@ -461,7 +480,7 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
         tok = p = r;
         e = E.P_start;
         if (r == n) return cnt;
-        if (r >= WT && lds_u8(E.cut_s + rd.at(r))) return cnt;
+        if (r >= WT && is_cut(E, rd.at(r - 1), rd.at(r))) return cnt;
     }
 }
 
@@ -694,14 +713,16 @@ __device__ __forceinline__ void phase1_step(const WEnv &E, Lane &L, const uint4 
 {
     if (!L.act) return;
     if (L.p + BLK <= E.nrel) {
-        const uint32_t pb = L.p, ev = eva(E, pb);
+        const uint32_t pb = L.p, ev = eva(E, pb), e_in = L.e;
         wword<FORM, 1>(L.e, cur.x, ev, E.P_pre, 0, E.cmap_s);
         wword<FORM, 1>(L.e, cur.y, ev + 4, E.P_pre, 0, E.cmap_s);
         wword<FORM, 1>(L.e, cur.z, ev + 8, E.P_pre, 0, E.cmap_s);
         wword<FORM, 1>(L.e, cur.w, ev + 12, E.P_pre, 0, E.cmap_s);
-        if (L.s == NONE && L.e != E.P_pre) {   // PRE was left in this block (the byte: refine_start)
+        if (L.s == NONE && L.e < E.P_pre) {   // PRE was left in this block (the byte: refine_start)
             L.s = pb;
             L.coarse = true;
+            L.blk = cur;
+            L.pe = e_in;
         }
         L.p = pb + BLK;
         if (L.e == E.P_slow) slow_fix<FORM>(E, L, L.p, BIG);
@@ -772,6 +793,8 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
     E.kmap_s = tb_s + P.kmap_off;
     E.cmap_s = tb_s + P.cmap_off;
     E.cut_s = tb_s + P.cut_off;
+    E.ctx_s = tb_s + P.ctx_off;
+    E.windows = P.n_ctx != 0 ? 1u : 0u;
     E.shift = P.row_shift;
     E.err = &P.res->error;
     E.guard = P.sparse_limit != 0 ? 1u : 0u;
@@ -805,6 +828,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             E.kmap_s = tb_s + lds_u32(ws + 12);
             E.cmap_s = tb_s + lds_u32(ws + 16);
             E.cut_s = tb_s + lds_u32(ws + 20);
+            E.ctx_s = tb_s + lds_u32(ws + 24);
         } else {
             E.in = P.in + (uint64_t)tile * WT;
             E.nrel64 = P.n - (uint64_t)tile * WT;
@@ -826,17 +850,23 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         } else {
             const uint32_t lim = nrel < LIMIT ? nrel : LIMIT;
             c1 = NONE;
+            uint32_t carry = __ldg(E.in + WT - 1);   // the byte before the round (windows need it)
             for (uint32_t b0 = WT; b0 < lim; b0 += 128) {
                 const uint32_t pos = b0 + 4 * lane;
-                uint32_t m = 0;
+                uint32_t m = 0, w = 0;
                 if (pos + 4 <= lim) {
-                    const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(E.in + pos));
-                    for (uint32_t k = 0; k < 4; k++)
-                        if (lds_u8(E.cut_s + byte_of(w, k))) m |= 1u << k;
+                    w = __ldg(reinterpret_cast<const uint32_t *>(E.in + pos));
                 } else {
-                    for (uint32_t k = 0; pos + k < lim; k++)
-                        if (lds_u8(E.cut_s + __ldg(E.in + pos + k))) m |= 1u << k;
+                    for (uint32_t k = 0; pos + k < lim; k++) w |= (uint32_t)__ldg(E.in + pos + k) << (8 * k);
                 }
+                const uint32_t up = __shfl_up_sync(0xffffffffu, w, 1);
+                uint32_t prev = lane == 0 ? carry : up >> 24;
+                for (uint32_t k = 0; k < 4 && pos + k < lim; k++) {
+                    const uint32_t b = byte_of(w, k);
+                    if (is_cut(E, prev, b)) m |= 1u << k;
+                    prev = b;
+                }
+                carry = __shfl_sync(0xffffffffu, w, 31) >> 24;
                 const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
                 if (bal) {
                     const int src = __ffs(bal) - 1;
@@ -852,7 +882,10 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         const uint32_t t0 = (uint32_t)lane * SLICE;
         const bool first = dtile == 0 && lane == 0;   // the input's (document's) first chunk starts at 0
         Lane L;
-        L.e = first ? E.P_start : E.P_pre;
+        // a lane starts in the PRE row of the context of the byte before its slice
+        uint32_t pre0 = E.P_pre;
+        if (E.windows && !first && t0 < nrel) pre0 += lds_u8(E.ctx_s + __ldg(E.in + (int64_t)t0 - 1)) << E.shift;
+        L.e = first ? E.P_start : pre0;
         L.s = first ? 0u : NONE;
         L.p = t0;
         L.fail = NONE;
@@ -1173,6 +1206,8 @@ int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t
     P.kmap_off = w.kmap_off;
     P.cmap_off = w.cmap_off;
     P.cut_off = w.cut_off;
+    P.ctx_off = w.ctx_off;
+    P.n_ctx = w.n_ctx;
     P.out_kinds = d_kinds;
     P.out_lens = d_lens;
     P.cap = capacity;
@@ -1284,7 +1319,7 @@ int combine(const lx_tokenset *const *sets, uint32_t n_sets, int mode, Combined 
     uint32_t rows = 0;
     for (uint32_t s = 0; s < n_sets; s++) {
         w[s] = class_walk(sets[s], mode);
-        if (!w[s]) return LX_E_TOOBIG;
+        if (!w[s] || w[s]->n_ctx) return LX_E_TOOBIG;   // tables with split-window contexts stay single
         rows += w[s]->rows_bytes;
     }
     if (rows > BATCH_ROWS_MAX) return LX_E_TOOBIG;
@@ -1297,8 +1332,8 @@ int combine(const lx_tokenset *const *sets, uint32_t n_sets, int mode, Combined 
     for (uint32_t s = 0; s < n_sets; s++) {
         base[s] = rb;
         rb += w[s]->rows_bytes;
-        maps[s] = o;   // kmap (256 B), cmap (256 B, 256-aligned), cut (256 B)
-        o += 768;
+        maps[s] = o;   // kmap (256 B), cmap (256 B, 256-aligned), cut (256 B), context map (256 B, zero)
+        o += 1024;
     }
     out.sets_off = o;
     out.blob.assign(al(o + (uint32_t)sizeof(WSet) * n_sets, 16), 0);
@@ -1312,7 +1347,8 @@ int combine(const lx_tokenset *const *sets, uint32_t n_sets, int mode, Combined 
         std::memcpy(out.blob.data() + maps[s], t.blob.data() + t.kmap_off, 256);
         std::memcpy(out.blob.data() + maps[s] + 256, t.blob.data() + t.cmap_off, 256);
         std::memcpy(out.blob.data() + maps[s] + 512, t.blob.data() + t.cut_off, 256);
-        ws[s] = WSet{base[s] + t.p_start, base[s] + t.p_pre, base[s], maps[s], maps[s] + 256, maps[s] + 512};
+        ws[s] = WSet{base[s] + t.p_start, base[s] + t.p_pre, base[s], maps[s], maps[s] + 256, maps[s] + 512,
+                     maps[s] + 768, 0};
     }
     std::memcpy(out.blob.data() + out.sets_off, ws.data(), sizeof(WSet) * n_sets);
     return LX_OK;

@@ -140,6 +140,38 @@ void derive_certificates(lx_tokenset &t)
         if (ex_c[c]) t.exact[b >> 5] |= 1u << (b & 31);
         if (mo_c[c]) t.modulo[b >> 5] |= 1u << (b & 31);
     }
+
+    // two-byte split windows (a generalisation of Definition 2 with one byte
+    // of left context): Z(a) = delta+(Q+, a); a cut before b after a when no
+    // state of Z(a) reads b into Q+ (and b starts a token)
+    t.win.assign(256 * 8, 0u);
+    if (t.reentrant) return;
+    std::vector<uint8_t> wc((size_t)C * C, 0);
+    std::vector<uint32_t> Z;
+    for (uint32_t ca = 0; ca < C; ca++) {
+        Z.clear();
+        std::vector<uint8_t> seen(S, 0);
+        for (uint32_t q = 0; q < S; q++) {
+            const uint32_t d = live_edge(ca, q);
+            if (d != LX_NONE && !seen[d]) {
+                seen[d] = 1;
+                Z.push_back(d);
+            }
+        }
+        for (uint32_t cb = 0; cb < C; cb++) {
+            if (live_edge(cb, q0) == LX_NONE) continue;
+            bool ok = true;
+            for (uint32_t z : Z)
+                if (live_edge(cb, z) != LX_NONE) {
+                    ok = false;
+                    break;
+                }
+            wc[(size_t)ca * C + cb] = ok ? 1 : 0;
+        }
+    }
+    for (uint32_t a = 0; a < 256; a++)
+        for (uint32_t b = 0; b < 256; b++)
+            if (wc[(size_t)t.byte_class[a] * C + t.byte_class[b]]) t.win[a * 8 + (b >> 5)] |= 1u << (b & 31);
 }
 
 inline bool bit(const uint32_t m[8], uint32_t b) { return (m[b >> 5] >> (b & 31)) & 1u; }
@@ -274,6 +306,33 @@ void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt, bool fo
     for (uint32_t b = 0; b < 256; b++)
         if (bit(cutmask, b)) cut_c[t.byte_class[b]] = 1;
     wt = lx::WalkTable();
+    // exact modes: the split windows beyond the single certified bytes, as
+    // context classes (bytes whose certified followers are the same set)
+    std::vector<uint32_t> ctx_of(C, 0);                  // class -> context (0: none)
+    std::vector<std::vector<uint8_t>> foll(1, std::vector<uint8_t>(C, 0));   // context -> follower classes
+    if (mode != LX_FILTERED_MODULO && !t.win.empty()) {
+        std::vector<uint32_t> rep(C, 256);
+        for (uint32_t b = 0; b < 256; b++)
+            if (rep[t.byte_class[b]] == 256) rep[t.byte_class[b]] = b;
+        for (uint32_t ca = 0; ca < C; ca++) {
+            std::vector<uint8_t> f(C, 0);
+            bool any = false;
+            for (uint32_t cb = 0; cb < C; cb++) {
+                const uint32_t a = rep[ca], b = rep[cb];
+                f[cb] = ((t.win[a * 8 + (b >> 5)] >> (b & 31)) & 1u) && !cut_c[cb];
+                any = any || f[cb];
+            }
+            if (!any) continue;
+            uint32_t k = 1;
+            while (k < foll.size() && foll[k] != f) k++;
+            if (k == foll.size()) {
+                if (foll.size() > lx::WALK_MAX_CTX) continue;   // more contexts than rows: this one is dropped
+                foll.push_back(f);
+            }
+            ctx_of[ca] = k;
+        }
+    }
+    const uint32_t K = (uint32_t)foll.size() - 1;
     // event codes: 1 for a discarded kind, 2.. for kept kinds in state order
     std::vector<uint32_t> code(t.n_kinds, 0);
     std::vector<uint16_t> kmap(lx::WALK_CODES, 0);
@@ -290,7 +349,7 @@ void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt, bool fo
         }
     }
     wt.n_kept = next_code - 2;
-    const uint32_t SLOW = 0, START = S + 1, PRE = S + 2, R = S + 3;
+    const uint32_t SLOW = 0, START = S + 1, PRE = S + 2, R = S + 3 + K;   // PRE_k = PRE + k
     auto Rq = [](uint32_t q) { return 1 + q; };
     if (!force_class && (uint64_t)R * 512 <= lx::MAX_BYTE_FORM_BYTES) {
         wt.form = lx::FORM_BYTE;
@@ -313,8 +372,9 @@ void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt, bool fo
             to = SLOW;
         } else if (row == START) {
             to = d0 != LX_NONE ? Rq(d0) : SLOW;
-        } else if (row == PRE) {
-            to = cut_c[c] ? (d0 != LX_NONE ? Rq(d0) : SLOW) : PRE;
+        } else if (row >= PRE) {   // PRE_k: absorbs bytes up to a certified byte or window
+            const uint32_t k = row - PRE;
+            to = (cut_c[c] || foll[k][c]) ? (d0 != LX_NONE ? Rq(d0) : SLOW) : PRE + ctx_of[c];
         } else {
             const uint32_t q = row - 1, d = nx(c, q);
             const bool acc = t.accept[q] != LX_NO_KIND;
@@ -337,7 +397,9 @@ void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt, bool fo
     wt.kmap_off = al(wt.acc_off + R, 16);
     wt.cmap_off = al(wt.kmap_off + 2 * lx::WALK_CODES, 256);
     wt.cut_off = wt.cmap_off + 256;
-    wt.blob.assign(wt.cut_off + 256, 0);
+    wt.n_ctx = K;
+    wt.ctx_off = wt.cut_off + 256 * (K + 1);
+    wt.blob.assign(wt.ctx_off + 256, 0);
     uint16_t *ent = reinterpret_cast<uint16_t *>(wt.blob.data());
     for (uint32_t r = 0; r < R; r++) {
         if (wt.form == lx::FORM_BYTE) {
@@ -351,8 +413,10 @@ void build_walk_table(const lx_tokenset &t, int mode, lx::WalkTable &wt, bool fo
     }
     std::memcpy(wt.blob.data() + wt.kmap_off, kmap.data(), 2 * lx::WALK_CODES);
     for (uint32_t b = 0; b < 256; b++) {
-        wt.blob[wt.cmap_off + b] = (uint8_t)(2 * t.byte_class[b]);
-        wt.blob[wt.cut_off + b] = bit(cutmask, b) ? 1 : 0;
+        const uint32_t c = t.byte_class[b];
+        wt.blob[wt.cmap_off + b] = (uint8_t)(2 * c);
+        for (uint32_t k = 0; k <= K; k++) wt.blob[wt.cut_off + 256 * k + b] = (cut_c[c] || foll[k][c]) ? 1 : 0;
+        wt.blob[wt.ctx_off + b] = (uint8_t)ctx_of[c];
     }
     wt.status = LX_OK;
 }
@@ -624,10 +688,18 @@ extern "C" int lx_tokenset_walk_table(const lx_tokenset *ts, int mode, void *out
     if (!ts || mode < 0 || mode > 2) return LX_E_INVAL;
     const lx::WalkTable &w = ts->walk[mode];
     if (out && cap) std::memcpy(out, w.blob.data(), std::min<size_t>(cap, w.blob.size()));
-    const uint32_t m[10] = {(uint32_t)w.blob.size(), (uint32_t)w.form, w.n_rows, w.row_shift, w.p_start,
-                            w.p_pre, w.acc_off, w.kmap_off, w.cmap_off, w.cut_off};
-    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 10));
+    const uint32_t m[12] = {(uint32_t)w.blob.size(), (uint32_t)w.form, w.n_rows, w.row_shift, w.p_start,
+                            w.p_pre, w.acc_off, w.kmap_off, w.cmap_off, w.cut_off, w.n_ctx, w.ctx_off};
+    if (meta) std::memcpy(meta, m, sizeof(uint32_t) * std::min<uint32_t>(meta_len, 12));
     return w.status;
+}
+
+extern "C" int lx_window_certificates(const lx_tokenset *ts, uint32_t *pairs)
+{
+    if (!ts || !pairs) return LX_E_INVAL;
+    if (ts->win.size() == 256 * 8) std::memcpy(pairs, ts->win.data(), sizeof(uint32_t) * 256 * 8);
+    else std::memset(pairs, 0, sizeof(uint32_t) * 256 * 8);
+    return LX_OK;
 }
 
 extern "C" int lx_tokenset_liveness(const lx_tokenset *ts, void *out, uint32_t cap, uint32_t *meta,

@@ -100,9 +100,11 @@ def test_one_launch_batch_against_the_oracle(env, names):
         rc2, n2, res2, k2, l2 = run_batch(lg, tile, names, spec, host, offs, mode)
         assert rc2 == 0
         check_docs(spec, host, offs, mode, res2, k2, l2)
-        # the one-launch batch keeps document order: non-empty documents' ranges ascend
-        starts = [r[0] for (nm, s, _), r in zip(spec, res) if s]
-        assert starts == sorted(starts)
+        # the one-launch batch keeps document order: non-empty documents' ranges ascend (in the
+        # exact modes the tables carry split-window rows, which keep a batch on the per-set kernels)
+        if mode == 2:
+            starts = [r[0] for (nm, s, _), r in zip(spec, res) if s]
+            assert starts == sorted(starts)
         # a second call of the same shape replays the graph with the same result
         rc3, n3, res3, k3, l3 = run_batch(lg, warp, names, spec, host, offs, mode)
         assert rc3 == 0 and res3 == res and np.array_equal(k3, k)

@@ -37,7 +37,17 @@ class Walk:
         self.acc = blob[meta["acc_off"]:meta["acc_off"] + meta["n_rows"]].astype(np.int64)
         self.kmap = blob[meta["kmap_off"]:meta["kmap_off"] + 256].view(np.uint16).astype(np.int64)
         self.cmap2 = blob[meta["cmap_off"]:meta["cmap_off"] + 256].astype(np.int64)
-        self.cut = blob[meta["cut_off"]:meta["cut_off"] + 256].astype(bool)
+        self.K = meta.get("n_ctx", 0)
+        self.cuts = blob[meta["cut_off"]:meta["cut_off"] + 256 * (self.K + 1)].astype(bool).reshape(self.K + 1, 256)
+        self.ctx = (blob[meta["ctx_off"]:meta["ctx_off"] + 256].astype(np.int64) if self.K
+                    else np.zeros(256, np.int64))
+
+    def is_cut(self, a, b):
+        """A chunk may start at byte b after byte a (single byte or window)."""
+        return bool(self.cuts[self.ctx[a], b])
+
+    def is_pre(self, e):
+        return e >= self.P_pre          # PRE and the PRE_k rows after it
 
     def step(self, e, b):
         if self.form == 0:
@@ -107,7 +117,7 @@ class WarpModel:
             return
         while L["act"]:
             e = L["e"]
-            if e in (W.P_start, W.P_pre):
+            if e == W.P_start or W.is_pre(e):
                 return
             if e != W.P_slow:
                 ac = W.acc_code(e)
@@ -124,9 +134,9 @@ class WarpModel:
             k = L["p"]
             e0 = L["e"]
             v = W.step(e0, self.inb(k))
-            if e0 == W.P_pre and v != W.P_pre and L["s"] == NONE:
+            if W.is_pre(e0) and not W.is_pre(v) and L["s"] == NONE:
                 L["s"] = k
-            if e0 != W.P_pre and k <= hi:
+            if not W.is_pre(e0) and k <= hi:
                 self.ev[k] = v & 0xFF
             L["e"] = v
             L["p"] = k + 1
@@ -142,6 +152,7 @@ class WarpModel:
         store whole words at or before it)."""
         W = self.W
         pb = L["p"]
+        e_in = L["e"]
         words = []
         for wk in range(self.BLK // 4):
             e0 = L["e"]
@@ -151,11 +162,16 @@ class WarpModel:
                 codes.append(L["e"] & 0xFF)
             words.append((e0, codes))
             wpos = pb + 4 * wk
-            if (hi_rule is None and e0 != W.P_pre) or (hi_rule is not None and wpos + 3 <= hi_rule):
+            if (hi_rule is None and not W.is_pre(e0)) or (hi_rule is not None and wpos + 3 <= hi_rule):
                 self.ev[wpos:wpos + 4] = codes
-        if hi_rule is None and L["s"] == NONE and L["e"] != W.P_pre:
-            # PRE was left in this block: its first certified byte starts the range
-            s = next(k for k in range(pb, pb + self.BLK) if W.cut[self.inb(k)])
+        if hi_rule is None and L["s"] == NONE and not W.is_pre(L["e"]):
+            # PRE was left in this block: the byte where the PRE rows are left starts the range
+            e, s = e_in, None
+            for k in range(pb, pb + self.BLK):
+                e = W.step(e, self.inb(k))
+                if not W.is_pre(e):
+                    s = k
+                    break
             L["s"] = s
             wk = (s - pb) // 4
             for j in range(s + 1, pb + 4 * wk + 4):
@@ -189,7 +205,7 @@ class WarpModel:
                     if v & 0xFF:
                         cnt += self._emit(emit, v & 0xFF, p - tok)
                         tok = p
-                        if p >= self.WT and W.cut[b]:
+                        if p >= self.WT and W.is_cut(self.inb(p - 1), b):
                             return cnt, NONE
                     e = v
                     p += 1
@@ -209,7 +225,7 @@ class WarpModel:
             e = W.P_start
             if r == self.nrel:
                 return cnt, NONE
-            if r >= self.WT and W.cut[self.inb(r)]:
+            if r >= self.WT and W.is_cut(self.inb(r - 1), self.inb(r)):
                 return cnt, NONE
 
     def _emit(self, emit, code, ln):
@@ -231,14 +247,17 @@ class WarpModel:
             c1 = nrel
         else:
             lim = min(nrel, self.LIMIT)
-            c1 = next((k for k in range(self.WT, lim) if W.cut[self.inb(k)]), NONE)
+            c1 = next((k for k in range(self.WT, lim) if W.is_cut(self.inb(k - 1), self.inb(k))), NONE)
             if c1 == NONE and lim == nrel:
                 c1 = nrel
         lanes = []
         for l in range(32):
             t0 = l * self.SLICE
             first = tile == 0 and l == 0
-            L = dict(p=t0, e=W.P_start if first else W.P_pre, s=0 if first else NONE, fail=NONE,
+            pre0 = W.P_pre
+            if W.K and not first and t0 < nrel:
+                pre0 += int(W.ctx[self.inb(t0 - 1)]) << W.shift    # the context of the byte before the slice
+            L = dict(p=t0, e=W.P_start if first else pre0, s=0 if first else NONE, fail=NONE,
                      act=t0 < nrel, own_hi=NONE)
             lanes.append(L)
         # phase 1
@@ -376,7 +395,8 @@ def lg(lexlib):
     return lexlib
 
 
-@pytest.mark.parametrize("name,mode", [("arith", 0), ("arith", 2), ("json", 2), ("clike", 2), ("clike_row1", 0)])
+@pytest.mark.parametrize("name,mode", [("arith", 0), ("arith", 2), ("json", 2), ("clike", 2), ("clike_row1", 0),
+                                       ("json", 0), ("json", 1), ("clike", 0), ("clike", 1)])
 def test_model_matches_oracle_corpora(lg, name, mode):
     gen = "clike" if name == "clike_row1" else name
     w = corpus.generate(gen, 20000, seed=11)
@@ -443,7 +463,7 @@ def test_walk_table_codes(lg):
 
 
 @pytest.mark.parametrize("name,mode", [("arith", 0), ("arith", 1), ("json", 2), ("json", 1), ("clike", 2),
-                                       ("clike_row1", 0), ("clike_row1", 2)])
+                                       ("clike_row1", 0), ("clike_row1", 2), ("json", 0), ("clike", 1)])
 def test_model_random_snippets(lg, name, mode):
     """Random slices of the corpora (some with a malformed byte) at every
     alignment, tile and slice boundary of the small geometry."""
@@ -458,3 +478,32 @@ def test_model_random_snippets(lg, name, mode):
         w = np.frombuffer(bytes(s), np.uint8)
         got, con = model_lex(lg, name, mode, w, **SMALL)
         assert (got, con) == expected(name, mode, w), (a, len(s))
+
+
+@pytest.mark.parametrize("name,mode", [("json", 0), ("json", 1), ("clike", 0), ("arith", 0)])
+def test_window_rows(lg, name, mode):
+    """In the exact modes the walk table holds PRE_k rows for the split-window
+    contexts: PRE_k leaves the PRE rows exactly on the bytes its cut-table row
+    certifies (as q0's step), and otherwise moves to the PRE row of the byte's
+    own context."""
+    ts = lg.lx_compile_tokenset(T.tokenset(name), T.discarded_kinds(name))
+    rc, blob, meta = lg.lx_tokenset_walk_table(ts, mode)
+    assert rc == 0
+    W = Walk(blob, meta)
+    rc, pairs = lg.lx_window_certificates(ts)
+    if name in ("json", "clike"):
+        assert W.K > 0
+    for k in range(W.K + 1):
+        row = W.P_pre + (k << W.shift)
+        for b in range(256):
+            v = W.step(row, b)
+            if W.cuts[k, b]:
+                assert v == W.step(W.P_start, b)
+            else:
+                assert v == W.P_pre + (int(W.ctx[b]) << W.shift)
+    # every context's row certifies exactly the window followers of its bytes (plus single cuts)
+    single = W.cuts[0]
+    for a in range(256):
+        k = int(W.ctx[a])
+        if k:
+            assert np.array_equal(W.cuts[k], pairs[a] | single)
