@@ -284,9 +284,9 @@ struct WriteTok {
 // past p1, so the context at p1 is its state.  Every token then costs its own
 // length plus one step.  Unguarded, a lane that takes more than STEP_BUDGET
 // steps gives up and flags EN_ERR_LOOKAHEAD; the caller runs again guarded.
-template <class Emit>
-__device__ uint16_t chunk_scan(const ScanEnv &E, bool has, uint64_t p0, uint64_t p1, uint16_t ctx, Emit &emit,
-                               uint64_t &fail)
+template <bool GUARDED, class Emit>
+__device__ __forceinline__ uint16_t chunk_scan_t(const ScanEnv &E, bool has, uint64_t p0, uint64_t p1, uint16_t ctx,
+                                                 Emit &emit, uint64_t &fail)
 {
     fail = NOPOS64;
     Bytes by{E.in, E.n, (reinterpret_cast<uintptr_t>(E.in) & 15u) == 0};
@@ -296,26 +296,24 @@ __device__ uint16_t chunk_scan(const ScanEnv &E, bool has, uint64_t p0, uint64_t
     uint64_t tok = p0, j = p0, last = NOPOS64;
     uint32_t qs = entered ? ctx : E.q0, q = qs, lq = 0, qp1 = qs, steps = 0;
     bool first = entered;
-    const bool guarded = E.live != nullptr;
     while (__any_sync(0xffffffffu, run)) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             if (!run) break;
             uint32_t t = j < E.n ? delta(E, q, by(j)) : (uint32_t)SCAN_NONE;
-            if (guarded) {
+            if (GUARDED) {
                 if (!lv_has(E, q, j)) {
                     t = SCAN_NONE;   // no accepting position ahead: the run ends here
                 } else if (first && j == p1) {
                     res = (uint16_t)q;   // the entered token runs past p1
                     run = false;
-                    break;
+                    continue;
                 }
-            } else if (++steps > E.budget) {
+            } else if (++steps > E.budget) {   // past the budget: give up, the caller reruns guarded
                 atomicOr(E.error, EN_ERR_LOOKAHEAD);
                 res = CTX_BAD;
-                fail = NOPOS64;
                 run = false;
-                break;
+                continue;
             }
             if (t != SCAN_NONE) {
                 q = t & ~(uint32_t)SCAN_ACCEPT;
@@ -346,7 +344,18 @@ __device__ uint16_t chunk_scan(const ScanEnv &E, bool has, uint64_t p0, uint64_t
             }
         }
     }
+    if (!GUARDED && steps > E.budget) fail = NOPOS64;
     return res;
+}
+
+// The unguarded scan (with its step budget) or, once the liveness prepass
+// has run, the guarded one; the choice is uniform over the launch.
+template <class Emit>
+__device__ __forceinline__ uint16_t chunk_scan(const ScanEnv &E, bool has, uint64_t p0, uint64_t p1, uint16_t ctx,
+                                               Emit &emit, uint64_t &fail)
+{
+    if (E.live) return chunk_scan_t<true>(E, has, p0, p1, ctx, emit, fail);
+    return chunk_scan_t<false>(E, has, p0, p1, ctx, emit, fail);
 }
 
 __device__ __forceinline__ uint32_t n_cand(const ScanEnv &E, uint32_t b)

@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         } else {
             const uint32_t lim = nrel < LIMIT ? nrel : LIMIT;
             c1 = NONE;
-            uint32_t carry = __ldg(E.in + WT - 1);   // the byte before the round (windows need it)
+            uint32_t carry = E.windows ? __ldg(E.in + WT - 1) : 0u;   // the byte before the round (windows)
             for (uint32_t b0 = WT; b0 < lim; b0 += 128) {
                 const uint32_t pos = b0 + 4 * lane;
                 uint32_t m = 0, w = 0;
@@ -859,14 +859,19 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
                 } else {
                     for (uint32_t k = 0; pos + k < lim; k++) w |= (uint32_t)__ldg(E.in + pos + k) << (8 * k);
                 }
-                const uint32_t up = __shfl_up_sync(0xffffffffu, w, 1);
-                uint32_t prev = lane == 0 ? carry : up >> 24;
-                for (uint32_t k = 0; k < 4 && pos + k < lim; k++) {
-                    const uint32_t b = byte_of(w, k);
-                    if (is_cut(E, prev, b)) m |= 1u << k;
-                    prev = b;
+                if (E.windows) {   // each byte with the byte before it
+                    const uint32_t up = __shfl_up_sync(0xffffffffu, w, 1);
+                    uint32_t prev = lane == 0 ? carry : up >> 24;
+                    for (uint32_t k = 0; k < 4 && pos + k < lim; k++) {
+                        const uint32_t b = byte_of(w, k);
+                        if (is_cut(E, prev, b)) m |= 1u << k;
+                        prev = b;
+                    }
+                    carry = __shfl_sync(0xffffffffu, w, 31) >> 24;
+                } else {           // single certified bytes: the cut table's first row
+                    for (uint32_t k = 0; k < 4 && pos + k < lim; k++)
+                        if (lds_u8(E.cut_s + byte_of(w, k))) m |= 1u << k;
                 }
-                carry = __shfl_sync(0xffffffffu, w, 31) >> 24;
                 const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
                 if (bal) {
                     const int src = __ffs(bal) - 1;
