@@ -48,6 +48,9 @@ namespace lx {
 namespace {
 
 constexpr uint32_t WT = 4096;                 // input bytes per warp tile
+// The kernels' FORM template argument: bit 0 the table's lookup form
+// (FORM_BYTE / FORM_CLASS), bit 1 (WIN) split-window rows (exact modes).
+constexpr int WIN = 2;
 constexpr uint32_t SLICE = WT / 32;           // bytes per lane slice (phase 1)
 constexpr uint32_t BLK = 16;                  // bytes per lockstep step of a lane
 constexpr uint32_t NB1 = SLICE / BLK;         // phase-1 steps
@@ -132,7 +135,6 @@ struct WEnv {
     uint32_t P_start, P_pre, P_slow;
     uint32_t tb_s, acc_s, kmap_s, cmap_s, cut_s, ctx_s, shift;   // P_pre: the first PRE row (PRE_k follow)
     uint32_t ev;                 // event buffer: code of position p at ev + p
-    uint32_t windows;            // the table has split-window contexts (PRE_k rows)
     unsigned int *err;           // the result record's error word
     uint32_t guard;              // 1: backtracking past its step budget stops the call (ERR_LOOKAHEAD)
     const uint8_t *in;           // the tile's first byte
@@ -151,7 +153,7 @@ __device__ __forceinline__ uint4 ldg16(const uint8_t *p)
 template <int FORM>
 __device__ __forceinline__ uint32_t wstep(const WEnv &E, uint32_t e, uint32_t b)
 {
-    const uint32_t a = FORM == FORM_BYTE ? ((e & ~0x1FEu) | (b << 1)) : ((e & ~0xFFu) | lds_u8(E.cmap_s + b));
+    const uint32_t a = (FORM & 1) == FORM_BYTE ? ((e & ~0x1FEu) | (b << 1)) : ((e & ~0xFFu) | lds_u8(E.cmap_s + b));
     return lds_u16(a);
 }
 
@@ -205,11 +207,11 @@ template <int FORM, int PH>
 __device__ __forceinline__ uint32_t wword(uint32_t &e, uint32_t w, uint32_t ev, uint32_t x, uint32_t y, uint32_t cm)
 {
     uint32_t pk;
-    const uint32_t mask = FORM == FORM_BYTE ? 0x1FEu : 0xFFu;   // the address bits an entry's byte or class replaces
-    if (FORM == FORM_BYTE && PH == 1)
+    const uint32_t mask = (FORM & 1) == FORM_BYTE ? 0x1FEu : 0xFFu;   // the address bits an entry's byte or class replaces
+    if ((FORM & 1) == FORM_BYTE && PH == 1)
         asm volatile(LXW_HEAD LXW_PRED1 LXW_BYTE_BODY LXW_PACK
                      : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm), "r"(mask) : "memory");
-    else if (FORM == FORM_BYTE)
+    else if ((FORM & 1) == FORM_BYTE)
         asm volatile(LXW_HEAD LXW_PRED2 LXW_BYTE_BODY LXW_PACK
                      : "+r"(e), "=r"(pk) : "r"(w), "r"(x), "r"(y), "r"(ev), "r"(cm), "r"(mask) : "memory");
     else if (PH == 1)
@@ -254,12 +256,20 @@ __device__ void refine_start(const WEnv &E, Lane &L)
     L.coarse = false;
     const uint32_t pb = L.s;
     const uint4 c = L.blk;
-    // replay the PRE rows over the block: the byte where they are left
     uint32_t j = 0, e = L.pe;
-    for (; j < BLK; j++) {
-        const uint32_t v = wstep<FORM>(E, e, byte_of(pick4(j >> 2, c.x, c.y, c.z, c.w), j & 3u));
-        e = v;
-        if (v < E.P_pre) break;
+    if (FORM & WIN) {   // replay the PRE rows over the block: the byte where they are left
+        for (; j < BLK; j++) {
+            const uint32_t v = wstep<FORM>(E, e, byte_of(pick4(j >> 2, c.x, c.y, c.z, c.w), j & 3u));
+            e = v;
+            if (v < E.P_pre) break;
+        }
+    } else {            // the first certified byte: PRE's step on it as q0's
+        uint32_t b = 0;
+        for (; j < BLK; j++) {
+            b = byte_of(pick4(j >> 2, c.x, c.y, c.z, c.w), j & 3u);
+            if (lds_u8(E.cut_s + b)) break;
+        }
+        e = wstep<FORM>(E, E.P_start, b);
     }
     if (j == BLK) j = BLK - 1;   // unreachable: the block leaves PRE
     L.s = pb + j;
@@ -446,7 +456,8 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
                 if (v & 0xFFu) {
                     emit(v & 0xFFu, p - tok);
                     tok = p;
-                    if (p >= WT && is_cut(E, rd.at(p - 1), b)) return cnt;
+                    if (p >= WT && ((FORM & WIN) ? is_cut(E, rd.at(p - 1), b) : lds_u8(E.cut_s + b) != 0))
+                        return cnt;
                 }
                 e = v;
                 p++;
@@ -480,7 +491,8 @@ __device__ uint64_t generic_chunk(const WEnv &E, uint64_t start, uint64_t *fail,
         tok = p = r;
         e = E.P_start;
         if (r == n) return cnt;
-        if (r >= WT && is_cut(E, rd.at(r - 1), rd.at(r))) return cnt;
+        if (r >= WT && ((FORM & WIN) ? is_cut(E, rd.at(r - 1), rd.at(r)) : lds_u8(E.cut_s + rd.at(r)) != 0))
+            return cnt;
     }
 }
 
@@ -722,7 +734,7 @@ __device__ __forceinline__ void phase1_step(const WEnv &E, Lane &L, const uint4 
             L.s = pb;
             L.coarse = true;
             L.blk = cur;
-            L.pe = e_in;
+            if (FORM & WIN) L.pe = e_in;
         }
         L.p = pb + BLK;
         if (L.e == E.P_slow) slow_fix<FORM>(E, L, L.p, BIG);
@@ -794,7 +806,6 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
     E.cmap_s = tb_s + P.cmap_off;
     E.cut_s = tb_s + P.cut_off;
     E.ctx_s = tb_s + P.ctx_off;
-    E.windows = P.n_ctx != 0 ? 1u : 0u;
     E.shift = P.row_shift;
     E.err = &P.res->error;
     E.guard = P.sparse_limit != 0 ? 1u : 0u;
@@ -850,7 +861,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         } else {
             const uint32_t lim = nrel < LIMIT ? nrel : LIMIT;
             c1 = NONE;
-            uint32_t carry = E.windows ? __ldg(E.in + WT - 1) : 0u;   // the byte before the round (windows)
+            uint32_t carry = (FORM & WIN) ? __ldg(E.in + WT - 1) : 0u;   // the byte before the round (windows)
             for (uint32_t b0 = WT; b0 < lim; b0 += 128) {
                 const uint32_t pos = b0 + 4 * lane;
                 uint32_t m = 0, w = 0;
@@ -859,7 +870,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
                 } else {
                     for (uint32_t k = 0; pos + k < lim; k++) w |= (uint32_t)__ldg(E.in + pos + k) << (8 * k);
                 }
-                if (E.windows) {   // each byte with the byte before it
+                if (FORM & WIN) {   // each byte with the byte before it
                     const uint32_t up = __shfl_up_sync(0xffffffffu, w, 1);
                     uint32_t prev = lane == 0 ? carry : up >> 24;
                     for (uint32_t k = 0; k < 4 && pos + k < lim; k++) {
@@ -889,7 +900,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         Lane L;
         // a lane starts in the PRE row of the context of the byte before its slice
         uint32_t pre0 = E.P_pre;
-        if (E.windows && !first && t0 < nrel) pre0 += lds_u8(E.ctx_s + __ldg(E.in + (int64_t)t0 - 1)) << E.shift;
+        if ((FORM & WIN) && !first && t0 < nrel) pre0 += lds_u8(E.ctx_s + __ldg(E.in + (int64_t)t0 - 1)) << E.shift;
         L.e = first ? E.P_start : pre0;
         L.s = first ? 0u : NONE;
         L.p = t0;
@@ -1106,7 +1117,9 @@ int warp_occupancy(lx_ctx *c, int form, bool batch, uint32_t threads, uint32_t s
     int o = 0, rc;
     if (batch) rc = occupancy_of<FORM_CLASS, true>(threads, smem, &o);
     else if (form == FORM_BYTE) rc = occupancy_of<FORM_BYTE, false>(threads, smem, &o);
-    else rc = occupancy_of<FORM_CLASS, false>(threads, smem, &o);
+    else if (form == FORM_CLASS) rc = occupancy_of<FORM_CLASS, false>(threads, smem, &o);
+    else if (form == (FORM_BYTE | WIN)) rc = occupancy_of<FORM_BYTE | WIN, false>(threads, smem, &o);
+    else rc = occupancy_of<FORM_CLASS | WIN, false>(threads, smem, &o);
     if (rc != LX_OK) return rc;
     if (o < 1) return LX_E_TOOBIG;
     c->occupancy.emplace_back(key, o);
@@ -1185,9 +1198,9 @@ int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t
     const uint32_t n_tiles = (uint32_t)n_tiles64;
     L.nwarps = warps_for(warps_setting(c, ts, mode), (uint32_t)w.blob.size(), &L.smem);
     if (L.nwarps < 1) return LX_E_TOOBIG;
-    L.form = w.form;
+    L.form = w.form | (w.n_ctx ? WIN : 0);
     int occ = 0;
-    rc = warp_occupancy(c, w.form, false, 32 * L.nwarps, L.smem, &occ);
+    rc = warp_occupancy(c, L.form, false, 32 * L.nwarps, L.smem, &occ);
     if (rc != LX_OK) return rc;
     L.grid = (uint32_t)std::min<uint64_t>((uint64_t)occ * c->num_sms, (n_tiles + L.nwarps - 1) / L.nwarps);
 
@@ -1231,8 +1244,12 @@ int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t
 
 void warp_launch(const WarpLaunch &L, cudaStream_t st)
 {
-    if (L.form == FORM_BYTE) lex_warps<FORM_BYTE, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P);
-    else lex_warps<FORM_CLASS, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P);
+    switch (L.form) {
+    case FORM_BYTE: lex_warps<FORM_BYTE, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
+    case FORM_CLASS: lex_warps<FORM_CLASS, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
+    case FORM_BYTE | WIN: lex_warps<FORM_BYTE | WIN, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
+    default: lex_warps<FORM_CLASS | WIN, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
+    }
 }
 
 }  // namespace
