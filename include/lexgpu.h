@@ -250,7 +250,7 @@ int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
 
 /*
  * lx_ctx_set_kernel -- which kernel lx_lex uses on this context.
- *   LX_KERNEL_AUTO (default): the warp-tile kernel (every warp owns 4096-byte
+ *   LX_KERNEL_AUTO (default): the warp-tile kernel (every warp owns 6144-byte
  *     tiles, event codes in the walk table) when the token set has an
  *     event-code walk table for the mode (lx_tokenset_walk_table) and d_in is
  *     16-byte aligned; the tile kernel (CTAs of 256 threads over 17408-byte
@@ -270,7 +270,7 @@ int lx_ctx_set_kernel(lx_ctx *ctx, int kernel);
 /*
  * lx_ctx_set_warps -- warps per CTA of the warp-tile kernel on this context
  * (1..20; 0 = as many as the shared-memory budget holds next to the table,
- * the default).  Each warp owns one 4096-byte tile at a time, so the setting
+ * the default).  Each warp owns one 6144-byte tile at a time, so the setting
  * trades resident warps (latency hiding) against L1 left beside shared
  * memory.  Same tokens either way; lx_autotune chooses it.  LX_E_INVAL for a
  * value above 20.

@@ -2,7 +2,7 @@
 // the default kernel of lx_lex for token sets with an event-code walk table
 // (internal.h) and 16-byte aligned inputs.
 //
-// Every warp claims tiles of WT input bytes from a global counter and owns
+// Every warp claims tiles of WT (6144) input bytes from a global counter and owns
 // them end to end; nothing but the one-time table staging synchronises the
 // CTA.  Per tile:
 //   (a) halo scan: the 32 lanes find the first certified byte at or past the
@@ -47,7 +47,7 @@
 namespace lx {
 namespace {
 
-constexpr uint32_t WT = 4096;                 // input bytes per warp tile
+constexpr uint32_t WT = 6144;                 // input bytes per warp tile (6 KiB: measured best of 2-8 KiB)
 // The kernels' FORM template argument: bit 0 the table's lookup form
 // (FORM_BYTE / FORM_CLASS), bit 1 (WIN) split-window rows (exact modes).
 constexpr int WIN = 2;
@@ -61,7 +61,7 @@ constexpr uint32_t LIMIT = EVB - BLK;         // chunk ends must lie below (room
 // 128 positions, so the 32 lanes' phase-1 stores (slices 128 positions
 // apart) fall in 32 different banks.
 constexpr uint32_t EV_BYTES = ((EVB + 16 + 4 * ((EVB + 16) / 128 + 1)) + 15) / 16 * 16;
-constexpr uint32_t STAGE_CAP = 1024;          // kept tokens per tile staged for coalesced writes
+constexpr uint32_t STAGE_CAP = 1536;          // kept tokens per tile staged for coalesced writes
 constexpr uint32_t WAREA = EV_BYTES + 4 * STAGE_CAP;   // shared bytes per warp
 constexpr uint32_t GS = 64;                   // tiles per look-back group
 constexpr uint32_t NONE = 0xFFFFFFFFu;
@@ -948,7 +948,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         uint32_t hi = c1 != NONE ? c1 : long_s1 - 1;
         if (fail < hi) hi = fail;
         uint32_t wa = 0, wb = 0, last = 0, cnt = 0;
-        uint64_t wm = 0;   // words of this lane's slice holding a code (bit i: word wa + i)
+        uint32_t lastw = NONE;   // the last word of this lane's range holding a code
         if (c0 != NONE) {
             if (hi != c1) {   // a failure or a chunk past the halo: clear every code after hi
                 const uint32_t z0 = eva(E, hi) + 1, z1 = (z0 + 15u) & ~15u;
@@ -963,12 +963,10 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             for (uint32_t i = wa; i < wb; i++) {
                 const uint32_t w = lds_u32(eva(E, 4 * i));
                 cnt += __popc(kept_mask(w));
-                wm |= (uint64_t)(w != 0) << (i - wa);
+                if (w) lastw = i;
             }
-            if (wm) {   // the lane's last code
-                const uint32_t i = wa + 63 - __clzll(wm);
-                last = 4 * i + (31 - __clz(lds_u32(eva(E, 4 * i)))) / 8;
-            }
+            if (lastw != NONE)   // the lane's last code
+                last = 4 * lastw + (31 - __clz(lds_u32(eva(E, 4 * lastw)))) / 8;
         }
         uint32_t excl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
@@ -1032,16 +1030,14 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
                 }
             } else {
             // more kept codes than the stage holds: one code per lane and
-            // iteration, the next non-empty word taken from the word mask
-            uint32_t idx = excl, w = 0, nz = 0, wpos = 0;
-            uint64_t todo = wm;
+            // iteration, the next non-empty word of the lane's range
+            uint32_t idx = excl, w = 0, nz = 0, wpos = 0, nextw = wa;
             for (;;) {
-                if (nz == 0 && todo) {
-                    const uint32_t i = wa + __ffsll(todo) - 1;
-                    todo &= todo - 1;
-                    w = lds_u32(eva(E, 4 * i));
+                while (nz == 0 && nextw < wb) {
+                    w = lds_u32(eva(E, 4 * nextw));
                     nz = event_mask(w);
-                    wpos = 4 * i;
+                    wpos = 4 * nextw;
+                    nextw++;
                 }
                 if (!__any_sync(0xffffffffu, nz != 0)) break;
                 if (nz) {

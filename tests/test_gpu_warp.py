@@ -1,4 +1,4 @@
-"""The warp-tile kernel of lx_lex (every warp owns 4096-byte tiles, event
+"""The warp-tile kernel of lx_lex (every warp owns 6144-byte tiles, event
 codes in the walk table) against the oracle and against the tile kernel,
 element by element, through the C ABI.
 
@@ -20,7 +20,7 @@ from lexinputs import tokensets as T
 
 pytestmark = pytest.mark.gpu
 
-WT = 4096
+WT = 6144
 
 
 @pytest.fixture(scope="module")
@@ -91,7 +91,8 @@ SETS = [("arith", 0), ("arith", 1), ("arith", 2), ("json", 1), ("json", 2), ("cl
 def test_corpora_ragged(env, name, mode):
     gen = "clike" if name == "clike_row1" else name
     base = corpus.generate(gen, 3 << 20, seed=101)
-    for n in (1, 15, 16, 17, 127, 128, 129, 4095, 4096, 4097, 5119, 5120, 5121, 3 * WT + 77, 100_003, base.size):
+    for n in (1, 15, 16, 17, 127, 128, 129, 191, 192, 193, WT - 1, WT, WT + 1, WT + 511, WT + 512, WT + 513,
+              3 * WT + 77, 100_003, base.size):
         check(env, name, base[:n], mode, both=n == base.size)
 
 
@@ -130,7 +131,7 @@ def test_no_certified_byte(env):
 
 
 def test_dense_tokens_overflow_the_stage(env):
-    # one-byte tokens: over 1024 kept tokens per 4096-byte tile
+    # one-byte tokens: over 1536 kept tokens per 6144-byte tile
     rng = random.Random(9)
     line = lambda: bytes(rng.choice(b"+-*/%~!;,") for _ in range(rng.randint(30, 300))) + b"\n"
     w = b"".join(line() for _ in range(3000))

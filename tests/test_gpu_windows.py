@@ -17,7 +17,7 @@ from lexinputs import tokensets as T
 
 pytestmark = pytest.mark.gpu
 
-WT = 4096
+WT = 6144
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +82,7 @@ def test_window_cuts_ragged(env, name, mode):
     # the corpus really has window cuts, and no single certified byte
     assert not oracle.certificates(T.tokenset(name)).exact.any()
     assert len(W.window_cuts(T.tokenset(name), base[:20000])) > 100
-    for n in (1, 2, 127, 128, 129, 4095, 4096, 4097, 3 * WT + 77, 100_003, base.size):
+    for n in (1, 2, 191, 192, 193, WT - 1, WT, WT + 1, 3 * WT + 77, 100_003, base.size):
         check(env, name, base[:n], mode)
 
 

@@ -61,7 +61,7 @@ class Walk:
 
 
 class WarpModel:
-    def __init__(self, walk, wt=4096, halo=512, blk=16):
+    def __init__(self, walk, wt=6144, halo=512, blk=16):
         self.W = walk
         self.WT, self.SLICE, self.HALO, self.BLK = wt, wt // 32, halo, blk
         self.EVB = wt + halo
@@ -407,7 +407,7 @@ def test_model_matches_oracle_corpora(lg, name, mode):
 
 @pytest.mark.parametrize("name,mode", [("json", 2), ("clike", 2), ("arith", 0)])
 def test_model_full_geometry(lg, name, mode):
-    w = corpus.generate(name, 3 * 4096 + 999, seed=12)
+    w = corpus.generate(name, 3 * 6144 + 999, seed=12)
     got, con = model_lex(lg, name, mode, w)
     want, econ = expected(name, mode, w)
     assert con == econ and got == want
