@@ -492,7 +492,7 @@ int lx_model_train_step(lx_model *m, const uint16_t *d_windows, const uint16_t *
  * chunks whose entry changed, until the chain from offset 0 is consistent:
  * the result is exact whatever the predictions.  Same output and errors as
  * lx_lex_enumerative; LX_E_INVAL when the model does not score states + 1
- * contexts of this token set.  At most 4 fix-up rounds run (on the device,
+ * contexts of this token set.  At most 8 fix-up rounds run (on the device,
  * with one read-back after them); chunks still unsettled then are decided by
  * the enumerative scan of lx_lex_enumerative as the judge (every chunk from
  * every candidate context, chains resolved from BOUNDARY at offset 0), after

@@ -43,7 +43,8 @@ constexpr int EN_NT = 256;             // threads of the plan / enumerate / emit
 constexpr int RS_NT = 1024;            // threads of the resolve kernel
 constexpr int SO_NT = 1024;            // threads of the offset kernels (one chunk each)
 constexpr uint32_t R1 = 16;            // chunks per run of the resolve kernels
-constexpr uint32_t SPEC_ROUNDS = 4;    // speculative rounds before the enumerative judge
+constexpr uint32_t SPEC_ROUNDS = 8;    // speculative rounds before the enumerative judge (a round that
+                                       // rescans nothing costs two short launches; the judge a whole enumeration)
 constexpr uint32_t STEP_BUDGET = 32 * 4096;   // steps of one unguarded chunk scan before the guard is called for
 constexpr unsigned EN_ERR_STATE = 1u;  // the resolve step met an impossible chain (never on valid tables)
 constexpr unsigned EN_ERR_LOOKAHEAD = 2u;   // a scan ran past STEP_BUDGET
