@@ -1101,6 +1101,7 @@ extern "C" void lx_ctx_free(lx_ctx *c)
     if (c->e_dev) cudaFree(c->e_dev);
     if (c->lv_dev) cudaFree(c->lv_dev);
     if (c->wb_dev) cudaFree(c->wb_dev);
+    if (c->w_spill) cudaFree(c->w_spill);
     if (c->b_host) cudaFreeHost(c->b_host);
     if (c->d_in) cudaFree(c->d_in);
     if (c->h_scratch) cudaFreeHost(c->h_scratch);

@@ -63,6 +63,7 @@ constexpr uint32_t LIMIT = EVB - BLK;         // chunk ends must lie below (room
 constexpr uint32_t EV_BYTES = ((EVB + 16 + 4 * ((EVB + 16) / 128 + 1)) + 15) / 16 * 16;
 constexpr uint32_t STAGE_CAP = 1536;          // kept tokens per tile staged for coalesced writes
 constexpr uint32_t WAREA = EV_BYTES + 4 * STAGE_CAP;   // shared bytes per warp
+constexpr uint32_t SPILL_CAP = LIMIT - STAGE_CAP;     // kept tokens of a tile past the stage, at most
 constexpr uint32_t GS = 64;                   // tiles per look-back group
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t BIG = 0x7FFFFFFFu;
@@ -113,6 +114,7 @@ struct WParams {
     uint16_t *out_kinds;
     uint32_t *out_lens;
     uint64_t cap;
+    uint32_t *spill;               // SPILL_CAP stage entries per warp of the grid
     unsigned long long *status;    // per tile: ST_AGG | kept count
     unsigned long long *gstatus;   // per group of GS tiles: ST_AGG | group count, or ST_INCL | inclusive prefix
     unsigned int *gdone;           // per group: tiles that have published
@@ -667,7 +669,7 @@ __device__ bool resolve_tile(const WParams &P, uint32_t tile, uint64_t &G)
 // A tile whose tokens wait in the warp's stage for their output offset.
 struct Pending {
     uint32_t tile;      // NONE: nothing pending
-    uint32_t staged;    // tokens in the stage (all of the tile's kept tokens)
+    uint32_t staged;    // the tile's kept tokens (stage, then spill slot)
     uint64_t fail;      // failure offset within the tile, or NONE64
     uint64_t agg;
     uint32_t doc, dtile;   // batches: its document and its index there
@@ -694,14 +696,16 @@ __device__ void report_failure(const WParams &P, uint32_t tile, uint64_t fail, u
     }
 }
 
-// The staged tokens of a tile to the output from index G, coalesced; kmap_s:
-// the kind map of the tile's token set.
-__device__ void copy_stage(const WParams &P, uint32_t kmap_s, uint32_t stage, uint32_t staged, uint64_t G)
+// The staged tokens of a tile to the output from index G, coalesced: the
+// first STAGE_CAP from the shared stage, the rest from the warp's spill slot;
+// kmap_s: the kind map of the tile's token set.
+__device__ void copy_stage(const WParams &P, uint32_t kmap_s, uint32_t stage, const uint32_t *spill, uint32_t staged,
+                           uint64_t G)
 {
     for (uint32_t i = threadIdx.x & 31; i < staged; i += 32) {
         const uint64_t o = G + i;
         if (o < P.cap) {
-            const uint32_t v = lds_u32(stage + 4 * i);
+            const uint32_t v = i < STAGE_CAP ? lds_u32(stage + 4 * i) : spill[i - STAGE_CAP];
             P.out_kinds[o] = (uint16_t)lds_u16(kmap_s + (v >> 16));
             P.out_lens[o] = v & 0xFFFFu;
         }
@@ -812,6 +816,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
     const uint32_t warea = ((tb_s + P.blob_bytes + 15u) & ~15u) + (uint32_t)wid * WAREA;
     E.ev = warea;
     const uint32_t stage = warea + EV_BYTES;
+    uint32_t *const spill = P.spill + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * SPILL_CAP;
     for (uint32_t i = lane; i < EV_BYTES / 16; i += 32) zero16(E.ev + 16 * i);
     __syncthreads();
     const uint32_t ahead = gridDim.x * (blockDim.x / 32);   // tiles the other warps take meanwhile
@@ -999,15 +1004,16 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             uint64_t G = 0;
             if (!resolve_tile(P, pend.tile, G)) break;
             report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
-            copy_stage(P, pend.kmap_s, stage, pend.staged, G);
+            copy_stage(P, pend.kmap_s, stage, spill, pend.staged, G);
             pend.tile = NONE;
             __syncwarp();
         }
 
         // (e) emit: (kind, length) of every kept code, in order, into the stage
-        const bool defer = !do_long && fast_total <= STAGE_CAP;
+        // (past STAGE_CAP into the warp's spill slot)
+        const bool defer = !do_long;
         uint64_t G = 0;
-        if (!defer) {   // rare: tokens beyond the stage or a chunk past the halo are written at once
+        if (!defer) {   // rare: a chunk past the halo is written at once
             if (!resolve_tile(P, tile, G)) break;
             report_failure<BATCH>(P, tile, fpos, G, agg, doc, dtile);
         }
@@ -1019,45 +1025,33 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             }
             prev = __shfl_up_sync(0xffffffffu, prev, 1);
             if (lane == 0 || prev < c0) prev = c0;
-            if (fast_total <= STAGE_CAP) {
-                // every lane its words, four codes per word without branches;
-                // the words read are cleared for the next tile
-                uint32_t sa = stage + 4 * excl, d = 4 * wa - prev;
+            // every lane its words, four codes per word without branches;
+            // the words read are cleared for the next tile
+            uint32_t d = 4 * wa - prev;
+            if (excl + cnt <= STAGE_CAP) {
+                uint32_t sa = stage + 4 * excl;
                 for (uint32_t i = wa; i < wb; i++) {
                     const uint32_t a = eva(E, 4 * i);
                     emit_word(sa, d, lds_u32(a));
                     sts_u32(a, 0);
                 }
-            } else {
-            // more kept codes than the stage holds: one code per lane and
-            // iteration, the next non-empty word of the lane's range
-            uint32_t idx = excl, w = 0, nz = 0, wpos = 0, nextw = wa;
-            for (;;) {
-                while (nz == 0 && nextw < wb) {
-                    w = lds_u32(eva(E, 4 * nextw));
-                    nz = event_mask(w);
-                    wpos = 4 * nextw;
-                    nextw++;
-                }
-                if (!__any_sync(0xffffffffu, nz != 0)) break;
-                if (nz) {
-                    const uint32_t bit = __ffs(nz) - 1;   // 8k + 7
-                    nz &= nz - 1;
-                    const uint32_t code = (w >> (bit - 7)) & 0xFFu;
-                    const uint32_t pos = wpos + (bit >> 3);
-                    if (code >= 4) {
-                        if (idx < STAGE_CAP) {
-                            sts_u32(stage + 4 * idx, (code << 16) | (pos - prev));
-                        } else if (G + idx < P.cap) {
-                            P.out_kinds[G + idx] = (uint16_t)lds_u16(E.kmap_s + 2 * (code >> 1));
-                            P.out_lens[G + idx] = pos - prev;
+            } else {   // this lane's codes reach past the stage
+                uint32_t idx = excl;
+                for (uint32_t i = wa; i < wb; i++) {
+                    const uint32_t a = eva(E, 4 * i), w = lds_u32(a);
+#pragma unroll
+                    for (uint32_t k = 0; k < 4; k++) {
+                        const uint32_t code = (w >> (8 * k)) & 0xFFu;
+                        if (code > 3) {
+                            const uint32_t v = (code << 16) | d;
+                            if (idx < STAGE_CAP) sts_u32(stage + 4 * idx, v);
+                            else spill[idx - STAGE_CAP] = v;
+                            idx++;
                         }
-                        idx++;
+                        d = code ? 1u : d + 1;
                     }
-                    prev = pos;
+                    sts_u32(a, 0);
                 }
-            }
-            for (uint32_t i = wa; i < wb; i++) sts_u32(eva(E, 4 * i), 0);   // clear the codes read
             }
         }
         __syncwarp();
@@ -1070,7 +1064,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             pend.dtile = dtile;
             pend.kmap_s = E.kmap_s;
         } else {
-            copy_stage(P, E.kmap_s, stage, fast_total < STAGE_CAP ? fast_total : STAGE_CAP, G);
+            copy_stage(P, E.kmap_s, stage, spill, fast_total, G);
             if (do_long && lane == 0) {
                 uint64_t f2;
                 generic_chunk<FORM>(E, long_s1 - 1, &f2, P.out_kinds, P.out_lens, P.cap, G + fast_total);
@@ -1082,7 +1076,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         uint64_t G = 0;
         if (resolve_tile(P, pend.tile, G)) {
             report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
-            copy_stage(P, pend.kmap_s, stage, pend.staged, G);
+            copy_stage(P, pend.kmap_s, stage, spill, pend.staged, G);
         }
     }
 }
@@ -1180,6 +1174,14 @@ struct WarpLaunch {
     int form = FORM_BYTE;
 };
 
+// The spill slots of a launch of `grid` CTAs of `nwarps` warps (uninitialised).
+int warp_spill(lx_ctx *c, uint32_t grid, uint32_t nwarps, uint32_t **out)
+{
+    const int rc = grow(&c->w_spill, &c->w_spill_bytes, sizeof(uint32_t) * SPILL_CAP * (size_t)grid * nwarps);
+    *out = static_cast<uint32_t *>(c->w_spill);
+    return rc;
+}
+
 int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t n, int mode, uint16_t *d_kinds,
                  uint32_t *d_lens, uint64_t capacity, uint64_t sparse_limit, WarpLaunch &L)
 {
@@ -1208,6 +1210,8 @@ int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t
     uint8_t *scr = static_cast<uint8_t *>(c->scratch);
     WParams &P = L.P;
     P = WParams{};
+    rc = warp_spill(c, L.grid, L.nwarps, &P.spill);
+    if (rc != LX_OK) return rc;
     P.in = d_in;
     P.n = n;
     P.blob = static_cast<const uint8_t *>(dt.d_walk[mode]);
@@ -1440,6 +1444,9 @@ int lex_batch_warp(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, c
         if (rc != LX_OK) return rc;
         moved = od != c->b_dev || oh != c->b_host;
     }
+    uint32_t *spill = nullptr;
+    rc = warp_spill(c, grid, nwarps, &spill);
+    if (rc != LX_OK) return rc;
     uint8_t *dv = static_cast<uint8_t *>(c->b_dev);
     uint8_t *hs = static_cast<uint8_t *>(c->b_host);
     std::memcpy(hs, hd.data(), sizeof(WDoc) * D);
@@ -1447,7 +1454,7 @@ int lex_batch_warp(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, c
     std::vector<uint64_t> gkey = {0xB47C5ull, D, TT, (uint64_t)mode, (uint64_t)(uintptr_t)d_kinds,
                                   (uint64_t)(uintptr_t)d_lens, capacity, (uint64_t)(uintptr_t)dv,
                                   (uint64_t)(uintptr_t)hs, c->timeout_ns, grid, nwarps,
-                                  (uint64_t)(uintptr_t)c->wb_dev};
+                                  (uint64_t)(uintptr_t)c->wb_dev, (uint64_t)(uintptr_t)spill};
     gkey.insert(gkey.end(), key.begin(), key.end());
     if (moved || gkey != c->b_key || !c->b_exec) {
         if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
@@ -1467,6 +1474,7 @@ int lex_batch_warp(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, c
         P.out_kinds = d_kinds;
         P.out_lens = d_lens;
         P.cap = capacity;
+        P.spill = spill;
         P.res = reinterpret_cast<WResult *>(dv);
         P.tile_counter = reinterpret_cast<unsigned int *>(dv + 32);
         P.status = reinterpret_cast<unsigned long long *>(dv + o_status);

@@ -68,6 +68,9 @@ struct lx_ctx {
     size_t wb_dev_bytes = 0;
     std::vector<uint64_t> wb_key;
     uint32_t wb_blob_bytes = 0, wb_rows = 0, wb_acc_off = 0, wb_sets_off = 0;
+    // the warp-tile kernel's per-warp spill slots (kept tokens of a tile beyond its shared stage)
+    void *w_spill = nullptr;
+    size_t w_spill_bytes = 0;
     // optional kernel timing
     bool timing = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};

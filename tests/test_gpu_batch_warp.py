@@ -5,7 +5,8 @@ memory), the async lx_lex and the warps-per-CTA setting, through the C ABI:
 * one-launch batches against the oracle document by document, and against
   the per-set tile-kernel batches (LX_KERNEL_TILE), on mixed JSON / C-like
   and JSON / block-comment C-like batches with empty documents, lexing
-  errors and documents shorter than one tile; the output in document order;
+  errors and documents shorter than one tile; documents with more kept
+  tokens per tile than the shared stage holds; the output in document order;
 * lx_lex_async: many launches back to back on one stream, one
   synchronization, every record and stream equal to lx_lex's; the capacity
   status; the argument errors;
@@ -108,6 +109,34 @@ def test_one_launch_batch_against_the_oracle(env, names):
         # a second call of the same shape replays the graph with the same result
         rc3, n3, res3, k3, l3 = run_batch(lg, warp, names, spec, host, offs, mode)
         assert rc3 == 0 and res3 == res and np.array_equal(k3, k)
+
+
+def test_one_launch_batch_dense_documents(env):
+    # C-like documents of one-byte operator tokens (over 1536 kept tokens
+    # per tile: the stage spills) between JSON documents, in one launch
+    lg = env
+    rng = random.Random(12)
+    names = ("json", "clike")
+    ops = b"+-*%~!;,"
+    spec, chunks, offs, pos = [], [], [], 0
+    for i in range(30):
+        if i % 2:
+            lines = rng.randint(1, 400)
+            w = b"\n".join(bytes(rng.choice(ops) for _ in range(rng.randint(30, 300))) for _ in range(lines))
+            spec.append(("clike", len(w), 0))
+        else:
+            w = bytes(corpus.generate("json", rng.choice([0, 1000, 50_000]), seed=300 + i))
+            spec.append(("json", len(w), 0))
+        offs.append(pos)
+        chunks.append(w + bytes(-len(w) % 16))
+        pos += len(chunks[-1])
+    host = np.frombuffer(b"".join(chunks) or b"\0", np.uint8).copy()
+    ctx = lg.lx_ctx_create()
+    rc, n_total, res, k, l = run_batch(lg, ctx, names, spec, host, offs, 2)
+    assert rc == 0, lg.lx_strerror(rc)
+    check_docs(spec, host, offs, 2, res, k, l)
+    starts = [r[0] for (nm, s, _), r in zip(spec, res) if s]
+    assert starts == sorted(starts)
 
 
 def test_one_launch_batch_tiny_and_single_set(env):

@@ -5,7 +5,8 @@ element by element, through the C ABI.
 Cases: every token set and mode on seeded corpora at ragged sizes; lexing
 errors near tile and slice edges; lines longer than the halo (the last chunk
 of a tile leaves it and is walked byte by byte); inputs with no certified
-byte at all; more kept tokens per tile than the shared stage holds;
+byte at all; more kept tokens per tile than the shared stage holds (up to
+one per byte, dense and sparse tiles in turn, full-mode corpora);
 backtracking-heavy inputs; the capacity protocol; empty and one-byte inputs.
 """
 
@@ -137,6 +138,29 @@ def test_dense_tokens_overflow_the_stage(env):
     w = b"".join(line() for _ in range(3000))
     check(env, "clike", w, 2)
     check(env, "clike", w, 1, both=False)
+
+
+def test_every_byte_a_token(env):
+    # up to one kept token per byte: a tile's first 1536 go to the shared
+    # stage, the rest to the warp's spill slot
+    rng = random.Random(11)
+    ops = b"()+-*/;"
+    w = bytes(rng.choice(ops) for _ in range(20 * WT + 777))
+    check(env, "arith", w, 0)
+    # dense and sparse tiles in turn: a deferred tile's spill slot is copied
+    # out before the warp's next tile fills it
+    parts = []
+    for i in range(40):
+        if i % 3 == 0:
+            parts.append(bytes(rng.choice(ops) for _ in range(WT + rng.randint(-500, 500))))
+        else:
+            parts.append(b"\n".join(b"abc" * rng.randint(1, 40) for _ in range(60)))
+    w = b"".join(parts)
+    for mode in (0, 2):
+        check(env, "arith", w, mode)
+    # full-mode C-like and JSON: about 1 850 / 1 400 kept tokens per tile
+    for name, seed in (("clike", 105), ("json", 106)):
+        check(env, name, corpus.generate(name, (2 << 20) + 4099, seed=seed), 0)
 
 
 def test_backtracking(env):
