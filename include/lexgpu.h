@@ -278,6 +278,26 @@ int lx_ctx_set_kernel(lx_ctx *ctx, int kernel);
 int lx_ctx_set_warps(lx_ctx *ctx, uint32_t warps);
 
 /*
+ * lx_ctx_set_warp_geometry -- the warp-tile kernel's per-warp geometry on
+ * this context.
+ *   LX_WARP_GEOMETRY_SPARSE: a chunk may end up to 512 bytes past its tile
+ *     and 1536 kept tokens per tile are staged in shared memory;
+ *   LX_WARP_GEOMETRY_DENSE: 1024 bytes and 1024 staged tokens, the rest of a
+ *     tile's tokens staged in global memory (for inputs whose certified
+ *     bytes lie far apart, or with many kept tokens per tile);
+ *   LX_WARP_GEOMETRY_AUTO (default): sparse for the first call on a token
+ *     set and mode; later calls take what the previous call on them showed:
+ *     dense if it kept more than 1536 tokens per tile on average, or if
+ *     more than one tile in 20000 had its last chunk end past 512 bytes.
+ * Same tokens either way (a chunk that ends past the halo is walked by one
+ * lane, which is slow, not wrong).  LX_E_INVAL for another value.
+ */
+#define LX_WARP_GEOMETRY_AUTO 0
+#define LX_WARP_GEOMETRY_SPARSE 1
+#define LX_WARP_GEOMETRY_DENSE 2
+int lx_ctx_set_warp_geometry(lx_ctx *ctx, int geometry);
+
+/*
  * lx_ctx_debug_withhold -- failure-detection test hook.  In later lx_lex
  * calls on this context, the CTA that processes tile `tile` (17 408-byte
  * tiles) never publishes its look-back aggregate, so the bounded look-back

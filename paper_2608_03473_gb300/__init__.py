@@ -59,7 +59,7 @@ EXPORTED = (
     "lx_tokenset_free",
     "lx_ctx_create", "lx_ctx_free", "lx_ctx_set_timeout_ms", "lx_ctx_enable_timing", "lx_ctx_last_kernel_ms",
     "lx_ctx_set_config", "lx_ctx_get_config", "lx_autotune", "lx_ctx_debug_withhold", "lx_ctx_set_kernel",
-    "lx_ctx_set_warps", "lx_lex_async",
+    "lx_ctx_set_warps", "lx_ctx_set_warp_geometry", "lx_lex_async",
     "lx_lex", "lx_lex_host", "lx_lex_noalloc", "lx_lex_batch", "lx_lex_enumerative", "lx_chunk_contexts",
     "lx_lex_speculative", "lx_model_create", "lx_model_free", "lx_model_info", "lx_model_get_params",
     "lx_model_set_params", "lx_model_windows", "lx_model_forward", "lx_model_gradient", "lx_model_train_step",
@@ -127,6 +127,7 @@ def load_library(path: Optional[str] = None):
             "lx_ctx_debug_withhold": (i32, [vp, u32]),
             "lx_ctx_set_kernel": (i32, [vp, i32]),
             "lx_ctx_set_warps": (i32, [vp, u32]),
+            "lx_ctx_set_warp_geometry": (i32, [vp, i32]),
             "lx_lex_async": (i32, [vp, vp, vp, u64, i32, vp, vp, u64, vp, vp]),
             "lx_ctx_get_config": (i32, [vp, vp, i32, vp, vp, vp, vp]),
             "lx_autotune": (i32, [vp, vp, i32, vp, u64, vp, vp, u64, vp]),
@@ -320,6 +321,17 @@ def lx_ctx_set_kernel(ctx: Ctx, kernel: int) -> int:
 def lx_ctx_set_warps(ctx: Ctx, warps: int) -> int:
     """Warps per CTA of the warp-tile kernel (0: as many as fit)."""
     return load_library().lx_ctx_set_warps(ctx.handle, int(warps))
+
+
+LX_WARP_GEOMETRY_AUTO, LX_WARP_GEOMETRY_SPARSE, LX_WARP_GEOMETRY_DENSE = 0, 1, 2
+
+
+def lx_ctx_set_warp_geometry(ctx: Ctx, geometry: int) -> int:
+    """The warp-tile kernel's geometry: LX_WARP_GEOMETRY_AUTO (chosen from the
+    previous call on the same token set and mode), _SPARSE (512-byte halo,
+    1536 staged tokens) or _DENSE (1024 and 1024, the rest staged in global
+    memory)."""
+    return load_library().lx_ctx_set_warp_geometry(ctx.handle, int(geometry))
 
 
 class AsyncResult(ctypes.Structure):

@@ -1082,7 +1082,7 @@ extern "C" int lx_ctx_create(lx_ctx **out)
     if (!c) return LX_E_NOMEM;
     c->device = dev;
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaMallocHost(&c->h_res, sizeof(Result)) != cudaSuccess) {
+        cudaMallocHost(&c->h_res, std::max(sizeof(Result), LAUNCH_RECORD_BYTES)) != cudaSuccess) {
         delete c;
         return LX_E_CUDA;
     }
@@ -1143,6 +1143,13 @@ extern "C" int lx_ctx_set_warps(lx_ctx *c, uint32_t warps)
 {
     if (!c || warps > 20) return LX_E_INVAL;
     c->warps = warps;
+    return LX_OK;
+}
+
+extern "C" int lx_ctx_set_warp_geometry(lx_ctx *c, int geometry)
+{
+    if (!c || geometry < LX_WARP_GEOMETRY_AUTO || geometry > LX_WARP_GEOMETRY_DENSE) return LX_E_INVAL;
+    c->warp_geometry = geometry;
     return LX_OK;
 }
 

@@ -49,21 +49,33 @@ namespace {
 
 constexpr uint32_t WT = 6144;                 // input bytes per warp tile (6 KiB: measured best of 2-8 KiB)
 // The kernels' FORM template argument: bit 0 the table's lookup form
-// (FORM_BYTE / FORM_CLASS), bit 1 (WIN) split-window rows (exact modes).
+// (FORM_BYTE / FORM_CLASS), bit 1 (WIN) split-window rows (exact modes),
+// bit 2 (DENSE) the geometry for many kept tokens per tile or far-apart cuts.
 constexpr int WIN = 2;
+constexpr int DENSE = 4;
 constexpr uint32_t SLICE = WT / 32;           // bytes per lane slice (phase 1)
 constexpr uint32_t BLK = 16;                  // bytes per lockstep step of a lane
 constexpr uint32_t NB1 = SLICE / BLK;         // phase-1 steps
-constexpr uint32_t HALO = 512;                // positions past the tile a chunk may end at
-constexpr uint32_t EVB = WT + HALO;           // event buffer positions
-constexpr uint32_t LIMIT = EVB - BLK;         // chunk ends must lie below (room for the last block)
+// A warp's geometry.  Sparse (the default): a chunk may end up to 512
+// positions past its tile and 1 536 kept tokens are staged in shared memory.
+// Dense: 1 024 positions (certified bytes far apart) and 1 024 staged tokens,
+// a tile's further tokens going to the warp's spill slot in global memory
+// (many kept tokens per tile), so that as many warps fit.
 // Event code of position p at ev + p + 4 (p >> 7): a 4-byte pad after every
 // 128 positions, so the 32 lanes' phase-1 stores (slices 128 positions
 // apart) fall in 32 different banks.
-constexpr uint32_t EV_BYTES = ((EVB + 16 + 4 * ((EVB + 16) / 128 + 1)) + 15) / 16 * 16;
-constexpr uint32_t STAGE_CAP = 1536;          // kept tokens per tile staged for coalesced writes
-constexpr uint32_t WAREA = EV_BYTES + 4 * STAGE_CAP;   // shared bytes per warp
-constexpr uint32_t SPILL_CAP = LIMIT - STAGE_CAP;     // kept tokens of a tile past the stage, at most
+template <int FORM>
+struct Geo {
+    static constexpr bool dense = (FORM & DENSE) != 0;
+    static constexpr uint32_t HALO = dense ? 1024 : 512;   // positions past the tile a chunk may end at
+    static constexpr uint32_t EVB = WT + HALO;             // event buffer positions
+    static constexpr uint32_t LIMIT = EVB - BLK;           // chunk ends must lie below (room for the last block)
+    static constexpr uint32_t EV_BYTES = ((EVB + 16 + 4 * ((EVB + 16) / 128 + 1)) + 15) / 16 * 16;
+    static constexpr uint32_t STAGE_CAP = dense ? 1024 : 1536;   // kept tokens per tile staged for coalesced writes
+    static constexpr uint32_t WAREA = EV_BYTES + 4 * STAGE_CAP;  // shared bytes per warp
+};
+constexpr uint32_t SPARSE_LIMIT = Geo<0>::LIMIT;
+constexpr uint32_t SPILL_CAP = Geo<DENSE>::LIMIT;   // spill slot entries per warp: a tile's kept tokens, at most
 constexpr uint32_t GS = 64;                   // tiles per look-back group
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t BIG = 0x7FFFFFFFu;
@@ -73,7 +85,8 @@ constexpr unsigned ERR_SMEM = 2u;
 constexpr unsigned ERR_SPARSE = 4u;   // a chunk ran past the sparse limit: certified bytes too far apart
 constexpr unsigned ERR_LOOKAHEAD = 8u;   // backtracking past its step budget (failed lookahead)
 
-static_assert(SLICE % BLK == 0 && WAREA % 16 == 0, "geometry");
+static_assert(SLICE % BLK == 0 && Geo<0>::WAREA % 16 == 0 && Geo<DENSE>::WAREA % 16 == 0, "geometry");
+static_assert(Geo<0>::LIMIT - Geo<0>::STAGE_CAP <= SPILL_CAP, "spill slot");
 
 struct WResult {
     unsigned long long total;          // kept tokens over all tiles
@@ -81,6 +94,8 @@ struct WResult {
     unsigned long long inv_fail_tok;   // ~output index at that failure
     unsigned int error;
     unsigned int pad;
+    unsigned int long_tiles;           // tiles whose last chunk ends past the sparse geometry's halo
+    unsigned int pad2[3];
 };
 
 // Batches: a document's tiles are consecutive in the launch's tile sequence
@@ -669,7 +684,7 @@ __device__ bool resolve_tile(const WParams &P, uint32_t tile, uint64_t &G)
 // A tile whose tokens wait in the warp's stage for their output offset.
 struct Pending {
     uint32_t tile;      // NONE: nothing pending
-    uint32_t staged;    // the tile's kept tokens (stage, then spill slot)
+    uint32_t staged;    // the tile's kept tokens (dense: | how many of them are in the stage << 16)
     uint64_t fail;      // failure offset within the tile, or NONE64
     uint64_t agg;
     uint32_t doc, dtile;   // batches: its document and its index there
@@ -697,15 +712,15 @@ __device__ void report_failure(const WParams &P, uint32_t tile, uint64_t fail, u
 }
 
 // The staged tokens of a tile to the output from index G, coalesced: the
-// first STAGE_CAP from the shared stage, the rest from the warp's spill slot;
+// first `split` from the shared stage, the rest from the warp's spill slot;
 // kmap_s: the kind map of the tile's token set.
-__device__ void copy_stage(const WParams &P, uint32_t kmap_s, uint32_t stage, const uint32_t *spill, uint32_t staged,
-                           uint64_t G)
+__device__ void copy_stage(const WParams &P, uint32_t kmap_s, uint32_t stage, const uint32_t *spill, uint32_t split,
+                           uint32_t staged, uint64_t G)
 {
     for (uint32_t i = threadIdx.x & 31; i < staged; i += 32) {
         const uint64_t o = G + i;
         if (o < P.cap) {
-            const uint32_t v = i < STAGE_CAP ? lds_u32(stage + 4 * i) : spill[i - STAGE_CAP];
+            const uint32_t v = i < split ? lds_u32(stage + 4 * i) : spill[i - split];
             P.out_kinds[o] = (uint16_t)lds_u16(kmap_s + (v >> 16));
             P.out_lens[o] = v & 0xFFFFu;
         }
@@ -784,6 +799,9 @@ template <int FORM, bool BATCH>
 __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
+    constexpr bool dense = Geo<FORM>::dense;
+    constexpr uint32_t EVB = Geo<FORM>::EVB, LIMIT = Geo<FORM>::LIMIT, EV_BYTES = Geo<FORM>::EV_BYTES;
+    constexpr uint32_t STAGE_CAP = Geo<FORM>::STAGE_CAP, WAREA = Geo<FORM>::WAREA;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t sbase = smem_u32(smem);
     const uint32_t tb_s = (sbase + 511u) & ~511u;
@@ -987,7 +1005,10 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         if (do_long && lane == 0) {
             gen_cnt = generic_chunk<FORM>(E, long_s1 - 1, &gen_fail, nullptr, nullptr, 0, 0, P.sparse_limit, &over);
             if (over) atomicOr(&P.res->error, over);   // the caller lexes the input another way
+            if (!dense) atomicAdd(&P.res->long_tiles, 1u);
         }
+        if (dense && lane == 0 && c0 != NONE && (c1 == NONE || (c1 >= SPARSE_LIMIT && c1 < nrel)))
+            atomicAdd(&P.res->long_tiles, 1u);   // long for the sparse geometry
         if (__shfl_sync(0xffffffffu, over ? 1u : 0u, 0)) {
             publish_tile(P, tile, 0);
             break;
@@ -1004,7 +1025,8 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             uint64_t G = 0;
             if (!resolve_tile(P, pend.tile, G)) break;
             report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
-            copy_stage(P, pend.kmap_s, stage, spill, pend.staged, G);
+            copy_stage(P, pend.kmap_s, stage, spill, dense ? pend.staged >> 16 : STAGE_CAP,
+                       dense ? pend.staged & 0xFFFFu : pend.staged, G);
             pend.tile = NONE;
             __syncwarp();
         }
@@ -1013,6 +1035,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         // (past STAGE_CAP into the warp's spill slot)
         const bool defer = !do_long;
         uint64_t G = 0;
+        uint32_t split = STAGE_CAP;   // dense: how many kept tokens are in the stage (the rest: spill slot)
         if (!defer) {   // rare: a chunk past the halo is written at once
             if (!resolve_tile(P, tile, G)) break;
             report_failure<BATCH>(P, tile, fpos, G, agg, doc, dtile);
@@ -1027,28 +1050,57 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             if (lane == 0 || prev < c0) prev = c0;
             // every lane its words, four codes per word without branches;
             // the words read are cleared for the next tile
-            uint32_t d = 4 * wa - prev;
-            if (excl + cnt <= STAGE_CAP) {
-                uint32_t sa = stage + 4 * excl;
+            if (!dense) {
+                uint32_t d = 4 * wa - prev;
+                if (excl + cnt <= STAGE_CAP) {
+                    uint32_t sa = stage + 4 * excl;
+                    for (uint32_t i = wa; i < wb; i++) {
+                        const uint32_t a = eva(E, 4 * i);
+                        emit_word(sa, d, lds_u32(a));
+                        sts_u32(a, 0);
+                    }
+                } else {   // this lane's codes reach past the stage
+                    uint32_t idx = excl;
+                    for (uint32_t i = wa; i < wb; i++) {
+                        const uint32_t a = eva(E, 4 * i), w = lds_u32(a);
+    #pragma unroll
+                        for (uint32_t k = 0; k < 4; k++) {
+                            const uint32_t code = (w >> (8 * k)) & 0xFFu;
+                            if (code > 3) {
+                                const uint32_t v = (code << 16) | d;
+                                if (idx < STAGE_CAP) sts_u32(stage + 4 * idx, v);
+                                else spill[idx - STAGE_CAP] = v;
+                                idx++;
+                            }
+                            d = code ? 1u : d + 1;
+                        }
+                        sts_u32(a, 0);
+                    }
+                }
+            } else if (fast_total <= STAGE_CAP) {
+                split = fast_total;
+                uint32_t d = 4 * wa - prev, sa = stage + 4 * excl;
                 for (uint32_t i = wa; i < wb; i++) {
                     const uint32_t a = eva(E, 4 * i);
                     emit_word(sa, d, lds_u32(a));
                     sts_u32(a, 0);
                 }
-            } else {   // this lane's codes reach past the stage
-                uint32_t idx = excl;
+            } else {
+                // all lanes one loop through generic pointers: excl + cnt ascends
+                // with the lane, so the lanes that fit the stage are a prefix; the
+                // others write the spill slot from the first misfit lane's index on
+                uint32_t d = 4 * wa - prev;
+                const uint32_t fit = __popc(__ballot_sync(0xffffffffu, excl + cnt <= STAGE_CAP));
+                split = fit == 32 ? fast_total : __shfl_sync(0xffffffffu, excl, fit & 31u);
+                uint32_t *gp = (uint32_t)lane < fit ? reinterpret_cast<uint32_t *>(smem + (stage - sbase)) + excl
+                                                    : spill + (excl - split);
                 for (uint32_t i = wa; i < wb; i++) {
                     const uint32_t a = eva(E, 4 * i), w = lds_u32(a);
 #pragma unroll
                     for (uint32_t k = 0; k < 4; k++) {
-                        const uint32_t code = (w >> (8 * k)) & 0xFFu;
-                        if (code > 3) {
-                            const uint32_t v = (code << 16) | d;
-                            if (idx < STAGE_CAP) sts_u32(stage + 4 * idx, v);
-                            else spill[idx - STAGE_CAP] = v;
-                            idx++;
-                        }
-                        d = code ? 1u : d + 1;
+                        const uint32_t c = (w >> (8 * k)) & 0xFFu;
+                        if (c > 3) *gp++ = (c << 16) | d;
+                        d = c ? 1u : d + 1u;
                     }
                     sts_u32(a, 0);
                 }
@@ -1057,14 +1109,14 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         __syncwarp();
         if (defer) {
             pend.tile = tile;
-            pend.staged = fast_total;
+            pend.staged = dense ? fast_total | (split << 16) : fast_total;
             pend.fail = fpos;
             pend.agg = agg;
             pend.doc = doc;
             pend.dtile = dtile;
             pend.kmap_s = E.kmap_s;
         } else {
-            copy_stage(P, E.kmap_s, stage, spill, fast_total, G);
+            copy_stage(P, E.kmap_s, stage, spill, split, fast_total, G);
             if (do_long && lane == 0) {
                 uint64_t f2;
                 generic_chunk<FORM>(E, long_s1 - 1, &f2, P.out_kinds, P.out_lens, P.cap, G + fast_total);
@@ -1076,7 +1128,8 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         uint64_t G = 0;
         if (resolve_tile(P, pend.tile, G)) {
             report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
-            copy_stage(P, pend.kmap_s, stage, spill, pend.staged, G);
+            copy_stage(P, pend.kmap_s, stage, spill, dense ? pend.staged >> 16 : STAGE_CAP,
+                       dense ? pend.staged & 0xFFFFu : pend.staged, G);
         }
     }
 }
@@ -1097,7 +1150,7 @@ int occupancy_of(uint32_t threads, uint32_t smem, int *o)
 
 int warp_occupancy(lx_ctx *c, int form, bool batch, uint32_t threads, uint32_t smem, int *occ)
 {
-    const uint64_t key = (3ull << 40) | ((uint64_t)batch << 39) | ((uint64_t)threads << 33) | ((uint64_t)form << 32) |
+    const uint64_t key = (3ull << 62) | ((uint64_t)threads << 40) | ((uint64_t)batch << 36) | ((uint64_t)form << 32) |
                          smem;
     for (auto &kv : c->occupancy)
         if (kv.first == key) {
@@ -1105,11 +1158,21 @@ int warp_occupancy(lx_ctx *c, int form, bool batch, uint32_t threads, uint32_t s
             return LX_OK;
         }
     int o = 0, rc;
-    if (batch) rc = occupancy_of<FORM_CLASS, true>(threads, smem, &o);
-    else if (form == FORM_BYTE) rc = occupancy_of<FORM_BYTE, false>(threads, smem, &o);
-    else if (form == FORM_CLASS) rc = occupancy_of<FORM_CLASS, false>(threads, smem, &o);
-    else if (form == (FORM_BYTE | WIN)) rc = occupancy_of<FORM_BYTE | WIN, false>(threads, smem, &o);
-    else rc = occupancy_of<FORM_CLASS | WIN, false>(threads, smem, &o);
+    if (batch) {
+        rc = occupancy_of<FORM_CLASS, true>(threads, smem, &o);
+    } else {
+        switch (form) {
+        case FORM_BYTE: rc = occupancy_of<FORM_BYTE, false>(threads, smem, &o); break;
+        case FORM_CLASS: rc = occupancy_of<FORM_CLASS, false>(threads, smem, &o); break;
+        case FORM_BYTE | WIN: rc = occupancy_of<FORM_BYTE | WIN, false>(threads, smem, &o); break;
+        case FORM_CLASS | WIN: rc = occupancy_of<FORM_CLASS | WIN, false>(threads, smem, &o); break;
+        case FORM_BYTE | DENSE: rc = occupancy_of<FORM_BYTE | DENSE, false>(threads, smem, &o); break;
+        case FORM_CLASS | DENSE: rc = occupancy_of<FORM_CLASS | DENSE, false>(threads, smem, &o); break;
+        case FORM_BYTE | WIN | DENSE: rc = occupancy_of<FORM_BYTE | WIN | DENSE, false>(threads, smem, &o); break;
+        case FORM_CLASS | WIN | DENSE: rc = occupancy_of<FORM_CLASS | WIN | DENSE, false>(threads, smem, &o); break;
+        default: return LX_E_INVAL;
+        }
+    }
     if (rc != LX_OK) return rc;
     if (o < 1) return LX_E_TOOBIG;
     c->occupancy.emplace_back(key, o);
@@ -1119,8 +1182,9 @@ int warp_occupancy(lx_ctx *c, int form, bool batch, uint32_t threads, uint32_t s
 
 // Warps per CTA next to a table blob of `blob_bytes`: as many as the shared
 // memory budget holds, at most MAX_WARPS (or the context's setting).
-uint32_t warps_for(uint32_t want, uint32_t blob_bytes, uint32_t *smem)
+uint32_t warps_for(uint32_t want, uint32_t blob_bytes, uint32_t *smem, bool dense = false)
 {
+    const uint32_t WAREA = dense ? Geo<DENSE>::WAREA : Geo<0>::WAREA;
     const uint32_t fixed = 512 + blob_bytes + 16;
     if (fixed + WAREA > SMEM_BUDGET) return 0;
     uint32_t nw = std::min<uint32_t>(MAX_WARPS, (SMEM_BUDGET - fixed) / WAREA);
@@ -1172,7 +1236,35 @@ struct WarpLaunch {
     uint32_t grid = 0, nwarps = 0, smem = 0;
     size_t need = 0;
     int form = FORM_BYTE;
+    bool dense = false;
 };
+
+// The geometry of the next call on (ts, mode): the context's setting, else
+// what the last call on them showed (sparse until one has run).
+bool warp_dense(const lx_ctx *c, const lx_tokenset *ts, int mode)
+{
+    if (c->warp_geometry != LX_WARP_GEOMETRY_AUTO) return c->warp_geometry == LX_WARP_GEOMETRY_DENSE;
+    const uint64_t key = ts->serial * 8 + (uint64_t)mode;
+    for (const auto &kv : c->warp_dense)
+        if (kv.first == key) return kv.second;
+    return false;
+}
+
+// After a call of n_tiles tiles: the dense geometry pays where the tiles
+// hold more kept tokens on average than the sparse stage, or where more than
+// one tile in 20 000 has its last chunk end past the sparse halo (every such
+// tile walks that chunk byte by byte while every later tile waits for its count).
+void note_geometry(lx_ctx *c, const lx_tokenset *ts, int mode, uint64_t tokens, uint64_t n_tiles, uint32_t long_tiles)
+{
+    const bool dense = tokens > (uint64_t)Geo<0>::STAGE_CAP * n_tiles || (uint64_t)long_tiles * 20000 > n_tiles;
+    const uint64_t key = ts->serial * 8 + (uint64_t)mode;
+    for (auto &kv : c->warp_dense)
+        if (kv.first == key) {
+            kv.second = dense;
+            return;
+        }
+    c->warp_dense.emplace_back(key, dense);
+}
 
 // The spill slots of a launch of `grid` CTAs of `nwarps` warps (uninitialised).
 int warp_spill(lx_ctx *c, uint32_t grid, uint32_t nwarps, uint32_t **out)
@@ -1194,9 +1286,10 @@ int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t
     const uint64_t n_tiles64 = (n + WT - 1) / WT;
     if (n_tiles64 > 0xFFFFFFF0ull) return LX_E_INVAL;
     const uint32_t n_tiles = (uint32_t)n_tiles64;
-    L.nwarps = warps_for(warps_setting(c, ts, mode), (uint32_t)w.blob.size(), &L.smem);
+    L.dense = warp_dense(c, ts, mode);
+    L.nwarps = warps_for(warps_setting(c, ts, mode), (uint32_t)w.blob.size(), &L.smem, L.dense);
     if (L.nwarps < 1) return LX_E_TOOBIG;
-    L.form = w.form | (w.n_ctx ? WIN : 0);
+    L.form = w.form | (w.n_ctx ? WIN : 0) | (L.dense ? DENSE : 0);
     int occ = 0;
     rc = warp_occupancy(c, L.form, false, 32 * L.nwarps, L.smem, &occ);
     if (rc != LX_OK) return rc;
@@ -1230,7 +1323,7 @@ int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t
     P.out_lens = d_lens;
     P.cap = capacity;
     P.res = reinterpret_cast<WResult *>(scr);
-    P.tile_counter = reinterpret_cast<unsigned int *>(scr + 32);
+    P.tile_counter = reinterpret_cast<unsigned int *>(scr + sizeof(WResult));
     P.status = reinterpret_cast<unsigned long long *>(scr + 64);
     P.gstatus = reinterpret_cast<unsigned long long *>(scr + o_gstatus);
     P.gdone = reinterpret_cast<unsigned int *>(scr + o_gdone);
@@ -1238,18 +1331,27 @@ int warp_prepare(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64_t
     P.timeout_ns = c->timeout_ns;
     P.withhold = c->withhold;
     P.sparse_limit = sparse_limit;
-    static_assert(sizeof(WResult) == 32, "record layout");
+    static_assert(sizeof(WResult) == 48 && sizeof(WResult) + 4 <= 64 && sizeof(WResult) <= LAUNCH_RECORD_BYTES,
+                  "record layout");
     return LX_OK;
 }
 
 void warp_launch(const WarpLaunch &L, cudaStream_t st)
 {
+#define LXW_LAUNCH(F) \
+    case F: lex_warps<F, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
     switch (L.form) {
-    case FORM_BYTE: lex_warps<FORM_BYTE, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
-    case FORM_CLASS: lex_warps<FORM_CLASS, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
-    case FORM_BYTE | WIN: lex_warps<FORM_BYTE | WIN, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
-    default: lex_warps<FORM_CLASS | WIN, false><<<L.grid, 32 * L.nwarps, L.smem, st>>>(L.P); break;
+        LXW_LAUNCH(FORM_BYTE)
+        LXW_LAUNCH(FORM_CLASS)
+        LXW_LAUNCH(FORM_BYTE | WIN)
+        LXW_LAUNCH(FORM_CLASS | WIN)
+        LXW_LAUNCH(FORM_BYTE | DENSE)
+        LXW_LAUNCH(FORM_CLASS | DENSE)
+        LXW_LAUNCH(FORM_BYTE | WIN | DENSE)
+        LXW_LAUNCH(FORM_CLASS | WIN | DENSE)
+    default: break;
     }
+#undef LXW_LAUNCH
 }
 
 }  // namespace
@@ -1278,6 +1380,8 @@ int lex_warp_device(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint6
     if (rc != LX_OK) return rc;
     const WResult r = *static_cast<const WResult *>(c->h_res);
     if (r.error & ERR_LOOKAHEAD) return LX_LOOKAHEAD;
+    if (r.error == 0 && c->warp_geometry == LX_WARP_GEOMETRY_AUTO)
+        note_geometry(c, ts, mode, r.total, L.P.n_tiles, r.long_tiles);
     if (r.error & ERR_SPARSE) return LX_SPARSE;
     if (r.error & ERR_TIMEOUT) return LX_E_TIMEOUT;
     if (r.error & ERR_SMEM) return LX_E_TOOBIG;
@@ -1476,7 +1580,7 @@ int lex_batch_warp(lx_ctx *c, const lx_tokenset *const *sets, uint32_t n_sets, c
         P.cap = capacity;
         P.spill = spill;
         P.res = reinterpret_cast<WResult *>(dv);
-        P.tile_counter = reinterpret_cast<unsigned int *>(dv + 32);
+        P.tile_counter = reinterpret_cast<unsigned int *>(dv + sizeof(WResult));
         P.status = reinterpret_cast<unsigned long long *>(dv + o_status);
         P.gstatus = reinterpret_cast<unsigned long long *>(dv + o_gstatus);
         P.gdone = reinterpret_cast<unsigned int *>(dv + o_gdone);

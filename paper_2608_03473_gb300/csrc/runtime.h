@@ -23,12 +23,15 @@ struct lx_tuned {
     uint32_t warps = 0;       // warps per CTA it chose for the warp-tile kernel (0: as many as fit)
 };
 
+// Bytes of the pinned buffer for a kernel's launch record (lx_ctx::h_res).
+constexpr size_t LAUNCH_RECORD_BYTES = 64;
+
 struct lx_ctx {
     int device = 0;
     int num_sms = 0;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
-    void *h_res = nullptr;   // pinned: the launch record read back by lx_lex
+    void *h_res = nullptr;   // pinned: the launch record read back by lx_lex (LAUNCH_RECORD_BYTES)
     uint64_t timeout_ns = 20ull * 1000 * 1000 * 1000;
     uint32_t withhold = 0xFFFFFFFFu;   // failure-detection tests (lx_ctx_debug_withhold)
     std::vector<std::pair<uint64_t, int>> occupancy;   // (form << 32 | shared bytes) -> CTAs per SM
@@ -68,6 +71,10 @@ struct lx_ctx {
     size_t wb_dev_bytes = 0;
     std::vector<uint64_t> wb_key;
     uint32_t wb_blob_bytes = 0, wb_rows = 0, wb_acc_off = 0, wb_sets_off = 0;
+    // the warp-tile kernel's geometry (lx_ctx_set_warp_geometry) and, in
+    // LX_WARP_GEOMETRY_AUTO, the choice per (token set serial * 8 + mode)
+    int warp_geometry = 0;
+    std::vector<std::pair<uint64_t, bool>> warp_dense;
     // the warp-tile kernel's per-warp spill slots (kept tokens of a tile beyond its shared stage)
     void *w_spill = nullptr;
     size_t w_spill_bytes = 0;

@@ -2,6 +2,10 @@
 codes in the walk table) against the oracle and against the tile kernel,
 element by element, through the C ABI.
 
+Both geometries (sparse: 512-byte halo, 1536 staged tokens; dense: 1024 and
+1024, the rest of a tile's tokens in the warp's global spill slot) on every
+case, and the automatic choice between them on repeated calls.
+
 Cases: every token set and mode on seeded corpora at ragged sizes; lexing
 errors near tile and slice edges; lines longer than the halo (the last chunk
 of a tile leaves it and is walked byte by byte); inputs with no certified
@@ -32,9 +36,13 @@ def env(lexlib):
     lg = lexlib
     warp = lg.lx_ctx_create()
     assert lg.lx_ctx_set_kernel(warp, lg.LX_KERNEL_WARP) == 0
+    assert lg.lx_ctx_set_warp_geometry(warp, lg.LX_WARP_GEOMETRY_SPARSE) == 0
     tile = lg.lx_ctx_create()
     assert lg.lx_ctx_set_kernel(tile, lg.LX_KERNEL_TILE) == 0
-    return lg, warp, tile
+    dense = lg.lx_ctx_create()
+    assert lg.lx_ctx_set_kernel(dense, lg.LX_KERNEL_WARP) == 0
+    assert lg.lx_ctx_set_warp_geometry(dense, lg.LX_WARP_GEOMETRY_DENSE) == 0
+    return lg, warp, tile, dense
 
 
 _ts = {}
@@ -71,12 +79,13 @@ def expected(name, w, mode):
 
 
 def check(env, name, w, mode, both=True):
-    lg, warp, tile = env
+    lg, warp, tile, dense = env
     ek, el, econ = expected(name, w, mode)
-    rc, nt, con, k, l = run(lg, warp, name, w, mode)
-    assert rc == 0, lg.lx_strerror(rc)
-    assert con == econ and nt == ek.size, (name, mode, con, econ, nt, ek.size)
-    assert np.array_equal(k, ek) and np.array_equal(l, el), (name, mode)
+    for ctx in (warp, dense):   # both geometries
+        rc, nt, con, k, l = run(lg, ctx, name, w, mode)
+        assert rc == 0, lg.lx_strerror(rc)
+        assert con == econ and nt == ek.size, (name, mode, con, econ, nt, ek.size)
+        assert np.array_equal(k, ek) and np.array_equal(l, el), (name, mode)
     if both:
         rc2, nt2, con2, k2, l2 = run(lg, tile, name, w, mode)
         assert rc2 == 0 and nt2 == nt and con2 == con
@@ -92,8 +101,9 @@ SETS = [("arith", 0), ("arith", 1), ("arith", 2), ("json", 1), ("json", 2), ("cl
 def test_corpora_ragged(env, name, mode):
     gen = "clike" if name == "clike_row1" else name
     base = corpus.generate(gen, 3 << 20, seed=101)
-    for n in (1, 15, 16, 17, 127, 128, 129, 191, 192, 193, WT - 1, WT, WT + 1, WT + 511, WT + 512, WT + 513,
-              3 * WT + 77, 100_003, base.size):
+    for n in (1, 15, 16, 17, 127, 128, 129, 191, 192, 193, WT - 1, WT, WT + 1, WT + 495, WT + 496, WT + 497,
+              WT + 511, WT + 512, WT + 513, WT + 1007, WT + 1008, WT + 1009, WT + 1024, 3 * WT + 77, 100_003,
+              base.size):
         check(env, name, base[:n], mode, both=n == base.size)
 
 
@@ -173,20 +183,21 @@ def test_backtracking(env):
 
 
 def test_capacity_and_small(env):
-    lg, warp, tile = env
+    lg, warp, tile, dense = env
     w = corpus.generate("json", 300_000, seed=104)
     ek, el, econ = expected("json", w, 2)
     cap = ek.size // 3
-    rc, nt, con, k, l = run(lg, warp, "json", w, 2, capacity=cap)
-    assert rc == lg.LX_E_CAPACITY and nt == ek.size and con == econ
-    assert np.array_equal(k, ek[:cap]) and np.array_equal(l, el[:cap])
+    for ctx in (warp, dense):
+        rc, nt, con, k, l = run(lg, ctx, "json", w, 2, capacity=cap)
+        assert rc == lg.LX_E_CAPACITY and nt == ek.size and con == econ
+        assert np.array_equal(k, ek[:cap]) and np.array_equal(l, el[:cap])
     for w in (b"", b"{", b"\n", b"1", b"\x01", b"[1]\n"):
         check(env, "json", w, 2)
 
 
 def test_warp_kernel_needs_aligned_input(env):
     import torch
-    lg, warp, tile = env
+    lg, warp, tile, dense = env
     w = corpus.generate("json", 10_000, seed=105)
     d = torch.zeros(w.size + 32, dtype=torch.uint8, device="cuda")
     d[3:3 + w.size].copy_(torch.from_numpy(w.copy()))
@@ -198,3 +209,24 @@ def test_warp_kernel_needs_aligned_input(env):
     rc, nt, con = lg.lx_lex(auto, tokenset(lg, "json"), d[3:3 + w.size], 2, k, l)
     ek, el, econ = expected("json", w, 2)
     assert rc == 0 and nt == ek.size and con == econ     # the tile kernel serves it
+
+
+def test_geometry_setting_and_auto(env):
+    lg = env[0]
+    assert lg.lx_ctx_set_warp_geometry(lg.lx_ctx_create(), 3) == lg.LX_E_INVAL
+    assert lg.lx_ctx_set_warp_geometry(lg.lx_ctx_create(), -1) == lg.LX_E_INVAL
+    # AUTO: the first call sparse, later ones as the previous call showed; the
+    # stream never changes.  Full-mode C-like (about 1 850 kept tokens per
+    # tile) and lines longer than the sparse halo both turn it dense.
+    auto = lg.lx_ctx_create()
+    assert lg.lx_ctx_set_kernel(auto, lg.LX_KERNEL_WARP) == 0
+    rng = random.Random(12)
+    long_lines = b"".join(b'{"s":"' + b"z" * rng.randint(600, 1500) + b'"}\n' if rng.random() < 0.2
+                          else b'{"a":1}\n' for _ in range(2000))
+    for name, w, mode in (("clike", corpus.generate("clike", (1 << 20) + 5, seed=106), 0),
+                          ("json", corpus.generate("json", (1 << 20) + 3, seed=107), 2),
+                          ("clike", long_lines, 2)):
+        ek, el, econ = expected(name, w, mode)
+        for _ in range(3):
+            rc, nt, con, k, l = run(lg, auto, name, w, mode)
+            assert rc == 0 and con == econ and np.array_equal(k, ek) and np.array_equal(l, el)
