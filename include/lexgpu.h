@@ -282,7 +282,7 @@ int lx_ctx_set_warps(lx_ctx *ctx, uint32_t warps);
  * this context.
  *   LX_WARP_GEOMETRY_SPARSE: a chunk may end up to 512 bytes past its tile
  *     and 1536 kept tokens per tile are staged in shared memory;
- *   LX_WARP_GEOMETRY_DENSE: 1024 bytes and 1024 staged tokens, the rest of a
+ *   LX_WARP_GEOMETRY_DENSE: 2048 bytes and 768 staged tokens, the rest of a
  *     tile's tokens staged in global memory (for inputs whose certified
  *     bytes lie far apart, or with many kept tokens per tile);
  *   LX_WARP_GEOMETRY_AUTO (default): sparse for the first call on a token

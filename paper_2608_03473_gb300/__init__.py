@@ -329,7 +329,7 @@ LX_WARP_GEOMETRY_AUTO, LX_WARP_GEOMETRY_SPARSE, LX_WARP_GEOMETRY_DENSE = 0, 1, 2
 def lx_ctx_set_warp_geometry(ctx: Ctx, geometry: int) -> int:
     """The warp-tile kernel's geometry: LX_WARP_GEOMETRY_AUTO (chosen from the
     previous call on the same token set and mode), _SPARSE (512-byte halo,
-    1536 staged tokens) or _DENSE (1024 and 1024, the rest staged in global
+    1536 staged tokens) or _DENSE (2048 and 768, the rest staged in global
     memory)."""
     return load_library().lx_ctx_set_warp_geometry(ctx.handle, int(geometry))
 

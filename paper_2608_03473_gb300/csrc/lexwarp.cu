@@ -58,20 +58,20 @@ constexpr uint32_t BLK = 16;                  // bytes per lockstep step of a la
 constexpr uint32_t NB1 = SLICE / BLK;         // phase-1 steps
 // A warp's geometry.  Sparse (the default): a chunk may end up to 512
 // positions past its tile and 1 536 kept tokens are staged in shared memory.
-// Dense: 1 024 positions (certified bytes far apart) and 1 024 staged tokens,
-// a tile's further tokens going to the warp's spill slot in global memory
-// (many kept tokens per tile), so that as many warps fit.
+// Dense: 2 048 positions (certified bytes far apart) and 768 staged tokens, a
+// tile's further tokens going to the warp's spill slot in global memory (many
+// kept tokens per tile), so that as many warps fit.
 // Event code of position p at ev + p + 4 (p >> 7): a 4-byte pad after every
 // 128 positions, so the 32 lanes' phase-1 stores (slices 128 positions
 // apart) fall in 32 different banks.
 template <int FORM>
 struct Geo {
     static constexpr bool dense = (FORM & DENSE) != 0;
-    static constexpr uint32_t HALO = dense ? 1024 : 512;   // positions past the tile a chunk may end at
+    static constexpr uint32_t HALO = dense ? 2048 : 512;   // positions past the tile a chunk may end at
     static constexpr uint32_t EVB = WT + HALO;             // event buffer positions
     static constexpr uint32_t LIMIT = EVB - BLK;           // chunk ends must lie below (room for the last block)
     static constexpr uint32_t EV_BYTES = ((EVB + 16 + 4 * ((EVB + 16) / 128 + 1)) + 15) / 16 * 16;
-    static constexpr uint32_t STAGE_CAP = dense ? 1024 : 1536;   // kept tokens per tile staged for coalesced writes
+    static constexpr uint32_t STAGE_CAP = dense ? 768 : 1536;   // kept tokens per tile staged for coalesced writes
     static constexpr uint32_t WAREA = EV_BYTES + 4 * STAGE_CAP;  // shared bytes per warp
 };
 constexpr uint32_t SPARSE_LIMIT = Geo<0>::LIMIT;

@@ -2,8 +2,8 @@
 codes in the walk table) against the oracle and against the tile kernel,
 element by element, through the C ABI.
 
-Both geometries (sparse: 512-byte halo, 1536 staged tokens; dense: 1024 and
-1024, the rest of a tile's tokens in the warp's global spill slot) on every
+Both geometries (sparse: 512-byte halo, 1536 staged tokens; dense: 2048 and
+768, the rest of a tile's tokens in the warp's global spill slot) on every
 case, and the automatic choice between them on repeated calls.
 
 Cases: every token set and mode on seeded corpora at ragged sizes; lexing
@@ -102,7 +102,7 @@ def test_corpora_ragged(env, name, mode):
     gen = "clike" if name == "clike_row1" else name
     base = corpus.generate(gen, 3 << 20, seed=101)
     for n in (1, 15, 16, 17, 127, 128, 129, 191, 192, 193, WT - 1, WT, WT + 1, WT + 495, WT + 496, WT + 497,
-              WT + 511, WT + 512, WT + 513, WT + 1007, WT + 1008, WT + 1009, WT + 1024, 3 * WT + 77, 100_003,
+              WT + 511, WT + 512, WT + 513, WT + 2031, WT + 2032, WT + 2033, WT + 2048, 3 * WT + 77, 100_003,
               base.size):
         check(env, name, base[:n], mode, both=n == base.size)
 
