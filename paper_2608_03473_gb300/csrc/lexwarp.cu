@@ -713,18 +713,64 @@ __device__ void report_failure(const WParams &P, uint32_t tile, uint64_t fail, u
 
 // The staged tokens of a tile to the output from index G, coalesced: the
 // first `split` from the shared stage, the rest from the warp's spill slot;
-// kmap_s: the kind map of the tile's token set.
+// kmap_s: the kind map of the tile's token set.  Each lane writes V
+// consecutive tokens at a time (kinds as one 2V-byte store, lengths as one
+// 4V-byte store) from the first index where G + i is a multiple of V, when
+// the output arrays are aligned for it and the capacity does not cut the
+// tile; the tokens before and after those groups, and every token otherwise,
+// one by one.  V = 2 for the sparse geometry, 4 for the dense one (measured).
+template <uint32_t V>
 __device__ void copy_stage(const WParams &P, uint32_t kmap_s, uint32_t stage, const uint32_t *spill, uint32_t split,
                            uint32_t staged, uint64_t G)
 {
-    for (uint32_t i = threadIdx.x & 31; i < staged; i += 32) {
+    static_assert(V == 2 || V == 4, "group size");
+    const uint32_t lane = threadIdx.x & 31;
+    auto val = [&](uint32_t i) { return i < split ? lds_u32(stage + 4 * i) : spill[i - split]; };
+    auto one = [&](uint32_t i) {
         const uint64_t o = G + i;
         if (o < P.cap) {
-            const uint32_t v = i < split ? lds_u32(stage + 4 * i) : spill[i - split];
+            const uint32_t v = val(i);
             P.out_kinds[o] = (uint16_t)lds_u16(kmap_s + (v >> 16));
             P.out_lens[o] = v & 0xFFFFu;
         }
+    };
+    const bool aligned = ((reinterpret_cast<uintptr_t>(P.out_kinds) & (2 * V - 1)) |
+                          (reinterpret_cast<uintptr_t>(P.out_lens) & (4 * V - 1))) == 0;
+    if (!aligned || G + staged > P.cap) {
+        for (uint32_t i = lane; i < staged; i += 32) one(i);
+        return;
     }
+    const uint32_t h = min((uint32_t)((V - (G & (V - 1))) & (V - 1)), staged);   // tokens before the first group
+    if (lane < h) one(lane);
+    const uint32_t ng = (staged - h) / V;
+    for (uint32_t q = lane; q < ng; q += 32) {
+        const uint32_t i = h + V * q;
+        const uint64_t o = G + i;
+        if (V == 2) {
+            const uint32_t v0 = val(i), v1 = val(i + 1);
+            const uint32_t k0 = lds_u16(kmap_s + (v0 >> 16)), k1 = lds_u16(kmap_s + (v1 >> 16));
+            *reinterpret_cast<uint32_t *>(P.out_kinds + o) = k0 | (k1 << 16);
+            *reinterpret_cast<uint2 *>(P.out_lens + o) = make_uint2(v0 & 0xFFFFu, v1 & 0xFFFFu);
+        } else {
+            uint32_t v0, v1, v2, v3;
+            if (i + 4 <= split && ((stage + 4 * i) & 15u) == 0) {
+                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(v0), "=r"(v1), "=r"(v2), "=r"(v3) : "r"(stage + 4 * i));
+            } else {
+                v0 = val(i);
+                v1 = val(i + 1);
+                v2 = val(i + 2);
+                v3 = val(i + 3);
+            }
+            const uint32_t k0 = lds_u16(kmap_s + (v0 >> 16)), k1 = lds_u16(kmap_s + (v1 >> 16));
+            const uint32_t k2 = lds_u16(kmap_s + (v2 >> 16)), k3 = lds_u16(kmap_s + (v3 >> 16));
+            *reinterpret_cast<uint2 *>(P.out_kinds + o) = make_uint2(k0 | (k1 << 16), k2 | (k3 << 16));
+            *reinterpret_cast<uint4 *>(P.out_lens + o) =
+                make_uint4(v0 & 0xFFFFu, v1 & 0xFFFFu, v2 & 0xFFFFu, v3 & 0xFFFFu);
+        }
+    }
+    const uint32_t t = h + V * ng;   // the last tokens, fewer than V
+    if (lane < staged - t) one(t + lane);
 }
 
 __device__ __forceinline__ uint4 blk_at(const WEnv &E, uint32_t q)
@@ -1025,7 +1071,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             uint64_t G = 0;
             if (!resolve_tile(P, pend.tile, G)) break;
             report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
-            copy_stage(P, pend.kmap_s, stage, spill, dense ? pend.staged >> 16 : STAGE_CAP,
+            copy_stage<dense ? 4 : 2>(P, pend.kmap_s, stage, spill, dense ? pend.staged >> 16 : STAGE_CAP,
                        dense ? pend.staged & 0xFFFFu : pend.staged, G);
             pend.tile = NONE;
             __syncwarp();
@@ -1116,7 +1162,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
             pend.dtile = dtile;
             pend.kmap_s = E.kmap_s;
         } else {
-            copy_stage(P, E.kmap_s, stage, spill, split, fast_total, G);
+            copy_stage<dense ? 4 : 2>(P, E.kmap_s, stage, spill, split, fast_total, G);
             if (do_long && lane == 0) {
                 uint64_t f2;
                 generic_chunk<FORM>(E, long_s1 - 1, &f2, P.out_kinds, P.out_lens, P.cap, G + fast_total);
@@ -1128,7 +1174,7 @@ __global__ void __launch_bounds__(32 * MAX_WARPS, 1) lex_warps(WParams P)
         uint64_t G = 0;
         if (resolve_tile(P, pend.tile, G)) {
             report_failure<BATCH>(P, pend.tile, pend.fail, G, pend.agg, pend.doc, pend.dtile);
-            copy_stage(P, pend.kmap_s, stage, spill, dense ? pend.staged >> 16 : STAGE_CAP,
+            copy_stage<dense ? 4 : 2>(P, pend.kmap_s, stage, spill, dense ? pend.staged >> 16 : STAGE_CAP,
                        dense ? pend.staged & 0xFFFFu : pend.staged, G);
         }
     }

@@ -230,3 +230,24 @@ def test_geometry_setting_and_auto(env):
         for _ in range(3):
             rc, nt, con, k, l = run(lg, auto, name, w, mode)
             assert rc == 0 and con == econ and np.array_equal(k, ek) and np.array_equal(l, el)
+
+
+def test_output_alignment(env):
+    # the output arrays at offsets 1-4 elements: tokens are written in groups
+    # of 2 (sparse) or 4 (dense) where the arrays are aligned for it, one by
+    # one otherwise
+    import torch
+    lg, warp, tile, dense = env
+    for name, mode in (("json", 2), ("clike", 0)):
+        w = corpus.generate(name, 3 * WT * 7 + 333, seed=108)
+        ek, el, econ = expected(name, w, mode)
+        d = torch.from_numpy(w.copy()).cuda()
+        for ctx in (warp, dense):
+            for off in (1, 2, 3, 4):
+                k = torch.zeros(ek.size + 8, dtype=torch.int16, device="cuda")
+                l = torch.zeros(ek.size + 8, dtype=torch.int32, device="cuda")
+                rc, nt, con = lg.lx_lex(ctx, tokenset(lg, name), d, mode, k[off:], l[off:], capacity=ek.size + 8 - off)
+                assert rc == 0 and nt == ek.size and con == econ
+                assert np.array_equal(k[off:off + nt].cpu().numpy().view(np.uint16).astype(np.int64), ek)
+                assert np.array_equal(l[off:off + nt].cpu().numpy().view(np.uint32).astype(np.int64), el)
+                assert not k[:off].any() and not l[:off].any() and not k[off + nt:].any()
