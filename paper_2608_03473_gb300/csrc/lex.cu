@@ -1517,27 +1517,35 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
     rc = grow(&c->d_in, &c->d_in_bytes, n);
     if (rc == LX_OK) rc = grow(&c->d_out, &c->d_out_bytes, capacity ? capacity * 6 + 16 : 16);
     if (rc != LX_OK) return rc;
-    uint32_t *d_lens = static_cast<uint32_t *>(c->d_out);
-    uint16_t *d_kinds = reinterpret_cast<uint16_t *>(d_lens + capacity);
-    const uint8_t *d_in = static_cast<const uint8_t *>(c->d_in);
     cudaStream_t st0 = static_cast<cudaStream_t>(stream);
-    if (c->kernel == LX_KERNEL_AUTO && ts->scan.status == LX_OK && !mode_has_cuts(ts, mode)) {
-        // no certified byte: the whole input in, the enumerative path, the tokens out
-        rc = cuda_err(cudaMemcpyAsync(c->d_in, h_in, n, cudaMemcpyHostToDevice, st0));
-        if (rc != LX_OK) return rc;
+    // the whole input in, one device-side call, the tokens out
+    auto whole = [&](bool enumerate) -> int {
+        int r = grow(&c->d_in, &c->d_in_bytes, n);
+        if (r == LX_OK) r = grow(&c->d_out, &c->d_out_bytes, capacity ? capacity * 6 + 16 : 16);
+        if (r == LX_OK) r = cuda_err(cudaMemcpyAsync(c->d_in, h_in, n, cudaMemcpyHostToDevice, st0));
+        if (r != LX_OK) return r;
+        uint32_t *dl = static_cast<uint32_t *>(c->d_out);
+        uint16_t *dk = reinterpret_cast<uint16_t *>(dl + capacity);
+        const uint8_t *di = static_cast<const uint8_t *>(c->d_in);
         uint64_t nt = 0, con = 0;
-        rc = lx_lex_enumerative(c, ts, d_in, n, mode, d_kinds, d_lens, capacity, &nt, &con, stream);
-        if (rc != LX_OK && rc != LX_E_CAPACITY) return rc;
+        r = enumerate ? lx_lex_enumerative(c, ts, di, n, mode, dk, dl, capacity, &nt, &con, stream)
+                      : lex_device(c, ts, di, n, mode, dk, dl, capacity, &nt, &con, st0);
+        if (r != LX_OK && r != LX_E_CAPACITY) return r;
         const uint64_t m = std::min(nt, capacity);
         int r2 = LX_OK;
-        if (m) r2 = cuda_err(cudaMemcpyAsync(h_kinds, d_kinds, 2 * m, cudaMemcpyDeviceToHost, st0));
-        if (m && r2 == LX_OK) r2 = cuda_err(cudaMemcpyAsync(h_lens, d_lens, 4 * m, cudaMemcpyDeviceToHost, st0));
+        if (m) r2 = cuda_err(cudaMemcpyAsync(h_kinds, dk, 2 * m, cudaMemcpyDeviceToHost, st0));
+        if (m && r2 == LX_OK) r2 = cuda_err(cudaMemcpyAsync(h_lens, dl, 4 * m, cudaMemcpyDeviceToHost, st0));
         if (r2 == LX_OK) r2 = cuda_err(cudaStreamSynchronize(st0));
         if (r2 != LX_OK) return r2;
         *n_tokens = nt;
         *consumed = con;
-        return rc;
-    }
+        return r;
+    };
+    // the warp-tile kernel where it applies (it also cuts at certified windows)
+    const bool warp = c->kernel != LX_KERNEL_TILE && ts->walk[mode].status == LX_OK;
+    const bool can_enumerate = c->kernel == LX_KERNEL_AUTO && ts->scan.status == LX_OK;
+    if (can_enumerate && !(warp ? warp_has_cuts(ts, mode) : mode_has_cuts(ts, mode)))
+        return whole(true);   // no certified byte: the enumerative path
 
     const std::vector<uint64_t> b = host_pieces(h, h_in, n);
     const uint32_t K = (uint32_t)b.size() - 1;
@@ -1552,6 +1560,17 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
         c->ev_in.push_back(e1);
         c->ev_lex.push_back(e2);
     }
+    if (warp) {
+        rc = lex_warp_host(c, ts, h_in, n, mode, h_kinds, h_lens, capacity, b.data(), K, n_tokens, consumed, st,
+                           can_enumerate ? SPARSE_LIMIT : 0);
+        if (rc != LX_SPARSE && rc != LX_LOOKAHEAD) return rc;
+        // certified bytes too far apart, or failed lookahead, in some piece:
+        // the whole input through lx_lex's plan
+        return whole(false);
+    }
+    uint32_t *d_lens = static_cast<uint32_t *>(c->d_out);
+    uint16_t *d_kinds = reinterpret_cast<uint16_t *>(d_lens + capacity);
+    const uint8_t *d_in = static_cast<const uint8_t *>(c->d_in);
 
     // scratch: one record + tile counter per piece, status words, spill regions
     const Layout L = make_layout((uint32_t)h.blob.size(), g.ks);

@@ -1459,6 +1459,125 @@ int lex_warp_async(lx_ctx *c, const lx_tokenset *ts, const uint8_t *d_in, uint64
 }
 
 // ---------------------------------------------------------------------------
+// host buffers: pieces copied in, lexed and copied out in a pipeline
+// ---------------------------------------------------------------------------
+namespace {
+
+// A launch record into pinned host memory by a one-warp kernel rather than a
+// device-to-host copy, which would queue on the copy engine behind the
+// previous piece's tokens.
+__global__ void copy_wrecord(const WResult *src, WResult *dst)
+{
+    if (threadIdx.x < sizeof(WResult) / 8)
+        reinterpret_cast<volatile unsigned long long *>(dst)[threadIdx.x] =
+            reinterpret_cast<const volatile unsigned long long *>(src)[threadIdx.x];
+}
+
+}  // namespace
+
+int lex_warp_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in, uint64_t n, int mode, uint16_t *h_kinds,
+                  uint32_t *h_lens, uint64_t capacity, const uint64_t *b, uint32_t K, uint64_t *n_tokens,
+                  uint64_t *consumed, cudaStream_t st, uint64_t sparse_limit)
+{
+    auto al = [](uint64_t x, uint64_t a) { return (x + a - 1) / a * a; };
+    // device layout: piece i's bytes at a 16-byte aligned offset; its tokens
+    // (at most one per byte) in its own output range, 4-token aligned
+    std::vector<uint64_t> in_off(K), out_off(K), cap(K);
+    uint64_t in_total = 0, out_total = 0, largest = 0;
+    uint32_t big = 0;
+    for (uint32_t i = 0; i < K; i++) {
+        const uint64_t len = b[i + 1] - b[i];
+        in_off[i] = in_total;
+        in_total = al(in_total + len, 16);
+        cap[i] = al(len + 1, 4);
+        out_off[i] = out_total;
+        out_total += cap[i];
+        if (len > largest) largest = len, big = i;
+    }
+    int rc = grow(&c->d_in, &c->d_in_bytes, in_total + 16);
+    if (rc == LX_OK) rc = grow(&c->d_out, &c->d_out_bytes, 6 * out_total + 64);
+    if (rc == LX_OK) rc = grow_host(&c->h_scratch, &c->h_scratch_bytes, sizeof(WResult) * (size_t)K);
+    if (rc != LX_OK) return rc;
+    uint8_t *d_in = static_cast<uint8_t *>(c->d_in);
+    uint32_t *d_lens = static_cast<uint32_t *>(c->d_out);
+    uint16_t *d_kinds = reinterpret_cast<uint16_t *>(d_lens + out_total);
+    WResult *h_res = static_cast<WResult *>(c->h_scratch);
+    WResult *h_res_dev = nullptr;   // the same pinned records, as the device sees them
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&h_res_dev), c->h_scratch, 0) != cudaSuccess)
+        return LX_E_CUDA;
+    // the scratch and spill slots grow for the largest piece first: no
+    // reallocation once launches are queued
+    WarpLaunch L;
+    rc = warp_prepare(c, ts, d_in + in_off[big], largest, mode, d_kinds + out_off[big], d_lens + out_off[big],
+                      cap[big], sparse_limit, L);
+    if (rc != LX_OK) return rc;
+    const bool dense = L.dense;
+    // the pieces in, each on its own event
+    for (uint32_t i = 0; i < K; i++) {
+        rc = cuda_err(cudaMemcpyAsync(d_in + in_off[i], h_in + b[i], b[i + 1] - b[i], cudaMemcpyHostToDevice, c->s_in));
+        if (rc == LX_OK) rc = cuda_err(cudaEventRecord(c->ev_in[i], c->s_in));
+        if (rc != LX_OK) return rc;
+    }
+    // the launches, in order on the caller's stream (one scratch, reused)
+    if (c->timing) cudaEventRecord(c->ev[0], st);
+    for (uint32_t i = 0; i < K; i++) {
+        rc = warp_prepare(c, ts, d_in + in_off[i], b[i + 1] - b[i], mode, d_kinds + out_off[i], d_lens + out_off[i],
+                          cap[i], sparse_limit, L);
+        if (rc == LX_OK && L.dense != dense) rc = LX_E_CUDA;   // one geometry per call
+        if (rc == LX_OK) rc = cuda_err(cudaStreamWaitEvent(st, c->ev_in[i], 0));
+        if (rc == LX_OK) rc = cuda_err(cudaMemsetAsync(c->scratch, 0, L.need, st));
+        if (rc != LX_OK) return rc;
+        warp_launch(L, st);
+        copy_wrecord<<<1, 32, 0, st>>>(L.P.res, h_res_dev + i);
+        rc = cuda_err(cudaGetLastError());
+        if (rc == LX_OK) rc = cuda_err(cudaEventRecord(c->ev_lex[i], st));
+        if (rc != LX_OK) return rc;
+    }
+    if (c->timing) cudaEventRecord(c->ev[1], st);
+    // each piece's tokens out as soon as it is lexed, after the previous pieces'
+    uint64_t out = 0, con = n, tokens = 0, n_tiles = 0;
+    uint32_t long_tiles = 0;
+    bool failed = false;
+    for (uint32_t i = 0; i < K && !failed && rc == LX_OK; i++) {
+        rc = cuda_err(cudaEventSynchronize(c->ev_lex[i]));
+        if (rc != LX_OK) break;
+        const WResult r = h_res[i];
+        if (r.error & ERR_LOOKAHEAD) rc = LX_LOOKAHEAD;   // the caller lexes the input another way
+        else if (r.error & ERR_SPARSE) rc = LX_SPARSE;
+        else if (r.error & ERR_TIMEOUT) rc = LX_E_TIMEOUT;
+        else if (r.error) rc = LX_E_TOOBIG;
+        if (rc != LX_OK) break;
+        uint64_t m = r.total;
+        if (r.inv_fail_pos) {   // Corollary 1: the first failing piece ends the stream
+            m = ~r.inv_fail_tok;
+            con = b[i] + ~r.inv_fail_pos;
+            failed = true;
+        }
+        const uint64_t lo = std::min(out, capacity), hi = std::min(out + m, capacity);
+        if (hi > lo) {
+            rc = cuda_err(cudaMemcpyAsync(h_kinds + lo, d_kinds + out_off[i], (hi - lo) * 2, cudaMemcpyDeviceToHost,
+                                          c->s_out));
+            if (rc == LX_OK)
+                rc = cuda_err(cudaMemcpyAsync(h_lens + lo, d_lens + out_off[i], (hi - lo) * 4,
+                                              cudaMemcpyDeviceToHost, c->s_out));
+        }
+        out += m;
+        tokens += r.total;
+        n_tiles += (b[i + 1] - b[i] + WT - 1) / WT;
+        long_tiles += r.long_tiles;
+    }
+    int r2 = cuda_err(cudaStreamSynchronize(c->s_out));
+    if (rc == LX_OK) rc = r2;
+    r2 = cuda_err(cudaStreamSynchronize(st));
+    if (rc == LX_OK) rc = r2;
+    if (rc != LX_OK) return rc;
+    if (!failed && c->warp_geometry == LX_WARP_GEOMETRY_AUTO) note_geometry(c, ts, mode, tokens, n_tiles, long_tiles);
+    *n_tokens = out;
+    *consumed = con;
+    return out > capacity ? LX_E_CAPACITY : LX_OK;
+}
+
+// ---------------------------------------------------------------------------
 // batches: every document of every token set in one launch
 // ---------------------------------------------------------------------------
 namespace {

@@ -85,6 +85,17 @@ struct lx_ctx {
 
 namespace lx {
 
+// lx_lex_host on the warp-tile kernel (lexwarp.cu): the K pieces [b[i],
+// b[i+1]) of the host input (cut at certified bytes) each copied to a
+// 16-byte aligned place on the device, lexed by their own launch with their
+// own output range, and their tokens copied out after the previous pieces'
+// once their records are in (same contract as lx_lex_host).  Uses the
+// context's s_in / s_out streams and K of its ev_in / ev_lex events.  With
+// sparse_limit != 0, LX_SPARSE or LX_LOOKAHEAD as lex_warp_device (some
+// piece stopped early; the host buffers then hold nothing defined).
+int lex_warp_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in, uint64_t n, int mode, uint16_t *h_kinds,
+                  uint32_t *h_lens, uint64_t capacity, const uint64_t *b, uint32_t K, uint64_t *n_tokens,
+                  uint64_t *consumed, cudaStream_t st, uint64_t sparse_limit);
 // LX_OK, LX_E_NOMEM for an allocation failure, LX_E_CUDA otherwise.
 int cuda_err(cudaError_t e);
 // Grow a device (grow) or pinned host (grow_host) buffer to at least `need`

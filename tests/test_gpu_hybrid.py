@@ -108,3 +108,18 @@ def test_lex_host_without_certified_byte(env):
     assert rc == 0 and con == econ and nt == ek.size
     assert np.array_equal(k[:nt].view(np.uint16).astype(np.int64), ek)
     assert np.array_equal(l[:nt].view(np.uint32).astype(np.int64), el)
+
+
+def test_lex_host_sparse_cuts_hand_over(env):
+    # minified JSON through lx_lex_host: the warp kernel stops at the sparse
+    # limit and the call takes the whole input through lx_lex's plan
+    lg, ts = env
+    ctx = lg.lx_ctx_create()
+    w = minified(3 << 20, 206)
+    k = np.zeros(w.size + 1, np.int16)
+    l = np.zeros(w.size + 1, np.int32)
+    rc, nt, con = lg.lx_lex_host(ctx, ts, w, lg.LX_FILTERED_MODULO, k, l)
+    ek, el, econ = expected(w, 2)
+    assert rc == 0 and con == econ and nt == ek.size
+    assert np.array_equal(k[:nt].view(np.uint16).astype(np.int64), ek)
+    assert np.array_equal(l[:nt].view(np.uint32).astype(np.int64), el)

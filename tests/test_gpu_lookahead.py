@@ -222,3 +222,29 @@ def test_unterminated_string(env):
         for fn in (lg.lx_lex, lg.lx_lex_enumerative):
             rc, nt, con, k, l, dt = run(lg, fn, ctx, ts, w, mode)
             assert rc == 0 and con == econ == cut and np.array_equal(k, ek) and np.array_equal(l, el), (mode, fn)
+
+
+def test_host_path_hands_over(env):
+    # lx_lex_host: a piece whose warp-kernel launch runs past its step budget
+    # ((a^k ;)^m) or past the sparse limit (a^n: no certified byte occurs)
+    # makes the call lex the whole input through lx_lex's guarded plan
+    lg, ctx = env
+    ts = tokenset(lg, "lookahead")
+    dfa = T.tokenset("lookahead")
+    w = (b"a" * 1000 + b";") * 1000
+    ek, el, econ = oracle.lex(dfa, w)
+    arr = np.frombuffer(w, np.uint8).copy()
+    hk = np.zeros(arr.size + 1, np.int16)
+    hl = np.zeros(arr.size + 1, np.int32)
+    rc, nt, con = lg.lx_lex_host(ctx, ts, arr, 0, hk, hl)
+    assert rc == 0 and con == econ and nt == ek.size
+    assert np.array_equal(hk[:nt].view(np.uint16).astype(np.int64), ek)
+    assert np.array_equal(hl[:nt].view(np.uint32).astype(np.int64), el)
+    n = 1_000_000
+    arr = np.full(n, ord("a"), np.uint8)
+    hk = np.zeros(n + 1, np.int16)
+    hl = np.zeros(n + 1, np.int32)
+    t0 = time.perf_counter()
+    rc, nt, con = lg.lx_lex_host(ctx, ts, arr, 0, hk, hl)
+    assert rc == 0 and nt == n and con == n and time.perf_counter() - t0 < 10.0
+    assert (hk[:n] == dfa.kind_id("a")).all() and (hl[:n] == 1).all()

@@ -245,14 +245,20 @@ def test_long_ranges_noalloc(gpu):
     assert np.array_equal(l[:nt].cpu().numpy().view(np.uint32).astype(np.int64), el)
 
 
+@pytest.mark.parametrize("kernel", ["warp", "tile"])
 @pytest.mark.parametrize("name,size", [("json", 96 << 20), ("clike", 130 << 20)])
-def test_lex_host_pieces(gpu, name, size):
+def test_lex_host_pieces(gpu, name, size, kernel):
     """Inputs of 64 MiB and more go through lx_lex_host in pieces split at
-    certified bytes on the host (copies overlapping the lexing): the stream
+    certified bytes on the host (copies overlapping the lexing; each piece
+    at a 16-byte aligned place with its own output range on the warp-tile
+    kernel, in one input and output array on the tile kernel): the stream
     must be the same, including a failure inside a later piece and the
     capacity protocol."""
     import torch
-    lg, ctx = gpu
+    lg, _ = gpu
+    ctx = lg.lx_ctx_create()
+    if kernel == "tile":
+        assert lg.lx_ctx_set_kernel(ctx, lg.LX_KERNEL_TILE) == 0
     ts = tokenset(lg, name)
     w = corpus.generate(name, size, seed=14)
     hk = torch.zeros(size // 2, dtype=torch.int16).pin_memory()

@@ -251,3 +251,19 @@ def test_output_alignment(env):
                 assert np.array_equal(k[off:off + nt].cpu().numpy().view(np.uint16).astype(np.int64), ek)
                 assert np.array_equal(l[off:off + nt].cpu().numpy().view(np.uint32).astype(np.int64), el)
                 assert not k[:off].any() and not l[:off].any() and not k[off + nt:].any()
+
+
+def test_host_pieces_both_geometries(env):
+    # full-mode C-like through lx_lex_host in pieces: the first call sparse,
+    # the next dense (about 1 850 kept tokens per tile), both the oracle's
+    lg = env[0]
+    ctx = lg.lx_ctx_create()
+    w = corpus.generate("clike", (70 << 20) + 13, seed=109)
+    ek, el, econ = expected("clike", w, 0)
+    for _ in range(2):
+        hk = np.zeros(ek.size + 1, np.int16)
+        hl = np.zeros(ek.size + 1, np.int32)
+        rc, nt, con = lg.lx_lex_host(ctx, tokenset(lg, "clike"), w, 0, hk, hl)
+        assert rc == 0 and con == econ and nt == ek.size
+        assert np.array_equal(hk[:nt].view(np.uint16).astype(np.int64), ek)
+        assert np.array_equal(hl[:nt].view(np.uint32).astype(np.int64), el)
