@@ -259,7 +259,7 @@ int lx_ctx_last_kernel_ms(lx_ctx *ctx, float *ms);
  *   LX_KERNEL_WARP: always the warp-tile kernel; lx_lex returns LX_E_INVAL
  *     for a call it cannot serve.
  * Both produce the same stream (tests compare them).  Returns LX_E_INVAL
- * for another value.  lx_lex_host always uses the tile kernel; lx_lex_batch
+ * for another value.  lx_lex_host follows the same choice; lx_lex_batch
  * takes the one-launch warp-tile batch unless LX_KERNEL_TILE is set.
  */
 #define LX_KERNEL_AUTO 0
@@ -370,8 +370,13 @@ int lx_lex_async(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *d_in, uint64
  * lx_lex.  Inputs of 64 MiB or more with a non-empty cut set are split on the
  * host into up to 8 pieces at certified bytes (the planner of Section 6) and
  * piece copies overlap the lexing of other pieces (two context-owned copy
- * streams; the launches run in order on `stream`).  Host buffers should be
- * pinned for full copy speed.  Returns after all copies have completed.
+ * streams; the launches run in order on `stream`).  On the warp-tile kernel
+ * each piece is copied to a 16-byte aligned place and lexed into its own
+ * output range, and its tokens are copied out behind the previous pieces';
+ * if some piece's certified bytes lie too far apart, or its backtracking
+ * runs past the step budget (failed lookahead), the whole input is copied
+ * in again and lexed by lx_lex's plan.  Host buffers should be pinned for
+ * full copy speed.  Returns after all copies have completed.
  */
 int lx_lex_host(lx_ctx *ctx, const lx_tokenset *ts, const uint8_t *h_in, uint64_t n, int mode,
                 uint16_t *h_kinds, uint32_t *h_lens, uint64_t capacity, uint64_t *n_tokens,
