@@ -507,3 +507,59 @@ def test_window_rows(lg, name, mode):
         k = int(W.ctx[a])
         if k:
             assert np.array_equal(W.cuts[k], pairs[a] | single)
+
+
+@pytest.mark.parametrize("name,mode", [("json", 2), ("clike", 0)])
+def test_model_dense_geometry(lg, name, mode):
+    # the dense geometry's 2048-position halo: lines of 600-1500 bytes leave
+    # the sparse halo but end inside this one
+    rng = random.Random(14)
+    base = corpus.generate(name, 3 * 6144, seed=15).tobytes()
+    filler = b'"' + b"q" * 20 + b'"' if name == "json" else b"x" * 20
+    long_lines = b"".join((b"[" + filler * rng.randint(30, 70) + b"]\n") if name == "json"
+                          else (filler * rng.randint(30, 70) + b";\n") for _ in range(12))
+    w = np.frombuffer(base[:7000] + long_lines + base[7000:], np.uint8)
+    got, con = model_lex(lg, name, mode, w, wt=6144, halo=2048)
+    want, econ = expected(name, mode, w)
+    assert con == econ and got == want
+
+
+def stage_split(counts, cap):
+    """The dense emission's placement: lanes whose codes all fit the stage
+    (a prefix, since the inclusive counts ascend) write it from their
+    exclusive prefix, the others the spill slot from the first misfit lane's
+    prefix on.  Returns (split, [(lane, 'stage'|'spill', first index)])."""
+    excl = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(int)
+    fit = int(np.sum(excl + np.asarray(counts) <= cap))
+    total = int(np.sum(counts))
+    split = total if fit == len(counts) else int(excl[fit])
+    return split, [(i, "stage" if i < fit else "spill", int(excl[i]) if i < fit else int(excl[i]) - split)
+                   for i in range(len(counts))]
+
+
+def test_stage_split_and_copy_groups():
+    rng = random.Random(16)
+    for _ in range(400):
+        cap = rng.choice([768, 1536])
+        counts = [rng.choice([0, rng.randint(0, 30), rng.randint(0, 200)]) for _ in range(32)]
+        total = sum(counts)
+        split, place = stage_split(counts, cap)
+        assert split <= cap and split <= total
+        stage, spill = {}, {}
+        for (lane, where, first), c in zip(place, counts):
+            for k in range(c):
+                (stage if where == "stage" else spill)[first + k] = (lane, k)
+        assert max(stage, default=-1) < cap and len(stage) == split and len(spill) == total - split
+        # the copy reads stage[0:split] then spill[0:total-split]: every token once, in lane order
+        order = [stage[i] for i in range(split)] + [spill[i] for i in range(total - split)]
+        assert order == [(lane, k) for lane in range(32) for k in range(counts[lane])]
+    # copy groups: the lanes' groups of V, the tokens before and after them, cover [0, staged) once
+    for V in (2, 4):
+        for G in range(0, 9):
+            for staged in range(0, 200):
+                h = min((V - (G & (V - 1))) & (V - 1), staged)
+                ng = (staged - h) // V
+                t = h + V * ng
+                cover = list(range(h)) + [h + V * q + j for q in range(ng) for j in range(V)] + list(range(t, staged))
+                assert sorted(cover) == list(range(staged)) and staged - t < V
+                assert all((G + h + V * q) % V == 0 for q in range(ng))
