@@ -1543,6 +1543,7 @@ extern "C" int lx_lex_host(lx_ctx *c, const lx_tokenset *ts, const uint8_t *h_in
     };
     // the warp-tile kernel where it applies (it also cuts at certified windows)
     const bool warp = c->kernel != LX_KERNEL_TILE && ts->walk[mode].status == LX_OK;
+    if (c->kernel == LX_KERNEL_WARP && !warp) return LX_E_INVAL;   // as lx_lex: asked for a kernel that cannot serve
     const bool can_enumerate = c->kernel == LX_KERNEL_AUTO && ts->scan.status == LX_OK;
     if (can_enumerate && !(warp ? warp_has_cuts(ts, mode) : mode_has_cuts(ts, mode)))
         return whole(true);   // no certified byte: the enumerative path
