@@ -1185,9 +1185,8 @@ int lx::grow(void **p, size_t *have, size_t need)
     if (*p) cudaFree(*p);
     *p = nullptr;
     *have = 0;
-    size_t sz = std::max(need, *have * 2);
-    int rc = cuda_err(cudaMalloc(p, sz));
-    if (rc == LX_OK) *have = sz;
+    int rc = cuda_err(cudaMalloc(p, need));   // exactly what is asked: buffers are sized per call
+    if (rc == LX_OK) *have = need;
     return rc;
 }
 
