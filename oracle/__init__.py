@@ -66,21 +66,26 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(lib):
+    """Declare the C signatures on a loaded liblexoracle (also used by the
+    mutation tests, which load deliberately broken copies)."""
+    i32, i64, p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    lib.orc_lex.restype = i64
+    lib.orc_lex.argtypes = [i32, i32, p, p, p, i64, p, p, i64, p]
+    lib.orc_filter.restype = i64
+    lib.orc_filter.argtypes = [p, p, i64, p, i32, p, p]
+    lib.orc_certificates.restype = ctypes.c_int
+    lib.orc_certificates.argtypes = [i32, i32, p, p, p, i32, p, p, p, p, p, p]
+    lib.par_lex.restype = i64
+    lib.par_lex.argtypes = [i32, p, p, p, p, i32, p, i64, i32, p, p, i64, p, p, p]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            i32, i64, p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
-            lib.orc_lex.restype = i64
-            lib.orc_lex.argtypes = [i32, i32, p, p, p, i64, p, p, i64, p]
-            lib.orc_filter.restype = i64
-            lib.orc_filter.argtypes = [p, p, i64, p, i32, p, p]
-            lib.orc_certificates.restype = ctypes.c_int
-            lib.orc_certificates.argtypes = [i32, i32, p, p, p, i32, p, p, p, p, p, p]
-            lib.par_lex.restype = i64
-            lib.par_lex.argtypes = [i32, p, p, p, p, i32, p, i64, i32, p, p, i64, p, p, p]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
 
 

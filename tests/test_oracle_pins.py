@@ -169,11 +169,66 @@ def test_conservativeness_witness():
             assert list(a[0]) == list(b[0]) and list(a[1]) == list(b[1])
 
 
+def _every_cut_keeps_pi_I(dfa, I, alphabet, byte, max_len):
+    """Bounded soundness: on every string over `alphabet` up to `max_len` bytes,
+    the chunked scan cut before every occurrence of `byte` gives pi_I of the
+    serial scan and the same consumed length (Theorem 3 and Corollary 1)."""
+    import itertools
+    nk = dfa.n_kinds
+    for L in range(1, max_len + 1):
+        for t in itertools.product(alphabet, repeat=L):
+            w = bytes(t)
+            k, l, con = oracle.lex(dfa, w)
+            cuts = [i for i in range(1, con) if w[i] == byte]
+            k2, l2, con2 = oracle.lex_chunks(dfa, w[:con], cuts)
+            a, b = oracle.discard(k, l, I, nk), oracle.discard(k2, l2, I, nk)
+            if con2 != con or list(a[0]) != list(b[0]) or list(a[1]) != list(b[1]):
+                return w
+    return None
+
+
+def test_modulo_needs_an_accepting_state():
+    # Definition 3, C(q) asks for tau(q) defined: in the discarded token a?b+
+    # the state after 'a' is not accepting, goes to the same state on 'b' as
+    # q0 and reaches only discarded kinds, yet a cut before the 'b' of "ab"
+    # leaves the chunk "a", which does not lex
+    dfa = _compile(("d", "a?b+", 0), ("semi", ";", 0))
+    I = [dfa.kind_id("d")]
+    c = oracle.certificates(dfa, I)
+    assert not c.modulo[ord("b")]
+    assert oracle.lex(dfa, b"ab")[2] == 2 and oracle.lex_chunks(dfa, b"ab", [1])[2] == 0
+    assert _every_cut_keeps_pi_I(dfa, I, b"ab;", ord("b"), 6) == b"ab"
+
+
+def test_modulo_through_a_non_accepting_inner_state():
+    # Definition 3, T(q) collects the kinds of the ACCEPTING states reachable
+    # from q: whitespace with line continuations (runs of spaces and of a
+    # backslash followed by a newline) passes through the non-accepting state
+    # after the backslash, and ' ' is still certified modulo I = {ws} --
+    # soundly, by the bounded check
+    dfa = _compile(("x", "x+", 0), ("ws", "( |\\\\\n)+", 0))
+    delta = dfa.delta_full()
+    after_bs = [q for q in range(dfa.n_states) if q != dfa.q0 and delta[q, ord("\\")] >= 0]
+    assert after_bs and all(dfa.accept[delta[q, ord("\\")]] < 0 for q in after_bs)
+    I = [dfa.kind_id("ws")]
+    c = oracle.certificates(dfa, I)
+    assert not c.exact[ord(" ")]
+    assert c.modulo[ord(" ")]
+    assert _every_cut_keeps_pi_I(dfa, I, b"x \\\n", ord(" "), 6) is None
+
+
 def test_empty_discard_set_recovers_exact():
-    for name in ("arith", "json", "clike", "clike_row1", "utf8"):
-        c = oracle.certificates(T.tokenset(name), [])
+    # Section 5: with I empty no accepting state has T(q) inside I, so C(q)
+    # never holds and Definition 3 reduces to Definition 2 -- also when q0 is
+    # re-entrant, where A(q0) fails and the byte stays refused
+    sets = [(name, T.tokenset(name)) for name in ("arith", "json", "clike", "clike_row1", "utf8")]
+    sets += [("a*", _compile(("a", "a*", 0))), ("(ab)*c", _compile(("t", "(ab)*c", 0)))]
+    for name, dfa in sets:
+        c = oracle.certificates(dfa, [])
         assert np.array_equal(c.exact_raw, c.modulo_raw), name
         assert np.array_equal(c.exact, c.modulo), name
+    assert not oracle.certificates(sets[-2][1], []).modulo_raw[ord("a")]
+    assert not oracle.certificates(sets[-1][1], []).modulo_raw[ord("c")]
 
 
 # --- Section 8: re2c sentinel contrast ---------------------------------------------
