@@ -10,15 +10,23 @@ the oracle's fast pins: the worked examples of the paper
 (test_oracle_discard_plan.py) and the Python re.fullmatch cross-check
 (test_oracle_re.py).  At least one pin must fail.  The planner and the
 chunked run, which are Python, are replaced by mutated copies in the same
-way.  A control run with an unmutated copy passes every pin, so the failures
-come from the planted mistakes and not from the harness.  Nothing here runs
-on a GPU.
+way.  The Python parts of the oracle (entry contexts, live sets, split
+windows, the FP64 model) are mutated in their source text and loaded in place
+of the real module before their own pins are loaded.  A control run with an
+unmutated copy passes every pin, so the failures come from the planted
+mistakes and not from the harness.  Pins that compare the oracle with the
+product's host code (those that take the library fixture) are left out: a
+mistake must be caught by what fixes the oracle, not by the product.
+Nothing here runs on a GPU.
 """
 
 import ctypes
 import importlib.util
+import inspect
 import os
 import subprocess
+import sys
+import types
 from typing import List
 
 import numpy as np
@@ -27,6 +35,8 @@ import pytest
 import oracle
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)     # some pin modules import helpers from others
 PIN_MODULES = ("test_oracle_pins.py", "test_oracle_discard_plan.py", "test_oracle_re.py")
 
 
@@ -40,32 +50,39 @@ def _load_module(fname):
 PINS = [_load_module(f) for f in PIN_MODULES]
 
 
-def _pin_calls():
-    """Every pin test with its arguments (parametrize marks expanded)."""
-    for mod in PINS:
+def _pin_calls(mods):
+    """Every pin test of `mods` with its arguments (parametrize marks
+    expanded); tests that take fixtures are skipped."""
+    for mod in mods:
         for name in sorted(dir(mod)):
             if not name.startswith("test_"):
                 continue
             f = getattr(mod, name)
             marks = [m for m in getattr(f, "pytestmark", []) if m.name == "parametrize"]
+            params = list(inspect.signature(f).parameters)
             if not marks:
-                yield f"{mod.__name__}.{name}", f, ()
+                if not params:
+                    yield f"{mod.__name__}.{name}", f, ()
                 continue
             assert len(marks) == 1, name
             argnames, argvalues = marks[0].args[0], marks[0].args[1]
-            several = "," in argnames if isinstance(argnames, str) else len(argnames) > 1
+            names = [a.strip() for a in argnames.split(",")] if isinstance(argnames, str) else list(argnames)
+            if params != names:
+                continue
             for v in argvalues:
                 vals = getattr(v, "values", v)
-                yield f"{mod.__name__}.{name}{vals}", f, tuple(vals) if several else (vals,)
+                yield f"{mod.__name__}.{name}{vals}", f, tuple(vals) if len(names) > 1 else (vals,)
 
 
-def _failing_pins() -> List[str]:
+def _failing_pins(mods=None, first=False) -> List[str]:
     failed = []
-    for name, f, args in _pin_calls():
+    for name, f, args in _pin_calls(PINS if mods is None else mods):
         try:
             f(*args)
         except Exception:        # an assertion, or a mistake that breaks the caller
             failed.append(name)
+            if first:
+                break
     return failed
 
 
@@ -188,3 +205,77 @@ def test_chunked_run_that_ignores_a_failing_chunk_fails_a_pin(monkeypatch):
         return np.concatenate(ks), np.concatenate(ls), int(w.size)
     monkeypatch.setattr(oracle, "lex_chunks", lex_chunks)
     assert _failing_pins(), "no pin catches a chunked run that reads past a failing chunk"
+
+
+# The Python submodules of the oracle: mutated source text, loaded in place
+# of the real module, then that module's own pins loaded against it.
+
+SUB_PINS = {"contexts": "test_oracle_contexts.py", "live": "test_oracle_live.py",
+            "windows": "test_oracle_windows.py", "model": "test_oracle_model.py"}
+
+
+def _swap_submodule(monkeypatch, sub, old, new):
+    path = os.path.join(os.path.dirname(oracle.__file__), sub + ".py")
+    src = open(path).read()
+    if old is not None:
+        assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+        src = src.replace(old, new)
+    mod = types.ModuleType("oracle." + sub)
+    mod.__file__ = path
+    mod.__package__ = "oracle"
+    exec(compile(src, path, "exec"), mod.__dict__)
+    monkeypatch.setitem(sys.modules, "oracle." + sub, mod)
+    monkeypatch.setattr(oracle, sub, mod, raising=False)
+    return [_load_module(SUB_PINS[sub])]
+
+
+PY_MUTATIONS = [
+    # entry contexts (the serial scan's state at an offset)
+    ("contexts", "context one byte late", "q = int(a.delta[q, w[p - 1]])", "q = int(a.delta[q, w[p]])"),
+    ("contexts", "halting offset not a boundary", "ctx[s] = BOUNDARY           # s == con(w)", "pass"),
+    ("contexts", "candidates without BOUNDARY", "return [BOUNDARY] + sorted(out)", "return sorted(out)"),
+    ("contexts", "first accepting end in a chunk run",
+     "last, kind = j, int(a.tau[q])\n    return last, kind",
+     "last, kind = j, int(a.tau[q])\n            break\n    return last, kind"),
+    ("contexts", "exit context from the chunk start",
+     "_state_after(a, w, a.q0, pos, p1)), None\n        pos = e",
+     "_state_after(a, w, a.q0, p0, p1)), None\n        pos = e"),
+    ("contexts", "exit context not passed on", "toks, ctx, fail = chunk_run(a, w, p0, p1, ctx)",
+     "toks, _, fail = chunk_run(a, w, p0, p1, ctx)"),
+    # live sets (the failed-lookahead guard)
+    ("live", "walk starts one byte late", "        j = k\n", "        j = k + 1\n"),
+    ("live", "acceptance only at the end of the input", "hit = acc[cur]", "hit = acc[cur] & (j + 1 == n)"),
+    ("live", "guard reads the next offset's set", "while j < n and live[j, q]:",
+     "while j < n and live[min(j + 1, n), q]:"),
+    ("live", "guarded scan ends every token at the first accept",
+     "last, kind = j, int(a.tau[q])\n        if last is None:",
+     "last, kind = j, int(a.tau[q])\n                break\n        if last is None:"),
+    # two-byte split windows
+    ("windows", "delta+ leaving Q+ counted as defined", "return t if t >= 0 and live[q] and live[t] else -1",
+     "return t if t >= 0 else -1"),
+    ("windows", "Z(a) without the states that start a token",
+     "Z = {dplus(q, x) for q in states} - {-1}", "Z = {dplus(q, x) for q in states if q != a.q0} - {-1}"),
+    ("windows", "delta+(q0, b) not required", "if dplus(a.q0, y) < 0:\n                continue", "pass"),
+    ("windows", "window bytes transposed", "P[w[p - 1], w[p]]", "P[w[p], w[p - 1]]"),
+    # the FP64 model
+    ("model", "kernel flipped in the forward convolution", "hp[:, k:k + W], Wc[:, k, :])",
+     "hp[:, K - 1 - k:K - 1 - k + W], Wc[:, k, :])"),
+    ("model", "softmax gradient without the label term", "dz[np.arange(B), y] -= 1.0", "pass"),
+    ("model", "sum instead of mean in the gradient", "dz /= B", "pass"),
+    ("model", "hidden ReLU mask dropped", "da1 = (dz @ W2.T) * (a1 > 0)", "da1 = dz @ W2.T"),
+    ("model", "embedding gradient with repeated bytes overwritten", "np.add.at(gemb, x, dh0)", "gemb[x] += dh0"),
+    ("model", "window one byte late", "q = int(p) - W // 2 + k", "q = int(p) - W // 2 + k + 1"),
+    ("model", "bfloat16 by truncation", "r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "r = (u >> 16) << 16"),
+]
+
+
+@pytest.mark.parametrize("sub", sorted(SUB_PINS))
+def test_unmutated_submodule_passes_its_pins(monkeypatch, sub):
+    mods = _swap_submodule(monkeypatch, sub, None, None)
+    assert _failing_pins(mods) == []
+
+
+@pytest.mark.parametrize("sub,name,old,new", PY_MUTATIONS, ids=[f"{m[0]}: {m[1]}" for m in PY_MUTATIONS])
+def test_planted_mistake_in_a_python_oracle_fails_a_pin(monkeypatch, sub, name, old, new):
+    mods = _swap_submodule(monkeypatch, sub, old, new)
+    assert _failing_pins(mods, first=True), f"no pin catches: {sub}: {name}"

@@ -69,6 +69,22 @@ def test_definition_2_on_random_sets(seed):
         assert bool(cert.exact[b]) == bool(P[:, b].all())
 
 
+@pytest.mark.parametrize("make", [T.ab_dead_chain, T.detached_state], ids=["ab_dead_chain", "detached_state"])
+def test_definition_2_on_the_live_subautomaton_examples(make):
+    # Section 4.1: states outside Q+ (a dead chain, a detached state) take no
+    # part in Definition 2, nor in the window condition built on delta+
+    d = make()
+    cert = oracle.certificates(d)
+    P = W.window_pairs(d)
+    start = d.delta_full()[d.q0]
+    assert not cert.reentrant and cert.exact.any()
+    for b in range(256):
+        if start[b] < 0 or not cert.live[start[b]]:
+            assert not P[:, b].any()
+            continue
+        assert bool(cert.exact[b]) == bool(P[:, b].all()), b
+
+
 def _boundaries(lens):
     return set(np.cumsum(lens).tolist()) | {0}
 
