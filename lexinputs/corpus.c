@@ -89,7 +89,7 @@ static void put(sink_t *s, uint8_t c)
 }
 static void puts_(sink_t *s, const char *t) { while (*t) put(s, (uint8_t)*t++); }
 
-static const char LOWER[] = "abcdefghijklmnopqrstuvwxyz";
+static const uint8_t LOWER[] = "abcdefghijklmnopqrstuvwxyz";
 static const char ALNUM[] = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ0123456789";
 static const char HEX[] = "0123456789abcdefABCDEF";
 
